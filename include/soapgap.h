@@ -1,0 +1,178 @@
+/*
+ * soapgap.h -- C ABI of the GB300 library for the separable-density SOAP descriptor
+ * and the GAP energy / forces / virial built on it (Caro, arXiv:1905.02142).
+ *
+ * Problem statement (Sec. I-IV of the paper): given periodic structures (Cartesian
+ * positions, lattice vectors, species), a cutoff r_cut, basis sizes n_max, l_max and the
+ * atom widths, compute for every atom i
+ *   c_nlm(i)  the expansion coefficients of its smoothed neighbour density (Eqs. 01, 05,
+ *             08, 15; the density smoothing of Sec. III.B; the radial recursion Eq. 04),
+ *   p_nn'l(i) = sum_m c_nlm c_n'lm   (Eq. 09),   q(i) = p(i) / |p(i)|   (Sec. I),
+ *   eps_i     = sum_s alpha_s (q_i . q_s)^zeta  over a sparse set (Sec. IV.A),
+ * the energy of each structure, the forces -dE/dx and the virial -dE/dstrain.
+ *
+ * Conventions
+ *   - Lengths in Angstrom.  cell rows are the lattice vectors; positions must lie inside
+ *     their cell (fractional coordinates in [0, 1)), otherwise SOAPGAP_E_INVALID_ARG.
+ *   - Neighbours: every atom j in every periodic image S with |x_j + S.h - x_i| < r_cut
+ *     (strict), except (i, i, S = 0); atom i itself enters once as the central term.
+ *   - Species map to separate density channels: channel = species(j) * n_max + n.
+ *   - Angular functions are real spherical harmonics; p is identical to Eq. 09's.
+ *   - Packed descriptor layout (length D = n_ch (n_ch+1)/2 * (l_max+1), n_ch = n_species
+ *     * n_max): for each channel pair c1 <= c2 (row-major upper triangle) and each
+ *     l = 0..l_max, p[c1][c2][l] times sqrt(2) when c1 != c2, so that dot products of
+ *     packed vectors equal the full sums over (n, n', l).  q uses this layout.
+ *   - Virial: W_ab = -sum over pairs (dE/dr_ij)_a (r_ij)_b  (= -dE/dstrain_ab).
+ *
+ * Precision (soapgap_params.precision)
+ *   SOAPGAP_FP64  every step in FP64: the radial recursion per pair in the primitive basis,
+ *                 the orthonormalisation W = S^-1/2 per atom, FP64 GEMM for the GAP kernel.
+ *   SOAPGAP_MIXED pair and power-spectrum kernels in FP32 with radial functions taken from
+ *                 an FP64-built table of the orthonormal-basis coefficients; GAP products
+ *                 on the tensor cores with FP32 accumulation; FP64 per-structure sums.
+ *   Float outputs typed "real" below are float for MIXED and double for FP64.
+ *
+ * Errors: every call returns 0 (SOAPGAP_OK) or a negative code; soapgap_last_error()
+ * returns a message for the last failure on that handle.  No call throws.
+ * Memory: the caller owns every input and output buffer.  The handle owns a device
+ * workspace that grows on demand and lives until soapgap_destroy.
+ * Streams: device work is enqueued on the caller's stream.  soapgap_compute and
+ * soapgap_backward synchronise that stream once (to size the pair list) and again at
+ * the end to report device-side errors.
+ */
+#ifndef SOAPGAP_H
+#define SOAPGAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define SOAPGAP_OK 0
+#define SOAPGAP_E_INVALID_ARG (-1) /* bad pointer, size, parameter, or atom outside cell */
+#define SOAPGAP_E_UNSUPPORTED (-2) /* n_max or l_max outside the supported range        */
+#define SOAPGAP_E_CAPACITY (-3)    /* a fixed-size buffer is too small (see message)    */
+#define SOAPGAP_E_CUDA (-4)        /* a CUDA runtime call or kernel failed              */
+#define SOAPGAP_E_STATE (-5)       /* call order violated (no model / no forward pass)  */
+
+/* precision */
+#define SOAPGAP_FP64 0
+#define SOAPGAP_MIXED 1
+
+/* soapgap_compute flags */
+#define SOAPGAP_DESC 1u   /* write q and |p|                            */
+#define SOAPGAP_ENERGY 2u /* write e_atom and e_struct (needs a model)  */
+#define SOAPGAP_FORCES 4u /* write forces (needs a model)               */
+#define SOAPGAP_VIRIAL 8u /* write virial (needs a model)               */
+
+/* Limits: 2 <= n_max <= 12 (the basis degenerates beyond 12, Sec. III.A),
+ * 0 <= l_max <= 12, 1 <= n_species <= 8. */
+#define SOAPGAP_MAX_NMAX 12
+#define SOAPGAP_MAX_LMAX 12
+#define SOAPGAP_MAX_SPECIES 8
+
+/* Hyperparameters (Eq. 15 and Sec. III.A-B).
+ *   r_cut          hard cutoff r_hard (> 0)
+ *   r_soft         start of the buffer zone, 0 < r_soft <= r_cut (== r_cut: no buffer)
+ *   sigma_r0       sigma_{0,r} (> 0), also the width of the Gaussian basis function
+ *   sigma_p0       sigma_{0,perp} (> 0)
+ *   alpha_r        d sigma_r / d r_j  (>= 0)
+ *   alpha_p        d sigma_perp / d r_j (>= 0)
+ *   amp_a          exponent a of the amplitude polynomial (>= 0)
+ *   n_f            filter parameter of the buffer zone (> 0; the paper uses 4)
+ *   central_weight weight of the central atom's own Gaussian (1 = counted once)
+ *   eq08_weight    0: angular weight 4 pi e^{-z} i_l(z) (projection of the Kaufmann
+ *                  expansion); 1: Eq. 08 as printed, with an extra (2l+1).            */
+typedef struct soapgap_params {
+    double r_cut, r_soft;
+    double sigma_r0, sigma_p0, alpha_r, alpha_p, amp_a, n_f, central_weight;
+    int32_t n_max, l_max, n_species;
+    int32_t precision;   /* SOAPGAP_FP64 or SOAPGAP_MIXED */
+    int32_t eq08_weight; /* 0 or 1 */
+} soapgap_params;
+
+/* A batch of periodic structures stored back to back.
+ *   atom_offs_host [n_struct+1] host int64, atom_offs_host[0] = 0, nondecreasing,
+ *                  atom_offs_host[n_struct] = n_atoms; atoms of structure s are
+ *                  atom_offs_host[s] .. atom_offs_host[s+1]-1
+ *   cell_host      [n_struct][3][3] host double, rows = lattice vectors, det != 0
+ *   pos            [n_atoms][3] DEVICE double, Cartesian, inside the cell
+ *   species        [n_atoms] DEVICE int32 in [0, n_species)                          */
+typedef struct soapgap_batch {
+    int32_t n_struct;
+    int32_t n_atoms;
+    const int64_t* atom_offs_host;
+    const double* cell_host;
+    const double* pos;
+    const int32_t* species;
+} soapgap_batch;
+
+typedef struct soapgap_handle soapgap_handle;
+
+/* Create a handle: validates the parameters, builds W = S^-1/2 in FP64 on the host
+ * (Sec. III.A) and, for MIXED, the radial table on the device.  *out is NULL on error. */
+int soapgap_create(const soapgap_params* params, soapgap_handle** out);
+
+/* The radial orthonormaliser W = S^-1/2 of Sec. III.A for (n_max, r_cut, sigma_r0), as the
+ * handle uses it: W [n_max][n_max] HOST double, row-major (g_n = sum_a W[n][a] phi_a).
+ * S is built and diagonalised in binary128 on the host and W rounded to FP64; no device
+ * work.  SOAPGAP_E_UNSUPPORTED if n_max is outside [2, 12] or S is not positive definite. */
+int soapgap_orthonormaliser(int32_t n_max, double r_cut, double sigma_r0, double* W);
+
+/* Packed descriptor length D. */
+int soapgap_descriptor_dim(const soapgap_handle* h, int32_t* dim);
+
+/* Set the GAP model (Sec. IV.A): q_sparse [M][D] host double, packed layout, each row a
+ * normalised descriptor; alpha [M] host double; zeta > 0.  Copies to the device and
+ * synchronises.  M >= 1. */
+int soapgap_set_model(soapgap_handle* h, const double* q_sparse, const double* alpha,
+                      int32_t m, double zeta);
+
+/* Forward evaluation on `stream` (a cudaStream_t, NULL = default stream).
+ * flags: any of SOAPGAP_DESC | ENERGY | FORCES | VIRIAL.  Outputs are DEVICE pointers;
+ * a NULL output is skipped, but every output selected by `flags` must be non-NULL:
+ *   q        [n_atoms][D] real      pnorm   [n_atoms] real   (|p| per atom)
+ *   e_atom   [n_atoms] real         e_struct [n_struct] double
+ *   forces   [n_atoms][3] double    virial  [n_struct][3][3] double
+ * With ENERGY the handle keeps what soapgap_backward needs. */
+int soapgap_compute(soapgap_handle* h, const soapgap_batch* batch, uint32_t flags,
+                    void* q, void* pnorm, void* e_atom, double* e_struct, double* forces,
+                    double* virial, void* stream);
+
+/* Adjoint of the last ENERGY evaluation on this handle, for the same batch:
+ * dE_dEstruct [n_struct] DEVICE double (weights of each structure's energy);
+ * grad_pos [n_atoms][3] DEVICE double receives d(sum_s w_s E_s)/dx (i.e. minus the
+ * force when w = 1); virial [n_struct][3][3] DEVICE double or NULL.
+ * Returns SOAPGAP_E_STATE without a preceding ENERGY evaluation. */
+int soapgap_backward(soapgap_handle* h, const soapgap_batch* batch, const double* dE_dEstruct,
+                     double* grad_pos, double* virial, void* stream);
+
+/* Same as soapgap_compute, but pos/species and every output are HOST pointers; the
+ * library copies inputs to its workspace and results back on `stream` and returns
+ * after the stream has finished. */
+int soapgap_compute_host(soapgap_handle* h, const soapgap_batch* batch, uint32_t flags,
+                         void* q, void* pnorm, void* e_atom, double* e_struct, double* forces,
+                         double* virial, void* stream);
+
+/* Number of neighbour pairs found by the last compute call (diagnostics). */
+int soapgap_last_pair_count(const soapgap_handle* h, int64_t* n_pairs);
+
+/* Copy the pair list of the last soapgap_compute call to HOST arrays, in canonical order
+ * (centre, neighbour species, neighbour, then shift S lexicographically):
+ *   centre[P], neighbour[P] int32 atom indices; shift[P][3] int32 image S (x_j + S.h).
+ * `capacity` is the length of the arrays; SOAPGAP_E_CAPACITY if it is below P. */
+int soapgap_export_pairs(soapgap_handle* h, int64_t capacity, int32_t* centre,
+                         int32_t* neighbour, int32_t* shift);
+
+/* Message describing the last error on h ("" if none); valid until the next call. */
+const char* soapgap_last_error(const soapgap_handle* h);
+
+/* Release the handle and its workspace (NULL is ignored). */
+void soapgap_destroy(soapgap_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SOAPGAP_H */

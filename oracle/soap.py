@@ -196,24 +196,45 @@ def associated_legendre(x: torch.Tensor, l_max: int) -> torch.Tensor:
                         for l in range(l_max + 1)], dim=-2)
 
 
+def reduced_legendre(x: torch.Tensor, l_max: int) -> torch.Tensor:
+    """P_lm(x) / (1-x^2)^(m/2) for 0 <= m <= l <= l_max (Condon-Shortley phase): the same
+    recursion in l as ``associated_legendre``, started from (-1)^m (2m-1)!!, so that the
+    sin(theta)^m factor can be carried by (x + iy)^m instead (no pole singularity)."""
+    rows = [[None] * (l_max + 1) for _ in range(l_max + 1)]
+    for m in range(l_max + 1):
+        pmm = torch.full_like(x, (-1.0) ** m * _double_factorial(2 * m - 1))
+        rows[m][m] = pmm
+        if m + 1 <= l_max:
+            rows[m + 1][m] = (2 * m + 1) * x * pmm
+        for l in range(m + 2, l_max + 1):
+            rows[l][m] = ((2 * l - 1) * x * rows[l - 1][m] - (l + m - 1) * rows[l - 2][m]) / (l - m)
+    zero = torch.zeros_like(x)
+    return torch.stack([torch.stack([rows[l][m] if m <= l else zero
+                                     for m in range(l_max + 1)], dim=-1)
+                        for l in range(l_max + 1)], dim=-2)
+
+
 def conj_spherical_harmonics(rhat: torch.Tensor, l_max: int):
     """Real and imaginary parts of Y*_lm(theta_j, phi_j), m >= 0 (Sec. III.C):
-    sqrt((2l+1)(l-m)! / (4 pi (l+m)!)) e^{-i m phi} P_lm(cos theta), with cos(m phi),
-    sin(m phi) from the Chebyshev recursion.  Returns two [P, l+1, m+1] tensors."""
+    sqrt((2l+1)(l-m)! / (4 pi (l+m)!)) e^{-i m phi} P_lm(cos theta).
+
+    sin(theta)^m e^{i m phi} = (x + i y)^m on the unit sphere, so the harmonics are
+    evaluated as the reduced P_lm times C_m - i S_m, where C_m = rho^m cos(m phi) and
+    S_m = rho^m sin(m phi) follow the Chebyshev recursion of Sec. III.C multiplied by
+    rho^m: C_m = 2x C_{m-1} - rho^2 C_{m-2} (same for S_m).  This is the same function
+    without the division by rho, so it and its gradient stay finite on the z axis.
+    Returns two [P, l+1, m+1] tensors.
+    """
     x, y, z = rhat[:, 0], rhat[:, 1], rhat[:, 2]
-    rho = torch.sqrt(x * x + y * y)
-    on_axis = rho == 0.0
-    safe = torch.where(on_axis, torch.ones_like(rho), rho)
-    cphi = torch.where(on_axis, torch.ones_like(rho), x / safe)
-    sphi = torch.where(on_axis, torch.zeros_like(rho), y / safe)
-    cos_m = [torch.ones_like(x), cphi]
-    sin_m = [torch.zeros_like(x), sphi]
+    rho2 = x * x + y * y
+    cos_m = [torch.ones_like(x), x]
+    sin_m = [torch.zeros_like(x), y]
     for m in range(2, l_max + 1):
-        cos_m.append(2.0 * cphi * cos_m[m - 1] - cos_m[m - 2])
-        sin_m.append(2.0 * cphi * sin_m[m - 1] - sin_m[m - 2])
+        cos_m.append(2.0 * x * cos_m[m - 1] - rho2 * cos_m[m - 2])
+        sin_m.append(2.0 * x * sin_m[m - 1] - rho2 * sin_m[m - 2])
     cos_m = torch.stack(cos_m[:l_max + 1], dim=-1)   # [P, m]
     sin_m = torch.stack(sin_m[:l_max + 1], dim=-1)
-    plm = associated_legendre(z, l_max)              # [P, l, m]
+    plm = reduced_legendre(z, l_max)                 # [P, l, m]
     k = np.zeros((l_max + 1, l_max + 1))
     for l in range(l_max + 1):
         for m in range(l + 1):

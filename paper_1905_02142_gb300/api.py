@@ -1,0 +1,221 @@
+"""Python binding of the CUDA library: handle management and argument marshalling.
+
+Every step of the computation runs in the library's CUDA kernels; this module only
+passes pointers (PyTorch CUDA tensors provide device memory and the stream).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+class SoapGapError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"soapgap error {code}: {msg}")
+        self.code = code
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    raise TypeError(type(t))
+
+
+class Structures:
+    """A batch of periodic structures: host metadata plus device positions/species."""
+
+    def __init__(self, pos, cell, species, atom_offs, device="cuda"):
+        self.atom_offs = np.ascontiguousarray(np.asarray(atom_offs, dtype=np.int64))
+        self.cell = np.ascontiguousarray(np.asarray(cell, dtype=np.float64).reshape(-1, 3, 3))
+        self.n_struct = int(self.cell.shape[0])
+        if isinstance(pos, torch.Tensor):
+            self.pos = pos.detach().to(device=device, dtype=torch.float64).contiguous()
+        else:
+            self.pos = torch.as_tensor(np.asarray(pos, dtype=np.float64), device=device).contiguous()
+        if isinstance(species, torch.Tensor):
+            self.species = species.to(device=device, dtype=torch.int32).contiguous()
+        else:
+            self.species = torch.as_tensor(np.asarray(species, dtype=np.int32), device=device).contiguous()
+        self.n_atoms = int(self.pos.shape[0])
+
+    @staticmethod
+    def from_batch(b, device="cuda") -> "Structures":
+        """From a synth.Batch (NumPy arrays)."""
+        return Structures(b.pos, b.cell, b.species, b.atom_offs, device=device)
+
+    def c_batch(self, pos=None, species=None) -> L.Batch:
+        return L.Batch(self.n_struct, self.n_atoms, self.atom_offs.ctypes.data, self.cell.ctypes.data,
+                       _ptr(self.pos if pos is None else pos),
+                       _ptr(self.species if species is None else species))
+
+
+class SoapGap:
+    """One descriptor/GAP configuration on the current CUDA device.
+
+    precision: "mixed" (FP32 pair kernels, tensor-core GAP) or "fp64".
+    """
+
+    def __init__(self, *, r_cut, r_soft=None, sigma_r0=0.5, sigma_p0=None, alpha_r=0.0,
+                 alpha_p=0.0, amp_a=1.0, n_f=4.0, central_weight=1.0, n_max=8, l_max=8,
+                 n_species=1, precision="mixed", eq08_weight=False):
+        self.lib = L.load()
+        self.precision = precision
+        self.dtype = torch.float32 if precision == "mixed" else torch.float64
+        p = L.Params(r_cut, r_cut if r_soft is None else r_soft, sigma_r0,
+                     sigma_r0 if sigma_p0 is None else sigma_p0, alpha_r, alpha_p, amp_a, n_f,
+                     central_weight, n_max, l_max, n_species,
+                     L.MIXED if precision == "mixed" else L.FP64, int(bool(eq08_weight)))
+        self.params = p
+        h = ctypes.c_void_p()
+        rc = self.lib.soapgap_create(ctypes.byref(p), ctypes.byref(h))
+        if rc != L.OK:
+            raise SoapGapError(rc, "soapgap_create failed (see stderr)")
+        self.h = h
+        d = ctypes.c_int32()
+        self._check(self.lib.soapgap_descriptor_dim(self.h, ctypes.byref(d)))
+        self.dim = int(d.value)
+        self.m = 0
+
+    @classmethod
+    def from_dict(cls, d: dict, precision="mixed"):
+        keys = ("r_cut", "r_soft", "sigma_r0", "sigma_p0", "alpha_r", "alpha_p", "amp_a", "n_f",
+                "central_weight", "n_max", "l_max", "n_species", "eq08_weight")
+        return cls(precision=precision, **{k: d[k] for k in keys if k in d})
+
+    def _check(self, rc):
+        if rc != L.OK:
+            msg = self.lib.soapgap_last_error(self.h)
+            raise SoapGapError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.soapgap_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_model(self, q_sparse, alpha, zeta):
+        qs = np.ascontiguousarray(np.asarray(q_sparse, dtype=np.float64))
+        al = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64))
+        if qs.ndim != 2 or qs.shape[1] != self.dim or al.shape != (qs.shape[0],):
+            raise ValueError(f"q_sparse must be [M, {self.dim}] and alpha [M]")
+        self._check(self.lib.soapgap_set_model(self.h, qs.ctypes.data, al.ctypes.data,
+                                               qs.shape[0], float(zeta)))
+        self.m = qs.shape[0]
+
+    def compute(self, s: Structures, *, desc=False, energy=False, forces=False, virial=False,
+                stream=None):
+        """Run one evaluation; returns a dict of CUDA tensors for the requested outputs."""
+        dev = s.pos.device
+        n, ns = s.n_atoms, s.n_struct
+        flags = (L.DESC if desc else 0) | (L.ENERGY if energy else 0) | \
+            (L.FORCES if forces else 0) | (L.VIRIAL if virial else 0)
+        out = {}
+        if desc:
+            out["q"] = torch.empty((n, self.dim), dtype=self.dtype, device=dev)
+            out["pnorm"] = torch.empty((n,), dtype=self.dtype, device=dev)
+        if energy:
+            out["e_atom"] = torch.empty((n,), dtype=self.dtype, device=dev)
+            out["e_struct"] = torch.empty((ns,), dtype=torch.float64, device=dev)
+        if forces:
+            out["forces"] = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        if virial:
+            out["virial"] = torch.empty((ns, 3, 3), dtype=torch.float64, device=dev)
+        st = (stream or torch.cuda.current_stream(dev)).cuda_stream
+        b = s.c_batch()
+        self._check(self.lib.soapgap_compute(
+            self.h, ctypes.byref(b), flags, _ptr(out.get("q")), _ptr(out.get("pnorm")),
+            _ptr(out.get("e_atom")), _ptr(out.get("e_struct")), _ptr(out.get("forces")),
+            _ptr(out.get("virial")), st))
+        return out
+
+    def backward(self, s: Structures, dE_dEstruct: torch.Tensor, virial=False, stream=None):
+        """Gradient of sum_s w_s E_s with respect to positions (after an energy evaluation)."""
+        dev = s.pos.device
+        w = dE_dEstruct.to(device=dev, dtype=torch.float64).contiguous()
+        grad = torch.empty((s.n_atoms, 3), dtype=torch.float64, device=dev)
+        vir = torch.empty((s.n_struct, 3, 3), dtype=torch.float64, device=dev) if virial else None
+        st = (stream or torch.cuda.current_stream(dev)).cuda_stream
+        b = s.c_batch()
+        self._check(self.lib.soapgap_backward(self.h, ctypes.byref(b), _ptr(w), _ptr(grad),
+                                              _ptr(vir), st))
+        return (grad, vir) if virial else grad
+
+    def compute_host(self, pos, cell, species, atom_offs, *, desc=False, energy=False,
+                     forces=False, virial=False):
+        """End-to-end call with host (NumPy) inputs and outputs."""
+        pos = np.ascontiguousarray(np.asarray(pos, dtype=np.float64))
+        species = np.ascontiguousarray(np.asarray(species, dtype=np.int32))
+        atom_offs = np.ascontiguousarray(np.asarray(atom_offs, dtype=np.int64))
+        cell = np.ascontiguousarray(np.asarray(cell, dtype=np.float64).reshape(-1, 3, 3))
+        n, ns = pos.shape[0], cell.shape[0]
+        npdt = np.float32 if self.precision == "mixed" else np.float64
+        flags = (L.DESC if desc else 0) | (L.ENERGY if energy else 0) | \
+            (L.FORCES if forces else 0) | (L.VIRIAL if virial else 0)
+        out = {}
+        if desc:
+            out["q"] = np.empty((n, self.dim), npdt)
+            out["pnorm"] = np.empty((n,), npdt)
+        if energy:
+            out["e_atom"] = np.empty((n,), npdt)
+            out["e_struct"] = np.empty((ns,), np.float64)
+        if forces:
+            out["forces"] = np.empty((n, 3), np.float64)
+        if virial:
+            out["virial"] = np.empty((ns, 3, 3), np.float64)
+        b = L.Batch(ns, n, atom_offs.ctypes.data, cell.ctypes.data, pos.ctypes.data,
+                    species.ctypes.data)
+        st = torch.cuda.current_stream().cuda_stream
+        self._check(self.lib.soapgap_compute_host(
+            self.h, ctypes.byref(b), flags, _ptr(out.get("q")), _ptr(out.get("pnorm")),
+            _ptr(out.get("e_atom")), _ptr(out.get("e_struct")), _ptr(out.get("forces")),
+            _ptr(out.get("virial")), st))
+        return out
+
+    def pair_count(self) -> int:
+        n = ctypes.c_int64()
+        self._check(self.lib.soapgap_last_pair_count(self.h, ctypes.byref(n)))
+        return int(n.value)
+
+    def pairs(self):
+        """Pair list of the last compute call: (centre, neighbour, shift[P, 3]) as NumPy."""
+        p = self.pair_count()
+        i = np.empty(max(p, 1), np.int32)
+        j = np.empty(max(p, 1), np.int32)
+        s = np.empty((max(p, 1), 3), np.int32)
+        self._check(self.lib.soapgap_export_pairs(self.h, p, i.ctypes.data, j.ctypes.data,
+                                                  s.ctypes.data))
+        return i[:p], j[:p], s[:p]
+
+
+class SoapGapEnergy(torch.autograd.Function):
+    """E_struct = GAP energies of a batch, differentiable with respect to positions.
+
+    forward(pos [N,3] CUDA float64, model: SoapGap, s: Structures) -> E_struct [S] float64.
+    The backward pass is the library's adjoint kernel chain (soapgap_backward).
+    """
+
+    @staticmethod
+    def forward(ctx, pos, model: SoapGap, s: Structures):
+        s2 = Structures(pos.detach(), s.cell, s.species, s.atom_offs, device=pos.device)
+        out = model.compute(s2, energy=True)
+        ctx.model = model
+        ctx.s = s2
+        return out["e_struct"]
+
+    @staticmethod
+    def backward(ctx, grad_e):
+        grad = ctx.model.backward(ctx.s, grad_e.detach())
+        return grad, None, None

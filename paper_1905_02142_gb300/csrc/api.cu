@@ -1,0 +1,599 @@
+// C ABI of the library (declared in include/soapgap.h): argument checks, FP64 set-up of
+// the radial basis on the host, the device workspace, and the launch sequence of one
+// evaluation.  No exception crosses the ABI; every failure returns a negative code and
+// leaves a message in the handle.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/soapgap.h"
+#include "internal.h"
+#include "soapmath.cuh"
+
+// --------------------------------------------------------------------- helpers
+int sg_cap_class(int nmax, int lmax) {
+  int m = nmax > lmax ? nmax : lmax;
+  return m <= 6 ? 0 : (m <= 8 ? 1 : (m <= 10 ? 2 : 3));
+}
+int sg_cap_n(int cls) { return 6 + 2 * cls; }
+int sg_cap_l(int cls) { return 6 + 2 * cls; }
+
+namespace {
+
+struct Buf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+cudaError_t ensure(Buf& b, size_t bytes) {
+  if (bytes <= b.cap && b.p) return cudaSuccess;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+  size_t want = bytes + bytes / 4 + 256;
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e != cudaSuccess) return e;
+  b.cap = want;
+  return cudaSuccess;
+}
+
+template <typename T> YlmCoef<T> ylm_coefficients() {
+  YlmCoef<T> y;
+  std::memset(&y, 0, sizeof(y));
+  for (int m = 0; m <= SG_MAX_LMAX; ++m) {
+    double prod = 1.0;
+    for (int k = 1; k <= m; ++k) prod *= (2.0 * k - 1.0) / (2.0 * k);
+    double seed = std::sqrt((2.0 * m + 1.0) / (4.0 * M_PI) * prod);
+    if (m > 0) seed *= std::sqrt(2.0);
+    y.seed[m] = (T)seed;
+    y.s1[m] = (T)std::sqrt(2.0 * m + 3.0);
+    for (int l = 0; l <= SG_MAX_LMAX; ++l) {
+      if (l >= m + 2) {
+        double l2 = (double)l * l, m2 = (double)m * m;
+        y.a[l][m] = (T)std::sqrt((4.0 * l2 - 1.0) / (l2 - m2));
+        y.b[l][m] = (T)std::sqrt((2.0 * l + 1.0) * ((l - 1.0) * (l - 1.0) - m2) /
+                                 ((2.0 * l - 3.0) * (l2 - m2)));
+      }
+      if (l >= m) {
+        double d = std::sqrt((double)(l - m) * (l + m + 1));
+        if (m == 0) d /= std::sqrt(2.0);
+        y.d[l][m] = (T)d;
+      }
+    }
+  }
+  return y;
+}
+
+}  // namespace
+
+struct soapgap_handle {
+  soapgap_params prm;
+  DevParams dp;
+  int cls = 0, NC = 0, LC = 0;
+  int D = 0, nch = 0, L = 0;
+  bool mixed = false;
+  BasisConst<double> bc64;   // W and cen_alpha (recursion path)
+  BasisConst<float> bc32;    // cen_n (table path)
+  YlmCoef<float> yc32;
+  YlmCoef<double> yc64;
+  TableInfo ti{};
+  Buf table;
+  // model
+  int M = 0;
+  double zeta = 0;
+  Buf qs, alpha;
+  bool has_model = false;
+  // workspace
+  Buf geom, atom_offs, atom_struct, atom_bin, atom_slot, bin_count, bin_start, bin_atoms, binpos;
+  Buf seg_count, seg_offs, scan_tmp, key_tmp, r_tmp, key, pair_j, pair_r, rev, dedr;
+  Buf c, q, pnorm, e_atom, eps_part, kp, g, vir_atom, struct_w, err, cen_tmp;
+  Buf host_in_pos, host_in_species, host_q, host_pnorm, host_e_atom, host_e_struct, host_forces,
+      host_virial;
+  int* h_err = nullptr;           // pinned
+  int* h_count = nullptr;         // pinned
+  StructGeom* h_geom = nullptr;   // pinned staging
+  size_t h_geom_cap = 0;
+  double* h_w = nullptr;
+  size_t h_w_cap = 0;
+  std::string msg;
+  int64_t last_pairs = 0;
+  int fw_atoms = -1, fw_struct = -1;
+  bool have_forward = false;
+  int n_bins = 0;
+};
+
+static int fail(soapgap_handle* h, int code, const std::string& m) {
+  if (h) h->msg = m;
+  return code;
+}
+
+#define CK(h, x)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (x);                                                               \
+    if (e_ != cudaSuccess)                                                              \
+      return fail((h), SOAPGAP_E_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+static int check_params(const soapgap_params* p, std::string& why) {
+  if (!p) { why = "params is NULL"; return SOAPGAP_E_INVALID_ARG; }
+  if (!(p->r_cut > 0) || !std::isfinite(p->r_cut)) { why = "r_cut must be > 0"; return SOAPGAP_E_INVALID_ARG; }
+  if (!(p->r_soft > 0) || p->r_soft > p->r_cut) { why = "need 0 < r_soft <= r_cut"; return SOAPGAP_E_INVALID_ARG; }
+  if (!(p->sigma_r0 > 0) || !(p->sigma_p0 > 0)) { why = "atom sigmas must be > 0"; return SOAPGAP_E_INVALID_ARG; }
+  if (!(p->alpha_r >= 0) || !(p->alpha_p >= 0) || !(p->amp_a >= 0)) { why = "alpha_r, alpha_p, amp_a must be >= 0"; return SOAPGAP_E_INVALID_ARG; }
+  if (p->r_soft < p->r_cut && !(p->n_f > 0)) { why = "n_f must be > 0"; return SOAPGAP_E_INVALID_ARG; }
+  if (!std::isfinite(p->central_weight)) { why = "central_weight must be finite"; return SOAPGAP_E_INVALID_ARG; }
+  if (p->precision != SOAPGAP_FP64 && p->precision != SOAPGAP_MIXED) { why = "precision must be FP64 or MIXED"; return SOAPGAP_E_INVALID_ARG; }
+  if (p->eq08_weight != 0 && p->eq08_weight != 1) { why = "eq08_weight must be 0 or 1"; return SOAPGAP_E_INVALID_ARG; }
+  if (p->n_max < 2 || p->n_max > SOAPGAP_MAX_NMAX) { why = "n_max must be in [2, 12] (the basis degenerates beyond 12)"; return SOAPGAP_E_UNSUPPORTED; }
+  if (p->l_max < 0 || p->l_max > SOAPGAP_MAX_LMAX) { why = "l_max must be in [0, 12]"; return SOAPGAP_E_UNSUPPORTED; }
+  if (p->n_species < 1 || p->n_species > SOAPGAP_MAX_SPECIES) { why = "n_species must be in [1, 8]"; return SOAPGAP_E_UNSUPPORTED; }
+  return SOAPGAP_OK;
+}
+
+extern "C" int soapgap_create(const soapgap_params* params, soapgap_handle** out) {
+  if (!out) return SOAPGAP_E_INVALID_ARG;
+  *out = nullptr;
+  std::string why;
+  int rc = check_params(params, why);
+  if (rc != SOAPGAP_OK) {
+    std::fprintf(stderr, "soapgap_create: %s\n", why.c_str());
+    return rc;
+  }
+  soapgap_handle* h = new (std::nothrow) soapgap_handle();
+  if (!h) return SOAPGAP_E_CUDA;
+  h->prm = *params;
+  const soapgap_params& p = *params;
+  h->dp = DevParams{p.r_cut, p.r_soft, p.sigma_r0, p.sigma_p0, p.alpha_r, p.alpha_p, p.amp_a,
+                    p.n_f, p.central_weight, p.n_max, p.l_max, p.n_species, p.eq08_weight};
+  h->cls = sg_cap_class(p.n_max, p.l_max);
+  h->NC = sg_cap_n(h->cls);
+  h->LC = sg_cap_l(h->cls);
+  h->nch = p.n_species * p.n_max;
+  h->L = (p.l_max + 1) * (p.l_max + 1);
+  h->D = h->nch * (h->nch + 1) / 2 * (p.l_max + 1);
+  h->mixed = p.precision == SOAPGAP_MIXED;
+  // W = S^-1/2: built in binary128 on the host, rounded to FP64 (Sec. III.A)
+  double Wd[SG_MAX_NMAX * SG_MAX_NMAX], cond = 0;
+  if (sg_orthonormaliser_q(p.n_max, p.r_cut, p.sigma_r0, Wd, &cond) != 0) {
+    delete h;
+    std::fprintf(stderr, "soapgap_create: overlap matrix is not positive definite\n");
+    return SOAPGAP_E_UNSUPPORTED;
+  }
+  std::memset(&h->bc64, 0, sizeof(h->bc64));
+  std::memset(&h->bc32, 0, sizeof(h->bc32));
+  for (int a = 0; a < p.n_max; ++a)
+    for (int b = 0; b < p.n_max; ++b) {
+      h->bc64.W[a][b] = Wd[a * p.n_max + b];
+    }
+  h->yc32 = ylm_coefficients<float>();
+  h->yc64 = ylm_coefficients<double>();
+  // central-atom constants (and the radial table for the mixed path)
+  cudaError_t e = ensure(h->cen_tmp, 2 * SG_MAX_NMAX * sizeof(double));
+  if (e == cudaSuccess) e = sg_central_terms(h->dp, h->bc64, (double*)h->cen_tmp.p,
+                                             (double*)h->cen_tmp.p + SG_MAX_NMAX, 0);
+  double cen[2 * SG_MAX_NMAX];
+  if (e == cudaSuccess) e = cudaMemcpy(cen, h->cen_tmp.p, sizeof(cen), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) {
+    for (int n = 0; n < p.n_max; ++n) {
+      h->bc32.cen[n] = (float)cen[n];
+      h->bc64.cen[n] = cen[SG_MAX_NMAX + n];
+    }
+    if (h->mixed) {
+      double smin = std::min(p.sigma_r0, p.sigma_p0);
+      double ht = std::min(0.02, smin / 25.0);
+      h->ti.K = (int)std::ceil(p.r_cut / ht);
+      h->ti.h = p.r_cut / h->ti.K;
+      h->ti.fp = (h->NC + h->LC + 1 + 3) / 4 * 4;
+      e = ensure(h->table, (size_t)(h->ti.K + 1) * 2 * h->ti.fp * sizeof(float));
+      if (e == cudaSuccess) e = sg_build_table(h->dp, h->bc64, h->cls, h->ti, (float*)h->table.p, 0);
+      if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+  }
+  if (e == cudaSuccess) e = cudaMallocHost(&h->h_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&h->h_count, 2 * sizeof(int));
+  if (e == cudaSuccess) e = ensure(h->err, sizeof(int));
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "soapgap_create: CUDA error: %s\n", cudaGetErrorString(e));
+    soapgap_destroy(h);
+    return SOAPGAP_E_CUDA;
+  }
+  *out = h;
+  return SOAPGAP_OK;
+}
+
+extern "C" int soapgap_orthonormaliser(int32_t n_max, double r_cut, double sigma_r0, double* W) {
+  if (!W || !(r_cut > 0) || !(sigma_r0 > 0)) return SOAPGAP_E_INVALID_ARG;
+  if (n_max < 2 || n_max > SOAPGAP_MAX_NMAX) return SOAPGAP_E_UNSUPPORTED;
+  double cond = 0;
+  return sg_orthonormaliser_q(n_max, r_cut, sigma_r0, W, &cond) == 0 ? SOAPGAP_OK : SOAPGAP_E_UNSUPPORTED;
+}
+
+extern "C" int soapgap_descriptor_dim(const soapgap_handle* h, int32_t* dim) {
+  if (!h || !dim) return SOAPGAP_E_INVALID_ARG;
+  *dim = h->D;
+  return SOAPGAP_OK;
+}
+
+extern "C" int soapgap_set_model(soapgap_handle* h, const double* q_sparse, const double* alpha,
+                                 int32_t m, double zeta) {
+  if (!h) return SOAPGAP_E_INVALID_ARG;
+  if (!q_sparse || !alpha || m < 1) return fail(h, SOAPGAP_E_INVALID_ARG, "set_model: need q_sparse, alpha and m >= 1");
+  if (!(zeta > 0) || !std::isfinite(zeta)) return fail(h, SOAPGAP_E_INVALID_ARG, "set_model: zeta must be > 0");
+  const size_t nq = (size_t)m * h->D;
+  const size_t es = h->mixed ? sizeof(float) : sizeof(double);
+  CK(h, ensure(h->qs, nq * es));
+  CK(h, ensure(h->alpha, (size_t)m * es));
+  if (h->mixed) {
+    std::vector<float> a(nq), b(m);
+    for (size_t i = 0; i < nq; ++i) a[i] = (float)q_sparse[i];
+    for (int i = 0; i < m; ++i) b[i] = (float)alpha[i];
+    CK(h, cudaMemcpy(h->qs.p, a.data(), nq * es, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->alpha.p, b.data(), (size_t)m * es, cudaMemcpyHostToDevice));
+  } else {
+    CK(h, cudaMemcpy(h->qs.p, q_sparse, nq * es, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->alpha.p, alpha, (size_t)m * es, cudaMemcpyHostToDevice));
+  }
+  h->M = m;
+  h->zeta = zeta;
+  h->has_model = true;
+  return SOAPGAP_OK;
+}
+
+// ---------------------------------------------------------------- geometry set-up
+static int setup_geometry(soapgap_handle* h, const soapgap_batch* b) {
+  const int S = b->n_struct;
+  if ((size_t)S > h->h_geom_cap) {
+    if (h->h_geom) cudaFreeHost(h->h_geom);
+    h->h_geom = nullptr;
+    h->h_geom_cap = 0;
+    CK(h, cudaMallocHost(&h->h_geom, sizeof(StructGeom) * (size_t)S));
+    h->h_geom_cap = S;
+  }
+  const double rc = h->prm.r_cut;
+  int bins = 0;
+  for (int s = 0; s < S; ++s) {
+    StructGeom& g = h->h_geom[s];
+    const double* c = b->cell_host + 9 * s;
+    for (int k = 0; k < 9; ++k) { g.h[k] = c[k]; g.h32[k] = (float)c[k]; }
+    const double det = c[0] * (c[4] * c[8] - c[5] * c[7]) - c[1] * (c[3] * c[8] - c[5] * c[6]) +
+                       c[2] * (c[3] * c[7] - c[4] * c[6]);
+    if (!(std::fabs(det) > 0) || !std::isfinite(det))
+      return fail(h, SOAPGAP_E_INVALID_ARG, "cell of structure " + std::to_string(s) + " is singular");
+    // inverse (rows of h are lattice vectors; fractional = x @ hinv)
+    double inv[9] = {c[4] * c[8] - c[5] * c[7], c[2] * c[7] - c[1] * c[8], c[1] * c[5] - c[2] * c[4],
+                     c[5] * c[6] - c[3] * c[8], c[0] * c[8] - c[2] * c[6], c[2] * c[3] - c[0] * c[5],
+                     c[3] * c[7] - c[4] * c[6], c[1] * c[6] - c[0] * c[7], c[0] * c[4] - c[1] * c[3]};
+    for (int k = 0; k < 9; ++k) g.hinv[k] = inv[k] / det;
+    const int na = (int)(b->atom_offs_host[s + 1] - b->atom_offs_host[s]);
+    double H = 0;
+    int mmax = 0;
+    for (int k = 0; k < 3; ++k) {
+      const double* u = c + 3 * ((k + 1) % 3);
+      const double* v = c + 3 * ((k + 2) % 3);
+      const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2],
+                   cz = u[0] * v[1] - u[1] * v[0];
+      const double dk = std::fabs(det) / std::sqrt(cx * cx + cy * cy + cz * cz);
+      int nb = (int)std::floor(dk / rc);
+      if (nb < 1) nb = 1;
+      const int nb_cap = std::max(1, (int)std::cbrt((double)std::max(na, 1)) + 1);
+      if (nb > 2 * nb_cap) nb = 2 * nb_cap;  // no more bins than atoms need
+      g.nb[k] = nb;
+      g.m[k] = (int)std::floor(rc * nb / dk) + 1;
+      if (g.m[k] > 100)
+        return fail(h, SOAPGAP_E_UNSUPPORTED, "cell too thin for r_cut (more than 100 images)");
+      mmax = std::max(mmax, g.m[k]);
+      H += std::sqrt(c[3 * k] * c[3 * k] + c[3 * k + 1] * c[3 * k + 1] + c[3 * k + 2] * c[3 * k + 2]);
+    }
+    const double X = H * (mmax + 3), u = std::ldexp(1.0, -24);
+    g.margin = (float)(2.0 * (2.0 * std::sqrt(3.0) * 5.0 * rc * X * u + 4.0 * rc * rc * u) + 1e-30);
+    g.bin_off = bins;
+    g.atom_off = (int)b->atom_offs_host[s];
+    g.n_atoms = na;
+    bins += g.nb[0] * g.nb[1] * g.nb[2];
+  }
+  h->n_bins = bins;
+  return SOAPGAP_OK;
+}
+
+__global__ void atom_struct_kernel(const int64_t* offs, int S, int* out) {
+  int s = blockIdx.x;
+  if (s >= S) return;
+  for (int64_t i = offs[s] + threadIdx.x; i < offs[s + 1]; i += blockDim.x) out[i] = s;
+}
+
+__global__ void fill_ones(double* w, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) w[i] = 1.0;
+}
+
+static std::string device_error_text(int code) {
+  std::string m;
+  if (code & SG_ERR_OUTSIDE_CELL) m += "an atom lies outside its cell (fractional coordinate not in [0,1)); ";
+  if (code & SG_ERR_COINCIDENT) m += "two atoms coincide (zero separation); ";
+  if (code & SG_ERR_PAIR_CAPACITY) m += "pair buffer overflow; ";
+  if (code & SG_ERR_NO_REVERSE) m += "pair list not symmetric; ";
+  return m;
+}
+
+template <typename T>
+static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* q_out,
+               void* pnorm_out, void* e_atom_out, double* e_struct, double* forces,
+               double* virial, const double* struct_w_user, double* grad_pos, bool backward,
+               cudaStream_t st) {
+  const int N = b->n_atoms, S = b->n_struct, nsp = h->prm.n_species;
+  const bool want_energy = (flags & (SOAPGAP_ENERGY | SOAPGAP_FORCES | SOAPGAP_VIRIAL)) != 0;
+  const bool want_grad = backward || (flags & (SOAPGAP_FORCES | SOAPGAP_VIRIAL)) != 0;
+  const size_t es = sizeof(T);
+  NbrBuffers nb{};
+  if (!backward) {
+    int rc = setup_geometry(h, b);
+    if (rc != SOAPGAP_OK) return rc;
+    const int nseg = N * nsp;
+    CK(h, ensure(h->geom, sizeof(StructGeom) * (size_t)S));
+    CK(h, ensure(h->atom_offs, sizeof(int64_t) * (size_t)(S + 1)));
+    CK(h, ensure(h->atom_struct, sizeof(int) * (size_t)std::max(N, 1)));
+    CK(h, ensure(h->atom_bin, sizeof(int) * (size_t)std::max(N, 1)));
+    CK(h, ensure(h->atom_slot, sizeof(int) * (size_t)std::max(N, 1)));
+    CK(h, ensure(h->bin_atoms, sizeof(int) * (size_t)std::max(N, 1)));
+    CK(h, ensure(h->binpos, sizeof(float4) * (size_t)std::max(N, 1)));
+    CK(h, ensure(h->bin_count, sizeof(int) * (size_t)(h->n_bins + 1)));
+    CK(h, ensure(h->bin_start, sizeof(int) * (size_t)(h->n_bins + 1)));
+    CK(h, ensure(h->seg_count, sizeof(int) * (size_t)std::max(nseg, 1)));
+    CK(h, ensure(h->seg_offs, sizeof(int) * (size_t)(nseg + 1)));
+    CK(h, ensure(h->scan_tmp, sizeof(int) * sg_scan_tmp_ints(std::max(std::max(nseg, h->n_bins), 1))));
+    CK(h, cudaMemcpyAsync(h->geom.p, h->h_geom, sizeof(StructGeom) * (size_t)S, cudaMemcpyHostToDevice, st));
+    CK(h, cudaMemcpyAsync(h->atom_offs.p, b->atom_offs_host, sizeof(int64_t) * (size_t)(S + 1),
+                          cudaMemcpyHostToDevice, st));
+    CK(h, cudaMemsetAsync(h->err.p, 0, sizeof(int), st));
+    atom_struct_kernel<<<S, 128, 0, st>>>((const int64_t*)h->atom_offs.p, S, (int*)h->atom_struct.p);
+  }
+  nb.geom = (const StructGeom*)h->geom.p;
+  nb.atom_struct = (const int*)h->atom_struct.p;
+  nb.atom_bin = (int*)h->atom_bin.p;
+  nb.atom_slot = (int*)h->atom_slot.p;
+  nb.bin_count = (int*)h->bin_count.p;
+  nb.bin_start = (int*)h->bin_start.p;
+  nb.bin_atoms = (int*)h->bin_atoms.p;
+  nb.binpos = (float4*)h->binpos.p;
+  nb.seg_count = (int*)h->seg_count.p;
+  nb.seg_offs = (int*)h->seg_offs.p;
+  nb.scan_tmp = (int*)h->scan_tmp.p;
+  nb.err = (int*)h->err.p;
+  if (!backward) {
+    CK(h, sg_nbr_bin(b->pos, N, h->n_bins, nb, st));
+    CK(h, sg_nbr_count(b->pos, b->species, N, nsp, h->prm.r_cut, nb, st));
+    CK(h, cudaMemcpyAsync(h->h_count, (int*)h->seg_offs.p + N * nsp, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaMemcpyAsync(h->h_err, h->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    if (*h->h_err) return fail(h, SOAPGAP_E_INVALID_ARG, device_error_text(*h->h_err));
+    h->last_pairs = *h->h_count;
+  }
+  const long long P = h->last_pairs;
+  const size_t Pc = (size_t)std::max(P, 1LL);
+  CK(h, ensure(h->key_tmp, 8 * Pc));
+  CK(h, ensure(h->r_tmp, sizeof(Vec4<T>) * Pc));
+  CK(h, ensure(h->key, 8 * Pc));
+  CK(h, ensure(h->pair_j, 4 * Pc));
+  CK(h, ensure(h->pair_r, sizeof(Vec4<T>) * Pc));
+  CK(h, ensure(h->rev, 4 * Pc));
+  nb.key_tmp = (unsigned long long*)h->key_tmp.p;
+  nb.r_tmp = h->r_tmp.p;
+  nb.key = (unsigned long long*)h->key.p;
+  nb.pair_j = (int*)h->pair_j.p;
+  nb.pair_r = h->pair_r.p;
+  nb.rev = (int*)h->rev.p;
+  const int L = h->L, nch = h->nch, D = h->D;
+  const size_t N1 = (size_t)std::max(N, 1);
+  CK(h, ensure(h->c, es * N1 * nch * L));
+  CK(h, ensure(h->q, es * N1 * D));
+  CK(h, ensure(h->pnorm, es * N1));
+  if (!backward) {
+    CK(h, sg_nbr_fill<T>(b->pos, b->species, N, nsp, h->prm.r_cut, P, nb, st));
+    FwdArgs<T> fa{};
+    fa.n_atoms = N; fa.nsp = nsp; fa.nmax = h->prm.n_max; fa.lmax = h->prm.l_max;
+    fa.species = b->species; fa.seg_offs = nb.seg_offs; fa.pair_r = (const Vec4<T>*)h->pair_r.p;
+    fa.table = (const float*)h->table.p; fa.ti = h->ti; fa.p = h->dp;
+    if constexpr (sizeof(T) == 4) { fa.yc = h->yc32; fa.bc = h->bc32; }
+    else { fa.yc = h->yc64; fa.bc = h->bc64; }
+    fa.c = (T*)h->c.p;
+    CK(h, sg_pair_forward<T>(fa, h->cls, h->mixed, st));
+    CK(h, sg_power_spectrum<T>((const T*)h->c.p, N, nch, h->prm.l_max, (T*)h->q.p, (T*)h->pnorm.p, st));
+    if ((flags & SOAPGAP_DESC) && q_out)
+      CK(h, cudaMemcpyAsync(q_out, h->q.p, es * (size_t)N * D, cudaMemcpyDeviceToDevice, st));
+    if ((flags & SOAPGAP_DESC) && pnorm_out)
+      CK(h, cudaMemcpyAsync(pnorm_out, h->pnorm.p, es * (size_t)N, cudaMemcpyDeviceToDevice, st));
+  }
+  if (want_energy || backward) {
+    const int M = h->M;
+    const int tiles = sg_gap_tiles(M);
+    CK(h, ensure(h->eps_part, es * N1 * tiles));
+    CK(h, ensure(h->e_atom, es * N1));
+    if (want_grad) {
+      CK(h, ensure(h->kp, es * N1 * M));
+      CK(h, ensure(h->g, es * N1 * D));
+      CK(h, ensure(h->vir_atom, es * N1 * 9));
+      CK(h, ensure(h->dedr, sizeof(Vec4<T>) * Pc));
+      CK(h, ensure(h->struct_w, sizeof(double) * (size_t)S));
+    }
+    CK(h, sg_gap_forward_simt<T>((const T*)h->q.p, (const T*)h->qs.p, (const T*)h->alpha.p, N, M, D,
+                                 h->zeta, (T*)h->eps_part.p, tiles, want_grad ? (T*)h->kp.p : nullptr, st));
+    if (want_grad) {
+      CK(h, sg_gap_backward_simt<T>((const T*)h->kp.p, (const T*)h->qs.p, N, M, D, (T*)h->g.p, st));
+      if (struct_w_user) {
+        CK(h, cudaMemcpyAsync(h->struct_w.p, struct_w_user, sizeof(double) * S, cudaMemcpyDeviceToDevice, st));
+      } else {
+        fill_ones<<<(S + 255) / 256, 256, 0, st>>>((double*)h->struct_w.p, S);
+      }
+      AdjArgs<T> aa{};
+      aa.n_atoms = N; aa.nsp = nsp; aa.nmax = h->prm.n_max; aa.lmax = h->prm.l_max; aa.dim = D;
+      aa.species = b->species; aa.atom_struct = (const int*)h->atom_struct.p;
+      aa.struct_w = (const double*)h->struct_w.p; aa.seg_offs = nb.seg_offs;
+      aa.pair_r = (const Vec4<T>*)h->pair_r.p; aa.table = (const float*)h->table.p; aa.ti = h->ti;
+      aa.p = h->dp;
+      if constexpr (sizeof(T) == 4) { aa.yc = h->yc32; aa.bc = h->bc32; }
+      else { aa.yc = h->yc64; aa.bc = h->bc64; }
+      aa.c = (const T*)h->c.p; aa.q = (const T*)h->q.p; aa.pnorm = (const T*)h->pnorm.p;
+      aa.g = (const T*)h->g.p; aa.dedr = (Vec4<T>*)h->dedr.p; aa.vir_atom = (T*)h->vir_atom.p;
+      cudaError_t e = sg_pair_adjoint<T>(aa, h->cls, h->mixed, st);
+      if (e == cudaErrorInvalidConfiguration)
+        return fail(h, SOAPGAP_E_UNSUPPORTED, "descriptor too large for the adjoint kernel's shared memory");
+      CK(h, e);
+    }
+    double* f_out = backward ? grad_pos : ((flags & SOAPGAP_FORCES) ? forces : nullptr);
+    double* v_out = (backward || (flags & SOAPGAP_VIRIAL)) ? virial : nullptr;
+    double* es_out = backward ? nullptr : e_struct;
+    CK(h, sg_finish<T>(N, S, nsp, (const int64_t*)h->atom_offs.p, nb.seg_offs, (const int*)h->rev.p,
+                       (const Vec4<T>*)h->dedr.p, (const T*)h->eps_part.p, tiles,
+                       v_out ? (const T*)h->vir_atom.p : nullptr, (T*)h->e_atom.p, es_out, f_out,
+                       v_out, !backward, st));
+    if (!backward && e_atom_out)
+      CK(h, cudaMemcpyAsync(e_atom_out, h->e_atom.p, es * (size_t)N, cudaMemcpyDeviceToDevice, st));
+  }
+  CK(h, cudaMemcpyAsync(h->h_err, h->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  if (*h->h_err) return fail(h, SOAPGAP_E_INVALID_ARG, device_error_text(*h->h_err));
+  if (!backward) {
+    h->have_forward = want_energy;
+    h->fw_atoms = N;
+    h->fw_struct = S;
+  }
+  h->msg.clear();
+  return SOAPGAP_OK;
+}
+
+static int check_batch(soapgap_handle* h, const soapgap_batch* b) {
+  if (!b) return fail(h, SOAPGAP_E_INVALID_ARG, "batch is NULL");
+  if (b->n_struct < 1 || b->n_atoms < 0) return fail(h, SOAPGAP_E_INVALID_ARG, "need n_struct >= 1 and n_atoms >= 0");
+  if (!b->atom_offs_host || !b->cell_host) return fail(h, SOAPGAP_E_INVALID_ARG, "atom_offs_host and cell_host are required");
+  if (b->atom_offs_host[0] != 0 || b->atom_offs_host[b->n_struct] != b->n_atoms)
+    return fail(h, SOAPGAP_E_INVALID_ARG, "atom_offs_host must start at 0 and end at n_atoms");
+  for (int s = 0; s < b->n_struct; ++s)
+    if (b->atom_offs_host[s + 1] < b->atom_offs_host[s]) return fail(h, SOAPGAP_E_INVALID_ARG, "atom_offs_host must be nondecreasing");
+  if (b->n_atoms > 0 && (!b->pos || !b->species)) return fail(h, SOAPGAP_E_INVALID_ARG, "pos and species are required");
+  if ((long long)b->n_atoms * h->prm.n_species >= (1LL << 30)) return fail(h, SOAPGAP_E_UNSUPPORTED, "too many atoms");
+  return SOAPGAP_OK;
+}
+
+extern "C" int soapgap_compute(soapgap_handle* h, const soapgap_batch* batch, uint32_t flags,
+                               void* q, void* pnorm, void* e_atom, double* e_struct, double* forces,
+                               double* virial, void* stream) {
+  if (!h) return SOAPGAP_E_INVALID_ARG;
+  int rc = check_batch(h, batch);
+  if (rc != SOAPGAP_OK) return rc;
+  if (flags & ~(SOAPGAP_DESC | SOAPGAP_ENERGY | SOAPGAP_FORCES | SOAPGAP_VIRIAL))
+    return fail(h, SOAPGAP_E_INVALID_ARG, "unknown flag bits");
+  if ((flags & SOAPGAP_DESC) && !q) return fail(h, SOAPGAP_E_INVALID_ARG, "DESC needs q");
+  if ((flags & SOAPGAP_ENERGY) && (!e_struct && !e_atom)) return fail(h, SOAPGAP_E_INVALID_ARG, "ENERGY needs e_struct or e_atom");
+  if ((flags & SOAPGAP_FORCES) && !forces) return fail(h, SOAPGAP_E_INVALID_ARG, "FORCES needs forces");
+  if ((flags & SOAPGAP_VIRIAL) && !virial) return fail(h, SOAPGAP_E_INVALID_ARG, "VIRIAL needs virial");
+  if ((flags & (SOAPGAP_ENERGY | SOAPGAP_FORCES | SOAPGAP_VIRIAL)) && !h->has_model)
+    return fail(h, SOAPGAP_E_STATE, "no GAP model: call soapgap_set_model first");
+  if (!(flags & SOAPGAP_DESC)) { q = nullptr; pnorm = nullptr; }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->mixed)
+    return run<float>(h, batch, flags, q, pnorm, e_atom, e_struct, forces, virial, nullptr, nullptr, false, st);
+  return run<double>(h, batch, flags, q, pnorm, e_atom, e_struct, forces, virial, nullptr, nullptr, false, st);
+}
+
+extern "C" int soapgap_backward(soapgap_handle* h, const soapgap_batch* batch, const double* dE_dEstruct,
+                                double* grad_pos, double* virial, void* stream) {
+  if (!h) return SOAPGAP_E_INVALID_ARG;
+  int rc = check_batch(h, batch);
+  if (rc != SOAPGAP_OK) return rc;
+  if (!h->have_forward || h->fw_atoms != batch->n_atoms || h->fw_struct != batch->n_struct)
+    return fail(h, SOAPGAP_E_STATE, "backward needs a preceding ENERGY evaluation of the same batch");
+  if (!dE_dEstruct || !grad_pos) return fail(h, SOAPGAP_E_INVALID_ARG, "backward needs dE_dEstruct and grad_pos");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->mixed)
+    return run<float>(h, batch, 0, nullptr, nullptr, nullptr, nullptr, nullptr, virial, dE_dEstruct, grad_pos, true, st);
+  return run<double>(h, batch, 0, nullptr, nullptr, nullptr, nullptr, nullptr, virial, dE_dEstruct, grad_pos, true, st);
+}
+
+extern "C" int soapgap_compute_host(soapgap_handle* h, const soapgap_batch* batch, uint32_t flags,
+                                    void* q, void* pnorm, void* e_atom, double* e_struct,
+                                    double* forces, double* virial, void* stream) {
+  if (!h) return SOAPGAP_E_INVALID_ARG;
+  int rc = check_batch(h, batch);
+  if (rc != SOAPGAP_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = batch->n_atoms, S = batch->n_struct, D = h->D;
+  const size_t es = h->mixed ? sizeof(float) : sizeof(double);
+  const size_t N1 = (size_t)std::max(N, 1);
+  CK(h, ensure(h->host_in_pos, sizeof(double) * 3 * N1));
+  CK(h, ensure(h->host_in_species, sizeof(int) * N1));
+  CK(h, cudaMemcpyAsync(h->host_in_pos.p, batch->pos, sizeof(double) * 3 * (size_t)N, cudaMemcpyHostToDevice, st));
+  CK(h, cudaMemcpyAsync(h->host_in_species.p, batch->species, sizeof(int) * (size_t)N, cudaMemcpyHostToDevice, st));
+  soapgap_batch db = *batch;
+  db.pos = (const double*)h->host_in_pos.p;
+  db.species = (const int32_t*)h->host_in_species.p;
+  void *dq = nullptr, *dpn = nullptr, *dea = nullptr;
+  double *des = nullptr, *df = nullptr, *dv = nullptr;
+  if (q) { CK(h, ensure(h->host_q, es * N1 * D)); dq = h->host_q.p; }
+  if (pnorm) { CK(h, ensure(h->host_pnorm, es * N1)); dpn = h->host_pnorm.p; }
+  if (e_atom) { CK(h, ensure(h->host_e_atom, es * N1)); dea = h->host_e_atom.p; }
+  if (e_struct) { CK(h, ensure(h->host_e_struct, sizeof(double) * S)); des = (double*)h->host_e_struct.p; }
+  if (forces) { CK(h, ensure(h->host_forces, sizeof(double) * 3 * N1)); df = (double*)h->host_forces.p; }
+  if (virial) { CK(h, ensure(h->host_virial, sizeof(double) * 9 * S)); dv = (double*)h->host_virial.p; }
+  rc = soapgap_compute(h, &db, flags, dq, dpn, dea, des, df, dv, stream);
+  if (rc != SOAPGAP_OK) return rc;
+  if (q && (flags & SOAPGAP_DESC)) CK(h, cudaMemcpyAsync(q, dq, es * (size_t)N * D, cudaMemcpyDeviceToHost, st));
+  if (pnorm && (flags & SOAPGAP_DESC)) CK(h, cudaMemcpyAsync(pnorm, dpn, es * (size_t)N, cudaMemcpyDeviceToHost, st));
+  if (e_atom && (flags & SOAPGAP_ENERGY)) CK(h, cudaMemcpyAsync(e_atom, dea, es * (size_t)N, cudaMemcpyDeviceToHost, st));
+  if (e_struct && (flags & SOAPGAP_ENERGY)) CK(h, cudaMemcpyAsync(e_struct, des, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
+  if (forces && (flags & SOAPGAP_FORCES)) CK(h, cudaMemcpyAsync(forces, df, sizeof(double) * 3 * (size_t)N, cudaMemcpyDeviceToHost, st));
+  if (virial && (flags & SOAPGAP_VIRIAL)) CK(h, cudaMemcpyAsync(virial, dv, sizeof(double) * 9 * S, cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  return SOAPGAP_OK;
+}
+
+extern "C" int soapgap_last_pair_count(const soapgap_handle* h, int64_t* n) {
+  if (!h || !n) return SOAPGAP_E_INVALID_ARG;
+  *n = h->last_pairs;
+  return SOAPGAP_OK;
+}
+
+extern "C" int soapgap_export_pairs(soapgap_handle* h, int64_t capacity, int32_t* centre,
+                                    int32_t* neighbour, int32_t* shift) {
+  if (!h || !centre || !neighbour || !shift) return SOAPGAP_E_INVALID_ARG;
+  const long long P = h->last_pairs;
+  if (capacity < P) return fail(h, SOAPGAP_E_CAPACITY, "export_pairs: arrays shorter than the pair count");
+  if (P == 0) return SOAPGAP_OK;
+  const int N = h->fw_atoms, nsp = h->prm.n_species;
+  std::vector<int> offs((size_t)N * nsp + 1);
+  std::vector<unsigned long long> keys((size_t)P);
+  CK(h, cudaMemcpy(offs.data(), h->seg_offs.p, sizeof(int) * offs.size(), cudaMemcpyDeviceToHost));
+  CK(h, cudaMemcpy(keys.data(), h->key.p, 8 * (size_t)P, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < N; ++i)
+    for (int p = offs[(size_t)i * nsp]; p < offs[(size_t)(i + 1) * nsp]; ++p) centre[p] = i;
+  for (long long p = 0; p < P; ++p) {
+    const unsigned long long k = keys[p];
+    neighbour[p] = (int32_t)(k >> 24);
+    shift[3 * p] = (int)((k >> 16) & 255) - 128;
+    shift[3 * p + 1] = (int)((k >> 8) & 255) - 128;
+    shift[3 * p + 2] = (int)(k & 255) - 128;
+  }
+  return SOAPGAP_OK;
+}
+
+extern "C" const char* soapgap_last_error(const soapgap_handle* h) {
+  return h ? h->msg.c_str() : "NULL handle";
+}
+
+extern "C" void soapgap_destroy(soapgap_handle* h) {
+  if (!h) return;
+  Buf* bufs[] = {&h->table, &h->qs, &h->alpha, &h->geom, &h->atom_offs, &h->atom_struct,
+                 &h->atom_bin, &h->atom_slot, &h->bin_count, &h->bin_start, &h->bin_atoms,
+                 &h->binpos, &h->seg_count, &h->seg_offs, &h->scan_tmp, &h->key_tmp, &h->r_tmp,
+                 &h->key, &h->pair_j, &h->pair_r, &h->rev, &h->dedr, &h->c, &h->q, &h->pnorm,
+                 &h->e_atom, &h->eps_part, &h->kp, &h->g, &h->vir_atom, &h->struct_w, &h->err,
+                 &h->cen_tmp, &h->host_in_pos, &h->host_in_species, &h->host_q, &h->host_pnorm,
+                 &h->host_e_atom, &h->host_e_struct, &h->host_forces, &h->host_virial};
+  for (Buf* b : bufs)
+    if (b->p) cudaFree(b->p);
+  if (h->h_err) cudaFreeHost(h->h_err);
+  if (h->h_count) cudaFreeHost(h->h_count);
+  if (h->h_geom) cudaFreeHost(h->h_geom);
+  delete h;
+}

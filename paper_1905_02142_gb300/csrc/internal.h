@@ -1,0 +1,124 @@
+// Launch interfaces between the C-ABI layer (api.cu) and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "common.cuh"
+
+// Compile-time capacity class of the pair kernels: (n_max, l_max) <= (NC, LC).
+int sg_cap_class(int nmax, int lmax);            // 0..3 -> (6,6) (8,8) (10,10) (12,12)
+int sg_cap_n(int cls);
+int sg_cap_l(int cls);
+
+// ---------------------------------------------------------------- basis_host.cpp
+// W = S^-1/2 (row-major, FP64) from a binary128 computation; returns 0 or -1.
+int sg_orthonormaliser_q(int nmax, double rc, double s0, double* W, double* cond);
+
+// ---------------------------------------------------------------- tables.cu
+struct TableInfo {
+  int K;         // intervals
+  int fp;        // floats per half-node (values, then h*derivatives): padded NC+LC+1
+  double h;      // node spacing
+};
+// Builds, for r_k = k h (k = 0..K), b_n(r) in the orthonormal basis (n < nmax, padded to NC),
+// 4 pi ilexp_l(z(r)) [x (2l+1) with eq08] (l <= lmax, padded to LC+1), and h * d/dr of each.
+cudaError_t sg_build_table(const DevParams& p, const BasisConst<double>& W, int cls,
+                           const TableInfo& ti, float* table, cudaStream_t st);
+// Central-atom constants: cen_n (orthonormal basis, for the table path) and cen_alpha.
+cudaError_t sg_central_terms(const DevParams& p, const BasisConst<double>& W, double* out_n,
+                             double* out_alpha, cudaStream_t st);
+
+// ---------------------------------------------------------------- neighbours.cu
+struct NbrBuffers {
+  const StructGeom* geom;    // [S]
+  const int* atom_struct;    // [N]
+  int* atom_bin;             // [N]
+  int* atom_slot;            // [N]
+  int* bin_count;            // [nbins]
+  int* bin_start;            // [nbins + 1]
+  int* bin_atoms;            // [N]
+  int* seg_count;            // [N*nsp]
+  int* seg_offs;             // [N*nsp + 1]
+  float4* binpos;            // [N] FP32 positions in bin order, .w = atom index
+  unsigned long long* key_tmp;  // [cap]
+  void* r_tmp;               // [cap] Vec4<T>, unsorted
+  unsigned long long* key;   // [cap]
+  int* pair_j;               // [cap]
+  void* pair_r;              // [cap] Vec4<T>
+  int* rev;                  // [cap]
+  int* scan_tmp;             // scan scratch
+  int* err;                  // device error word
+};
+size_t sg_scan_tmp_ints(int n);
+cudaError_t sg_exclusive_scan(const int* in, int* out, int n, int* tmp, cudaStream_t st);
+cudaError_t sg_nbr_bin(const double* pos, int n_atoms, int n_bins, const NbrBuffers& b,
+                       cudaStream_t st);
+cudaError_t sg_nbr_count(const double* pos, const int* species, int n_atoms, int nsp, double rc,
+                         const NbrBuffers& b, cudaStream_t st);
+template <typename T>
+cudaError_t sg_nbr_fill(const double* pos, const int* species, int n_atoms, int nsp, double rc,
+                        long long cap, const NbrBuffers& b, cudaStream_t st);
+
+// ---------------------------------------------------------------- pair_fwd.cu
+template <typename T> struct FwdArgs {
+  int n_atoms, nsp, nmax, lmax;
+  const int* species;
+  const int* seg_offs;
+  const Vec4<T>* pair_r;
+  const float* table;     // table path
+  TableInfo ti;
+  DevParams p;            // recursion path
+  YlmCoef<T> yc;
+  BasisConst<T> bc;       // W (recursion path) and central terms (both)
+  T* c;                   // [N][nsp*nmax][L]
+};
+template <typename T> cudaError_t sg_pair_forward(const FwdArgs<T>& a, int cls, bool table,
+                                                  cudaStream_t st);
+
+// ---------------------------------------------------------------- powspec.cu
+template <typename T>
+cudaError_t sg_power_spectrum(const T* c, int n_atoms, int nch, int lmax, T* q, T* pnorm,
+                              cudaStream_t st);
+
+// ---------------------------------------------------------------- gap_simt.cu
+// eps_part[i][t] = sum over sparse tile t of alpha_s S_is^zeta,
+// kp[i][s] = zeta alpha_s S_is^(zeta-1)   (kp may be NULL: energy only)
+template <typename T>
+cudaError_t sg_gap_forward_simt(const T* q, const T* qs, const T* alpha, int n, int m, int d,
+                                double zeta, T* eps_part, int n_tiles, T* kp, cudaStream_t st);
+int sg_gap_tiles(int m);
+// g[i][k] = sum_s kp[i][s] qs[s][k]
+template <typename T>
+cudaError_t sg_gap_backward_simt(const T* kp, const T* qs, int n, int m, int d, T* g,
+                                 cudaStream_t st);
+
+// ---------------------------------------------------------------- pair_adj.cu
+template <typename T> struct AdjArgs {
+  int n_atoms, nsp, nmax, lmax, dim;
+  const int* species;
+  const int* atom_struct;
+  const double* struct_w;   // [S] dE/dE_struct
+  const int* seg_offs;
+  const Vec4<T>* pair_r;
+  const float* table;
+  TableInfo ti;
+  DevParams p;
+  YlmCoef<T> yc;
+  BasisConst<T> bc;
+  const T* c;               // [N][nch][L]
+  const T* q;               // [N][D]
+  const T* pnorm;           // [N]
+  const T* g;               // [N][D] dE/dq (before the structure weight)
+  Vec4<T>* dedr;            // [P] dE/dr_ij
+  T* vir_atom;              // [N][9]
+};
+template <typename T> cudaError_t sg_pair_adjoint(const AdjArgs<T>& a, int cls, bool table,
+                                                  cudaStream_t st);
+
+// ---------------------------------------------------------------- forces.cu
+template <typename T>
+cudaError_t sg_finish(int n_atoms, int n_struct, int nsp, const int64_t* atom_offs_dev,
+                      const int* seg_offs, const int* rev, const Vec4<T>* dedr,
+                      const T* eps_part, int n_tiles, const T* vir_atom, T* e_atom,
+                      double* e_struct, double* forces, double* virial, bool sign_force,
+                      cudaStream_t st);

@@ -1,0 +1,373 @@
+// Cell-list neighbour builder, bit-exact against a brute-force FP64 search.
+//
+// A pair (i, j, S) is kept when |x_j + S.h - x_i|^2 < r_cut^2, evaluated in FP64 with
+// one fixed operation order and no contraction into FMA:
+//   s = (S1*h1 + S2*h2) + S3*h3,  r = (x_j + s) - x_i  in canonical orientation
+//   (i < j, or i == j with S lexicographically positive), r = -((x_i + (-s)) - x_j)
+//   otherwise, d2 = (rx*rx + ry*ry) + rz*rz.
+// The canonical orientation makes the set exactly symmetric ((j, i, -S) is kept with
+// r_ji = -r_ij bit for bit), which the deterministic force gather relies on.
+// Candidates come from bins laid out in fractional coordinates; an FP32 distance decides
+// every candidate whose d2 is farther than a rigorous rounding margin from r_cut^2 (or
+// from 0), and the FP64 expression decides the rest, so the set equals the FP64 one.
+// Pairs of each (centre, neighbour species) segment are sorted by (j, S).
+#include "internal.h"
+
+// ---------------------------------------------------------------- scan
+#define SCAN_BLOCK 1024
+size_t sg_scan_tmp_ints(int n) { return (size_t)(n + SCAN_BLOCK - 1) / SCAN_BLOCK + 1; }
+
+__global__ void scan_block_sums(const int* in, int n, int* sums) {
+  __shared__ int sh[32];
+  int i = blockIdx.x * SCAN_BLOCK + threadIdx.x;
+  int v = 0;
+  for (int k = 0; k < SCAN_BLOCK / 256; ++k) {
+    int idx = blockIdx.x * SCAN_BLOCK + k * 256 + threadIdx.x;
+    if (idx < n) v += in[idx];
+  }
+  (void)i;
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int w = threadIdx.x < 8 ? sh[threadIdx.x] : 0;
+    w = warp_sum(w);
+    if (threadIdx.x == 0) sums[blockIdx.x] = w;
+  }
+}
+
+// single block: exclusive scan of the block sums in place (nb <= a few thousand)
+__global__ void scan_sums(int* sums, int nb) {
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += 1024) {
+    int idx = base + threadIdx.x;
+    int v = idx < nb ? sums[idx] : 0;
+    // block inclusive scan
+    __shared__ int sh[1024];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      int t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += t;
+      __syncthreads();
+    }
+    int incl = sh[threadIdx.x];
+    int c = carry;
+    if (idx < nb) sums[idx] = c + incl - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = c + incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sums[nb] = carry;
+}
+
+__global__ void scan_apply(const int* in, int* out, int n, const int* sums) {
+  __shared__ int sh[SCAN_BLOCK];
+  const int base = blockIdx.x * SCAN_BLOCK;
+  for (int k = threadIdx.x; k < SCAN_BLOCK; k += blockDim.x) sh[k] = (base + k < n) ? in[base + k] : 0;
+  __syncthreads();
+  // per-thread sequential chunk of 4, then a block scan of chunk totals
+  const int t = threadIdx.x;  // 256 threads, 4 items each
+  int v0 = sh[4 * t], v1 = sh[4 * t + 1], v2 = sh[4 * t + 2], v3 = sh[4 * t + 3];
+  int tot = v0 + v1 + v2 + v3;
+  __shared__ int ts[256];
+  ts[t] = tot;
+  __syncthreads();
+  for (int o = 1; o < 256; o <<= 1) {
+    int x = t >= o ? ts[t - o] : 0;
+    __syncthreads();
+    ts[t] += x;
+    __syncthreads();
+  }
+  int excl = ts[t] - tot + sums[blockIdx.x];
+  int idx = base + 4 * t;
+  if (idx < n) out[idx] = excl;
+  if (idx + 1 < n) out[idx + 1] = excl + v0;
+  if (idx + 2 < n) out[idx + 2] = excl + v0 + v1;
+  if (idx + 3 < n) out[idx + 3] = excl + v0 + v1 + v2;
+  if (blockIdx.x == gridDim.x - 1 && t == 255) out[n] = sums[gridDim.x];
+}
+
+// out[0..n] = exclusive scan of in[0..n-1], out[n] = total.  tmp: sg_scan_tmp_ints(n) ints.
+cudaError_t sg_exclusive_scan(const int* in, int* out, int n, int* tmp, cudaStream_t st) {
+  if (n <= 0) {
+    cudaMemsetAsync(out, 0, sizeof(int), st);
+    return cudaGetLastError();
+  }
+  const int nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
+  scan_block_sums<<<nb, 256, 0, st>>>(in, n, tmp);
+  scan_sums<<<1, 1024, 0, st>>>(tmp, nb);
+  scan_apply<<<nb, 256, 0, st>>>(in, out, n, tmp);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- binning
+__global__ void bin_assign(const double* __restrict__ pos, int n, NbrBuffers b) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const StructGeom& g = b.geom[b.atom_struct[i]];
+  double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+  int bi[3];
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double f = x * g.hinv[k] + y * g.hinv[3 + k] + z * g.hinv[6 + k];
+    if (!(f >= -1e-9 && f < 1.0 + 1e-9)) bad = true;
+    int c = (int)floor(f * g.nb[k]);
+    c = c < 0 ? 0 : (c >= g.nb[k] ? g.nb[k] - 1 : c);
+    bi[k] = c;
+  }
+  if (bad) atomicOr(b.err, SG_ERR_OUTSIDE_CELL);
+  int id = g.bin_off + (bi[0] * g.nb[1] + bi[1]) * g.nb[2] + bi[2];
+  b.atom_bin[i] = id;
+  b.atom_slot[i] = atomicAdd(&b.bin_count[id], 1);
+}
+
+__global__ void bin_fill(const double* __restrict__ pos, int n, NbrBuffers b, float4* binpos) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int at = b.bin_start[b.atom_bin[i]] + b.atom_slot[i];
+  b.bin_atoms[at] = i;
+  binpos[at] = make_float4((float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2],
+                           __int_as_float(i));
+}
+
+cudaError_t sg_nbr_bin(const double* pos, int n_atoms, int n_bins, const NbrBuffers& b,
+                       cudaStream_t st) {
+  cudaMemsetAsync(b.bin_count, 0, sizeof(int) * (size_t)n_bins, st);
+  if (n_atoms > 0) bin_assign<<<(n_atoms + 255) / 256, 256, 0, st>>>(pos, n_atoms, b);
+  cudaError_t e = sg_exclusive_scan(b.bin_count, b.bin_start, n_bins, b.scan_tmp, st);
+  if (e != cudaSuccess) return e;
+  if (n_atoms > 0)
+    bin_fill<<<(n_atoms + 255) / 256, 256, 0, st>>>(pos, n_atoms, b, b.binpos);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- pair search
+__device__ __forceinline__ int floor_div(int a, int n) { return a >= 0 ? a / n : -((-a + n - 1) / n); }
+
+__device__ __forceinline__ bool lex_positive(int s1, int s2, int s3) {
+  return s1 > 0 || (s1 == 0 && (s2 > 0 || (s2 == 0 && s3 > 0)));
+}
+
+// exact FP64 separation (fixed operation order, no FMA) in canonical orientation
+__device__ __forceinline__ void exact_sep(const double* __restrict__ pos, int i, int j,
+                                         const double s[3], bool canon, double r[3],
+                                         double& d2) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double xi = pos[3 * i + c], xj = pos[3 * j + c];
+    r[c] = canon ? __dsub_rn(__dadd_rn(xj, s[c]), xi) : -__dsub_rn(__dadd_rn(xi, -s[c]), xj);
+  }
+  d2 = __dadd_rn(__dadd_rn(__dmul_rn(r[0], r[0]), __dmul_rn(r[1], r[1])), __dmul_rn(r[2], r[2]));
+}
+
+// Visit every kept pair of atom i; lanes of the warp take candidates in parallel.
+// fn(lane_has_pair, j, S1, S2, S3, r[3], d2) is called by all lanes together.
+template <typename Fn>
+__device__ __forceinline__ void visit_pairs(const double* __restrict__ pos, const float4* binpos,
+                                            int i, double rc, const NbrBuffers& b, Fn&& fn) {
+  const int lane = threadIdx.x & 31;
+  const StructGeom& g = b.geom[b.atom_struct[i]];
+  const double rc2 = rc * rc;
+  const float rc2f = (float)rc2;
+  const float margin = g.margin;
+  const float xi = (float)pos[3 * i], yi = (float)pos[3 * i + 1], zi = (float)pos[3 * i + 2];
+  const int bin = b.atom_bin[i] - g.bin_off;
+  const int c0 = bin / (g.nb[1] * g.nb[2]), c1 = (bin / g.nb[2]) % g.nb[1], c2 = bin % g.nb[2];
+  for (int d0 = -g.m[0]; d0 <= g.m[0]; ++d0) {
+    const int t0 = c0 + d0, S1 = floor_div(t0, g.nb[0]), b0 = t0 - S1 * g.nb[0];
+    for (int d1 = -g.m[1]; d1 <= g.m[1]; ++d1) {
+      const int t1 = c1 + d1, S2 = floor_div(t1, g.nb[1]), b1 = t1 - S2 * g.nb[1];
+      for (int d2i = -g.m[2]; d2i <= g.m[2]; ++d2i) {
+        const int t2 = c2 + d2i, S3 = floor_div(t2, g.nb[2]), b2 = t2 - S3 * g.nb[2];
+        double s[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          s[c] = __dadd_rn(__dadd_rn(__dmul_rn((double)S1, g.h[c]), __dmul_rn((double)S2, g.h[3 + c])),
+                           __dmul_rn((double)S3, g.h[6 + c]));
+        const float sx = (float)s[0], sy = (float)s[1], sz = (float)s[2];
+        const int tb = g.bin_off + (b0 * g.nb[1] + b1) * g.nb[2] + b2;
+        const int beg = b.bin_start[tb], end = b.bin_start[tb + 1];
+        const bool zero_shift = (S1 == 0 && S2 == 0 && S3 == 0);
+        const bool lexpos = lex_positive(S1, S2, S3);
+        for (int base = beg; base < end; base += 32) {
+          const int k = base + lane;
+          bool keep = false;
+          int j = -1;
+          double r[3] = {0, 0, 0}, d2 = 0;
+          if (k < end) {
+            const float4 pj = binpos[k];
+            j = __float_as_int(pj.w);
+            if (!(j == i && zero_shift)) {
+              // explicit round-to-nearest ops: the count and fill kernels decide alike
+              const float dx = __fsub_rn(__fadd_rn(pj.x, sx), xi);
+              const float dy = __fsub_rn(__fadd_rn(pj.y, sy), yi);
+              const float dz = __fsub_rn(__fadd_rn(pj.z, sz), zi);
+              const float d2f = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+              const bool near_cut = fabsf(d2f - rc2f) <= margin;
+              const bool near_zero = d2f <= margin;
+              if (near_cut || near_zero || d2f < rc2f) {
+                if (near_cut || near_zero) {
+                  const bool canon = (j > i) || (j == i && lexpos);
+                  exact_sep(pos, i, j, s, canon, r, d2);
+                  keep = d2 < rc2;
+                  if (keep && d2 == 0.0) atomicOr(b.err, SG_ERR_COINCIDENT);
+                } else {
+                  keep = true;
+                  d2 = -1.0;  // exact value computed on demand by the caller
+                }
+              }
+            }
+          }
+          fn(keep, j, S1, S2, S3, s, r, d2);
+        }
+      }
+    }
+  }
+}
+
+__global__ void count_kernel(const double* __restrict__ pos, const int* __restrict__ species,
+                             int n, int nsp, double rc, NbrBuffers b, const float4* binpos) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const int i = warp;
+  int cnt[SG_MAX_SPECIES];
+#pragma unroll
+  for (int s = 0; s < SG_MAX_SPECIES; ++s) cnt[s] = 0;
+  visit_pairs(pos, binpos, i, rc, b,
+              [&](bool keep, int j, int, int, int, const double*, const double*, double) {
+                if (keep) {
+                  const int sj = species[j];
+#pragma unroll
+                  for (int s = 0; s < SG_MAX_SPECIES; ++s) cnt[s] += (s == sj);
+                }
+              });
+  for (int s = 0; s < nsp; ++s) {
+    int v = warp_sum(cnt[s]);
+    if (lane == 0) b.seg_count[i * nsp + s] = v;
+  }
+}
+
+cudaError_t sg_nbr_count(const double* pos, const int* species, int n_atoms, int nsp, double rc,
+                         const NbrBuffers& b, cudaStream_t st) {
+  if (n_atoms > 0) {
+    const int threads = 128;
+    const long long blocks = ((long long)n_atoms * 32 + threads - 1) / threads;
+    count_kernel<<<(unsigned)blocks, threads, 0, st>>>(pos, species, n_atoms, nsp, rc, b,
+                                                      b.binpos);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return sg_exclusive_scan(b.seg_count, b.seg_offs, n_atoms * nsp, b.scan_tmp, st);
+}
+
+__device__ __forceinline__ unsigned long long pair_key(int j, int s1, int s2, int s3) {
+  return ((unsigned long long)(unsigned)j << 24) | ((unsigned long long)(s1 + 128) << 16) |
+         ((unsigned long long)(s2 + 128) << 8) | (unsigned long long)(s3 + 128);
+}
+
+template <typename T>
+__global__ void fill_kernel(const double* __restrict__ pos, const int* __restrict__ species,
+                            int n, int nsp, double rc, long long cap, NbrBuffers b,
+                            const float4* binpos, Vec4<T>* rout) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const int i = warp;
+  int next[SG_MAX_SPECIES];
+  for (int s = 0; s < nsp; ++s) next[s] = b.seg_offs[i * nsp + s];
+  visit_pairs(pos, binpos, i, rc, b,
+              [&](bool keep, int j, int S1, int S2, int S3, const double* s, const double* r0,
+                  double d2) {
+                int sj = keep ? species[j] : -1;
+                for (int sp = 0; sp < nsp; ++sp) {
+                  const unsigned mask = __ballot_sync(0xffffffffu, keep && sj == sp);
+                  if (keep && sj == sp) {
+                    const int at = next[sp] + __popc(mask & ((1u << lane) - 1u));
+                    double r[3] = {r0[0], r0[1], r0[2]};
+                    if (d2 < 0.0) {
+                      const bool canon = (j > i) || (j == i && lex_positive(S1, S2, S3));
+                      exact_sep(pos, i, j, s, canon, r, d2);
+                    }
+                    if (at < cap) {
+                      b.key_tmp[at] = pair_key(j, S1, S2, S3);
+                      Vec4<T> v;
+                      v.x = (T)r[0]; v.y = (T)r[1]; v.z = (T)r[2]; v.w = (T)sqrt(d2);
+                      rout[at] = v;
+                    } else {
+                      atomicOr(b.err, SG_ERR_PAIR_CAPACITY);
+                    }
+                  }
+                  next[sp] += __popc(mask);
+                }
+              });
+}
+
+// rank sort inside each (centre, species) segment, then keys -> j and sorted vectors
+template <typename T>
+__global__ void sort_kernel(int nseg, NbrBuffers b, const Vec4<T>* rin, Vec4<T>* rout) {
+  const int seg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (seg >= nseg) return;
+  const int beg = b.seg_offs[seg], end = b.seg_offs[seg + 1];
+  for (int e = beg + lane; e < end; e += 32) {
+    const unsigned long long k = b.key_tmp[e];
+    int rank = 0;
+    for (int o = beg; o < end; ++o) rank += (__ldg(b.key_tmp + o) < k);
+    b.key[beg + rank] = k;
+    b.pair_j[beg + rank] = (int)(k >> 24);
+    rout[beg + rank] = rin[e];
+  }
+}
+
+// reverse index: pair (i, j, S) -> position of (j, i, -S) in segment (j, species(i))
+__global__ void rev_kernel(int n, int nsp, const int* __restrict__ species, NbrBuffers b) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  const int si = species[i];
+  const int beg = b.seg_offs[i * nsp], end = b.seg_offs[(i + 1) * nsp];
+  for (int p = beg + lane; p < end; p += 32) {
+    const unsigned long long k = b.key[p];
+    const int j = (int)(k >> 24);
+    const int s1 = (int)((k >> 16) & 255) - 128, s2 = (int)((k >> 8) & 255) - 128,
+              s3 = (int)(k & 255) - 128;
+    const unsigned long long want = pair_key(i, -s1, -s2, -s3);
+    int lo = b.seg_offs[j * nsp + si], hi = b.seg_offs[j * nsp + si + 1] - 1, found = -1;
+    while (lo <= hi) {
+      const int mid = (lo + hi) >> 1;
+      const unsigned long long km = b.key[mid];
+      if (km == want) { found = mid; break; }
+      if (km < want) lo = mid + 1; else hi = mid - 1;
+    }
+    if (found < 0) atomicOr(b.err, SG_ERR_NO_REVERSE);
+    b.rev[p] = found < 0 ? p : found;
+  }
+}
+
+template <typename T>
+cudaError_t sg_nbr_fill(const double* pos, const int* species, int n_atoms, int nsp, double rc,
+                        long long cap, const NbrBuffers& b, cudaStream_t st) {
+  if (n_atoms == 0) return cudaSuccess;
+  const int threads = 128;
+  const long long blocks = ((long long)n_atoms * 32 + threads - 1) / threads;
+  Vec4<T>* unsorted = reinterpret_cast<Vec4<T>*>(b.r_tmp);
+  fill_kernel<T><<<(unsigned)blocks, threads, 0, st>>>(pos, species, n_atoms, nsp, rc, cap, b,
+                                                       b.binpos, unsorted);
+  const long long nseg = (long long)n_atoms * nsp;
+  const long long sblocks = (nseg * 32 + threads - 1) / threads;
+  Vec4<T>* sorted = reinterpret_cast<Vec4<T>*>(b.pair_r);
+  sort_kernel<T><<<(unsigned)sblocks, threads, 0, st>>>((int)nseg, b, unsorted, sorted);
+  rev_kernel<<<(unsigned)blocks, threads, 0, st>>>(n_atoms, nsp, species, b);
+  return cudaGetLastError();
+}
+
+template cudaError_t sg_nbr_fill<float>(const double*, const int*, int, int, double, long long,
+                                        const NbrBuffers&, cudaStream_t);
+template cudaError_t sg_nbr_fill<double>(const double*, const int*, int, int, double, long long,
+                                         const NbrBuffers&, cudaStream_t);

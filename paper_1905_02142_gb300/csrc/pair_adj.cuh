@@ -1,0 +1,242 @@
+// Adjoint pair kernel: dE/dq -> dE/dp -> dE/dc -> dE/dr_ij for every pair, recomputing
+// the pair's radial and angular terms instead of storing dc/dr.
+//
+// Per atom (one warp):
+//   h      = dE/dp = (g - q (q.g)) / |p|                          (q = p/|p|, Sec. I)
+//   G_l    = M_l c_l with M_l[c][c] = 2 h_(c,c,l), M_l[c][c'] = sqrt(2) h_(min,max,l)
+//            (derivative of the packed power spectrum, Eq. 09)   -> dE/dc[ch][lm]
+//   recursion path: G_alpha = W^T G_n (c_n = W c_alpha, Sec. III.A)
+// Per pair (one lane), with c_nlm += b_n(r) a_lm(r_vec), a_lm = 4 pi ilexp_l(z(r)) Y_lm(r_hat):
+//   u_lm  = sum_n G[n][lm] b_n,   u'_lm = sum_n G[n][lm] b_n'(r)
+//   dE/dr_vec = r_hat sum_lm (u'_lm il_l + u_lm il_l') Y_lm
+//             + (1/r)(I - r_hat r_hat^T) sum_lm u_lm il_l grad_u P_lm
+// where P_lm is the polynomial extension of Y_lm off the sphere.  The radial derivatives
+// come from the table (Hermite derivative) or from forward-mode duals through Eq. 04.
+#pragma once
+#include "internal.h"
+#include "soapmath.cuh"
+
+template <int NC, int LC>
+__device__ __forceinline__ void table_interp_d(const float* __restrict__ tab, const TableInfo& ti,
+                                               float r, float* f, float* df) {
+  constexpr int F = NC + LC + 1;
+  float x = r * (float)(1.0 / ti.h);
+  int k = (int)x;
+  k = k < 0 ? 0 : (k >= ti.K ? ti.K - 1 : k);
+  float t = x - (float)k;
+  const float* n0 = tab + (size_t)k * 2 * ti.fp;
+  const float* n1 = n0 + 2 * ti.fp;
+  float t2 = t * t;
+  float h00 = (2.f * t - 3.f) * t2 + 1.f, h10 = ((t - 2.f) * t + 1.f) * t;
+  float h01 = (3.f - 2.f * t) * t2, h11 = (t - 1.f) * t2;
+  float d00 = 6.f * t * (t - 1.f), d10 = (3.f * t - 4.f) * t + 1.f, d11 = (3.f * t - 2.f) * t;
+  float invh = (float)(1.0 / ti.h);
+#pragma unroll
+  for (int j = 0; j < F; ++j) {
+    float v0 = __ldg(n0 + j), g0 = __ldg(n0 + ti.fp + j);
+    float v1 = __ldg(n1 + j), g1 = __ldg(n1 + ti.fp + j);
+    f[j] = h00 * v0 + h10 * g0 + h01 * v1 + h11 * g1;
+    df[j] = (d00 * (v0 - v1) + d10 * g0 + d11 * g1) * invh;
+  }
+}
+
+__device__ __forceinline__ void pair_index(int pc, int nch, int& c1, int& c2) {
+  int c = 0, rem = pc;
+  while (rem >= nch - c) { rem -= nch - c; ++c; }
+  c1 = c;
+  c2 = c + rem;
+}
+
+template <typename T, int NC, int LC, bool TABLE>
+__global__ void __launch_bounds__(SG_WARPS * 32)
+pair_adj_kernel(const AdjArgs<T> a, int smem_per_warp) {
+  constexpr int NP = (NC + 3) / 4 * 4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* base_s = reinterpret_cast<T*>(smem_raw) + (size_t)warp * smem_per_warp;
+  const int L = (a.lmax + 1) * (a.lmax + 1);
+  const int nch = a.nsp * a.nmax;
+  const int D = a.dim;
+  T* Gs = base_s;                          // [nsp][L][NP]
+  T* cs = Gs + (size_t)a.nsp * L * NP;     // [nch][L]
+  T* hs = cs + (size_t)nch * L;            // [D]
+  const T FOUR_PI = (T)12.566370614359172;
+
+  for (int atom = blockIdx.x * SG_WARPS + warp; atom < a.n_atoms; atom += gridDim.x * SG_WARPS) {
+    // ---- prologue: dE/dc in shared memory
+    const T w = (T)a.struct_w[a.atom_struct[atom]];
+    const T* qi = a.q + (size_t)atom * D;
+    const T* gi = a.g + (size_t)atom * D;
+    T dot = 0;
+    for (int k = lane; k < D; k += 32) dot += qi[k] * gi[k];
+    dot = warp_sum(dot);
+    const T inv_norm = T(1) / a.pnorm[atom];
+    for (int k = lane; k < D; k += 32) hs[k] = w * (gi[k] - qi[k] * dot) * inv_norm;
+    const T* ci = a.c + (size_t)atom * nch * L;
+    for (int k = lane; k < nch * L; k += 32) cs[k] = ci[k];
+    __syncwarp();
+    const int lp1 = a.lmax + 1;
+    const T SQRT2 = (T)1.4142135623730951;
+    for (int k = lane; k < nch * L; k += 32) {
+      const int c1 = k / L, lm = k - c1 * L;
+      int l = 0;
+      while ((l + 1) * (l + 1) <= lm) ++l;
+      T acc = 0;
+      for (int c2 = 0; c2 < nch; ++c2) {
+        const int lo = c1 < c2 ? c1 : c2, hi = c1 < c2 ? c2 : c1;
+        const int pc = lo * nch - lo * (lo - 1) / 2 + (hi - lo);
+        const T hv = hs[pc * lp1 + l];
+        const T mcoef = (c1 == c2) ? T(2) * hv : SQRT2 * hv;
+        acc += mcoef * cs[c2 * L + lm];
+      }
+      const int s = c1 / a.nmax, n = c1 - s * a.nmax;
+      Gs[((size_t)s * L + lm) * NP + n] = acc;
+    }
+    for (int k = lane; k < a.nsp * L; k += 32)
+      for (int n = a.nmax; n < NP; ++n) Gs[(size_t)k * NP + n] = T(0);
+    __syncwarp();
+    if constexpr (!TABLE) {
+      // G_alpha = W^T G_n (lane-local per (s, lm) row)
+      for (int k = lane; k < a.nsp * L; k += 32) {
+        T gn[NC];
+#pragma unroll
+        for (int n = 0; n < NC; ++n) gn[n] = (n < a.nmax) ? Gs[(size_t)k * NP + n] : T(0);
+#pragma unroll
+        for (int al = 0; al < NC; ++al) {
+          T acc = 0;
+#pragma unroll
+          for (int n = 0; n < NC; ++n) acc = fma(a.bc.W[n][al], gn[n], acc);
+          if (al < a.nmax) Gs[(size_t)k * NP + al] = acc;
+        }
+      }
+      __syncwarp();
+    }
+
+    // ---- pairs
+    T vir[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) vir[t] = 0;
+    for (int s = 0; s < a.nsp; ++s) {
+      const int beg = a.seg_offs[atom * a.nsp + s];
+      const int end = a.seg_offs[atom * a.nsp + s + 1];
+      const T* Gsp = Gs + (size_t)s * L * NP;
+      for (int pidx = beg + lane; pidx < end; pidx += 32) {
+        const Vec4<T> v = a.pair_r[pidx];
+        const T r = v.w, inv = T(1) / r;
+        const T ux = v.x * inv, uy = v.y * inv, uz = v.z * inv;
+        T bn[NC], dbn[NC], il[LC + 1], dil[LC + 1];
+        if constexpr (TABLE) {
+          float f[NC + LC + 1], df[NC + LC + 1];
+          table_interp_d<NC, LC>(a.table, a.ti, (float)r, f, df);
+#pragma unroll
+          for (int n = 0; n < NC; ++n) { bn[n] = f[n]; dbn[n] = df[n]; }
+#pragma unroll
+          for (int l = 0; l <= LC; ++l) { il[l] = f[NC + l]; dil[l] = df[NC + l]; }
+        } else {
+          using Dd = Dual<double>;
+          Dd rd((double)r, 1.0);
+          Dd ba[NC];
+          radial_alpha<Dd, NC>(rd, a.p, ba);
+          Dd spp = a.p.s0p + a.p.ap * rd;
+          Dd ild[LC + 1];
+          ilexp_all<Dd, LC>(rd * rd / (spp * spp), ild);
+#pragma unroll
+          for (int n = 0; n < NC; ++n) { bn[n] = (T)ba[n].v; dbn[n] = (T)ba[n].d; }
+#pragma unroll
+          for (int l = 0; l <= LC; ++l) {
+            const T wl = (l <= a.lmax) ? FOUR_PI * (T)(a.p.eq08 ? (2.0 * l + 1.0) : 1.0) : T(0);
+            il[l] = wl * (T)ild[l].v;
+            dil[l] = wl * (T)ild[l].d;
+          }
+        }
+        T srad = 0, hx = 0, hy = 0, hz = 0;
+        for_each_ylm_grad<T, LC>(ux, uy, uz, a.yc,
+            [&](int l, int m, T y, T gx, T gy, T gz) {
+              if (l > a.lmax) return;
+              const T* grow = Gsp + (size_t)lm_index(l, m) * NP;
+              T u0 = 0, u1 = 0;
+#pragma unroll
+              for (int n = 0; n < NC; ++n) {
+                const T gv = grow[n];
+                u0 = fma(gv, bn[n], u0);
+                u1 = fma(gv, dbn[n], u1);
+              }
+              srad = fma(fma(u1, il[l], u0 * dil[l]), y, srad);
+              const T wv = u0 * il[l];
+              hx = fma(wv, gx, hx);
+              hy = fma(wv, gy, hy);
+              hz = fma(wv, gz, hz);
+            });
+        const T hdot = hx * ux + hy * uy + hz * uz;
+        Vec4<T> o;
+        o.x = ux * srad + (hx - hdot * ux) * inv;
+        o.y = uy * srad + (hy - hdot * uy) * inv;
+        o.z = uz * srad + (hz - hdot * uz) * inv;
+        o.w = T(0);
+        a.dedr[pidx] = o;
+        const T gvec[3] = {o.x, o.y, o.z}, rvec[3] = {v.x, v.y, v.z};
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+          for (int q2 = 0; q2 < 3; ++q2) vir[3 * p + q2] -= gvec[p] * rvec[q2];
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const T vt = warp_sum(vir[t]);
+      if (lane == 0) a.vir_atom[(size_t)atom * 9 + t] = vt;
+    }
+    __syncwarp();
+  }
+}
+
+template <typename T, int NC, int LC, bool TABLE>
+static cudaError_t launch_adj(const AdjArgs<T>& a, cudaStream_t st) {
+  constexpr int NP = (NC + 3) / 4 * 4;
+  const int L = (a.lmax + 1) * (a.lmax + 1);
+  const int nch = a.nsp * a.nmax;
+  int per_warp = a.nsp * L * NP + nch * L + a.dim;
+  per_warp = (per_warp + 3) / 4 * 4;
+  const size_t smem = (size_t)SG_WARPS * per_warp * sizeof(T);
+  if (smem > 220 * 1024) return cudaErrorInvalidConfiguration;
+  auto kern = pair_adj_kernel<T, NC, LC, TABLE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SG_WARPS * 32, smem);
+  if (per_sm < 1) per_sm = 1;
+  long long need = (a.n_atoms + SG_WARPS - 1) / SG_WARPS;
+  long long grid = (long long)sms * per_sm * 4;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, SG_WARPS * 32, smem, st>>>(a, per_warp);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t sg_pair_adjoint(const AdjArgs<T>& a, int cls, bool table, cudaStream_t st) {
+  if (a.n_atoms == 0) return cudaSuccess;
+  if (table) {
+    if constexpr (sizeof(T) == 4) {
+      switch (cls) {
+        case 0: return launch_adj<T, 6, 6, true>(a, st);
+        case 1: return launch_adj<T, 8, 8, true>(a, st);
+        case 2: return launch_adj<T, 10, 10, true>(a, st);
+        default: return launch_adj<T, 12, 12, true>(a, st);
+      }
+    }
+    return cudaErrorInvalidValue;
+  }
+  if constexpr (sizeof(T) == 8) {
+    switch (cls) {
+      case 0: return launch_adj<T, 6, 6, false>(a, st);
+      case 1: return launch_adj<T, 8, 8, false>(a, st);
+      case 2: return launch_adj<T, 10, 10, false>(a, st);
+      default: return launch_adj<T, 12, 12, false>(a, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+

@@ -1,0 +1,301 @@
+"""Parity of the CUDA library (through its C ABI) with the FP64 oracle.
+
+Bars (relative, see parity_helpers):
+  neighbour pairs   bit-exact (same (i, j, S) list in canonical order)
+  FP64 path         p within 1e-11 where cond(S) allows (n_max <= 6), else within the
+                    rounding bound 50 eps sqrt(cond S); energies 1e-10; forces 1e-9
+  mixed path        p within 1e-5; energies 1e-4; forces 1e-3 RMS
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import Params, basis, gap, neighbours, soap
+
+from parity_helpers import oracle_W, rel_all, rel_rows, sparse_model
+
+pytestmark = pytest.mark.gpu
+
+MIXED = dict(p=1e-5, e=1e-4, f=1e-3)
+
+
+def fp64_p_tol(P):
+    cond = np.linalg.cond(basis.overlap_matrix(P.n_max, P.r_cut, P.sigma_r0))
+    return max(1e-11, 50 * 2.2e-16 * np.sqrt(cond))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_02142_gb300 import build
+    build.build()
+
+
+def model_for(params: dict, precision, qs=None, al=None, zeta=None):
+    from paper_1905_02142_gb300.api import SoapGap
+    m = SoapGap.from_dict(params, precision=precision)
+    if qs is not None:
+        m.set_model(qs, al, zeta)
+    return m
+
+
+def structures(batch):
+    from paper_1905_02142_gb300.api import Structures
+    return Structures.from_batch(batch)
+
+
+def params_dict(P: Params):
+    return dict(r_cut=P.r_cut, r_soft=P.r_soft, sigma_r0=P.sigma_r0, sigma_p0=P.sigma_p0,
+                alpha_r=P.alpha_r, alpha_p=P.alpha_p, amp_a=P.amp_a, n_f=P.n_f,
+                central_weight=P.central_weight, n_max=P.n_max, l_max=P.l_max,
+                n_species=P.n_species, eq08_weight=P.eq08_weight)
+
+
+def oracle_pairs(batch, r_cut, centers=None):
+    pr = neighbours.batch_pairs(batch, r_cut, centers=centers)
+    return pr["i"], pr["j"], pr["shift"]
+
+
+# ------------------------------------------------------------------ neighbours
+SMALL_BATCH = synth.batched_boxes(10, n_lo=4, n_hi=150, seed=77)
+
+
+@pytest.mark.parametrize("case", ["box64_n6l6", "box1000_n8l8", "twospecies4096_n8l8", "batch",
+                                  "triclinic_small"])
+def test_pair_list_bit_exact(case):
+    if case == "batch":
+        batch, P = SMALL_BATCH, Params(r_cut=4.5, r_soft=4.0, sigma_r0=0.5, sigma_p0=0.5)
+    elif case == "triclinic_small":
+        batch = synth.concat([synth.random_box(7, side=3.1, dmin=1.0, seed=5, shear=0.35,
+                                               species_probs=(0.5, 0.5))])
+        P = Params(r_cut=5.0, r_soft=4.5, sigma_r0=0.5, sigma_p0=0.5, n_species=2)
+    else:
+        w = synth.get_workload(case)
+        batch, P = w.structures(), Params.from_dict(w.params())
+    m = model_for(params_dict(P), "mixed")
+    m.compute(structures(batch), desc=True)
+    gi, gj, gs = m.pairs()
+    oi, oj, os_ = oracle_pairs(batch, P.r_cut)
+    assert len(gi) == len(oi)
+    assert np.array_equal(gi, oi) and np.array_equal(gj, oj) and np.array_equal(gs, os_)
+
+
+def test_pair_list_bit_exact_100k_sampled():
+    w = synth.get_workload("box100k_n10l10")
+    batch = w.structures()
+    m = model_for(w.params(), "mixed")
+    m.compute(structures(batch), desc=True)
+    gi, gj, gs = m.pairs()
+    centers = np.sort(np.random.default_rng(0).choice(batch.n_atoms, 24, replace=False))
+    oi, oj, os_ = oracle_pairs(batch, w.r_cut, centers=centers)
+    sel = np.isin(gi, centers)
+    assert np.array_equal(gi[sel], oi) and np.array_equal(gj[sel], oj) and np.array_equal(gs[sel], os_)
+    # every pair has its reverse (symmetry) and the count matches the density estimate
+    assert len(gi) == pytest.approx(batch.n_atoms * 0.15 * 4 / 3 * np.pi * 125, rel=0.05)
+
+
+# ------------------------------------------------------------------ descriptors
+@pytest.mark.parametrize("name,precision", [("box64_n6l6", "fp64"), ("box64_n6l6", "mixed"),
+                                            ("box1000_n8l8", "fp64"), ("box1000_n8l8", "mixed")])
+def test_descriptors(name, precision):
+    w = synth.get_workload(name)
+    batch, P = w.structures(), Params.from_dict(w.params())
+    m = model_for(w.params(), precision)
+    out = m.compute(structures(batch), desc=True)
+    q = out["q"].double().cpu().numpy()
+    pn = out["pnorm"].double().cpu().numpy()
+    centers = None if batch.n_atoms <= 1000 else np.arange(0, batch.n_atoms, 7)
+    ref = soap.descriptors(batch, P, centers=centers, W=oracle_W(P.n_max, P.r_cut, P.sigma_r0))
+    c = ref["centers"]
+    p_gpu = q[c] * pn[c][:, None]
+    p_ref = (ref["q"] * ref["pnorm"][:, None]).numpy()
+    err = rel_rows(p_gpu, p_ref)
+    tol = fp64_p_tol(P) if precision == "fp64" else MIXED["p"]
+    print(f"{name} {precision}: max rel err of p = {err:.3e} (tol {tol:.1e})")
+    assert err < tol
+
+
+# ------------------------------------------------------------------ energies and forces
+def check_energy_forces(batch, name, precision, m_sparse=None, atoms_for_forces=None, virial=True):
+    P, qs, al, zeta = sparse_model(name, m_sparse)
+    model = model_for(params_dict(P), precision, qs, al, zeta)
+    out = model.compute(structures(batch), energy=True, forces=True, virial=virial)
+    e_atom = out["e_atom"].double().cpu().numpy()
+    e_struct = out["e_struct"].cpu().numpy()
+    f = out["forces"].cpu().numpy()
+    W = oracle_W(P.n_max, P.r_cut, P.sigma_r0)
+    tol = MIXED if precision == "mixed" else dict(e=1e-10, f=1e-9)
+    if atoms_for_forces is None:
+        ref = gap.evaluate(batch, P, qs, al, zeta, W=W, virial=virial)
+        e_err = rel_all(e_atom[None], ref["e_atom"][None])
+        es_err = float(np.max(np.abs(e_struct - ref["e_struct"]) / np.abs(ref["e_struct"])))
+        f_err = rel_all(f, ref["forces"])
+        v_err = rel_all(out["virial"].cpu().numpy().reshape(-1, 9),
+                        ref["virial"].reshape(-1, 9)) if virial else 0.0
+    else:
+        fr, atoms = gap.forces_at(batch, P, qs, al, zeta, atoms_for_forces, W=W)
+        d = soap.descriptors(batch, P, centers=atoms, W=W)
+        eps = gap.local_energies(d["q"], torch.as_tensor(qs), torch.as_tensor(al), zeta).numpy()
+        e_err = rel_all(e_atom[atoms][None], eps[None])
+        es_err = 0.0
+        f_err = rel_all(f[atoms], fr)
+        v_err = 0.0
+    print(f"{name} {precision}: eps {e_err:.2e} E {es_err:.2e} F {f_err:.2e} W {v_err:.2e}")
+    assert e_err < tol["e"] and es_err < tol["e"]
+    assert f_err < tol["f"] and v_err < tol["f"]
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_energy_forces_box64(precision):
+    w = synth.get_workload("box64_n6l6")
+    check_energy_forces(w.structures(), "box64_n6l6", precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_energy_forces_box1000(precision):
+    w = synth.get_workload("box1000_n8l8")
+    check_energy_forces(w.structures(), "box1000_n8l8", precision, m_sparse=100)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_energy_forces_small_batch(precision):
+    check_energy_forces(SMALL_BATCH, "batch256_n8l8", precision, m_sparse=64)
+
+
+def test_energy_forces_two_species_sampled():
+    w = synth.get_workload("twospecies4096_n8l8")
+    atoms = np.random.default_rng(1).choice(4096, 6, replace=False)
+    check_energy_forces(w.structures(), "twospecies4096_n8l8", "mixed", m_sparse=300,
+                        atoms_for_forces=atoms, virial=False)
+
+
+def test_energy_forces_100k_sampled_full_model():
+    w = synth.get_workload("box100k_n10l10")
+    atoms = np.random.default_rng(2).choice(w.n_atoms, 4, replace=False)
+    check_energy_forces(w.structures(), "box100k_n10l10", "mixed", atoms_for_forces=atoms,
+                        virial=False)
+
+
+# ------------------------------------------------------------------ hyperparameter variants
+def hp_variants(golden):
+    hs = golden["hyperparameter_sets"]
+    out = []
+    for key in ("optimised_adsorption_informed", "sobol_optimum", "fair_comparison"):
+        h = hs[key]
+        out.append(Params(r_cut=h["r_cut"], r_soft=h["r_cut"] - 0.5, sigma_r0=h["sigma_r0"],
+                          sigma_p0=h["sigma_p0"], alpha_r=h["alpha_r"], alpha_p=h["alpha_p"],
+                          amp_a=h["amp_a"], n_max=h["n_max"], l_max=h["l_max"]))
+    out.append(Params(r_cut=4.0, r_soft=4.0, sigma_r0=0.5, sigma_p0=0.5, n_max=2, l_max=0))
+    out.append(Params(r_cut=4.0, r_soft=3.0, sigma_r0=0.4, sigma_p0=0.6, n_max=5, l_max=11,
+                      eq08_weight=True, central_weight=0.0))
+    return out
+
+
+@pytest.mark.parametrize("k", range(5))
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_hyperparameter_variants(golden, k, precision):
+    P = hp_variants(golden)[k]
+    batch = synth.concat([synth.random_box(40, side=7.5, dmin=1.0, seed=40 + k)])
+    W = oracle_W(P.n_max, P.r_cut, P.sigma_r0)
+    qs = soap.descriptors(synth.concat([synth.random_box(12, side=5.0, dmin=1.0, seed=90 + k)]),
+                          P, W=W)["q"].numpy()
+    al = synth.gap_weights(len(qs), 5 + k)
+    zeta = 3.0 if k < 2 else 2.0
+    model = model_for(params_dict(P), precision, qs, al, zeta)
+    out = model.compute(structures(batch), desc=True, energy=True, forces=True)
+    ref_d = soap.descriptors(batch, P, W=W)
+    ref = gap.evaluate(batch, P, qs, al, zeta, W=W, virial=False)
+    p_gpu = out["q"].double().cpu().numpy() * out["pnorm"].double().cpu().numpy()[:, None]
+    p_err = rel_rows(p_gpu, (ref_d["q"] * ref_d["pnorm"][:, None]).numpy())
+    e_err = rel_all(out["e_atom"].double().cpu().numpy()[None], ref["e_atom"][None])
+    f_err = rel_all(out["forces"].cpu().numpy(), ref["forces"])
+    print(f"HP set {k} {precision}: p {p_err:.2e} eps {e_err:.2e} F {f_err:.2e}")
+    if precision == "mixed":
+        assert p_err < MIXED["p"] and e_err < MIXED["e"] and f_err < MIXED["f"]
+    else:
+        assert p_err < fp64_p_tol(P) and e_err < 1e-9 and f_err < 1e-8
+
+
+# ------------------------------------------------------------------ API paths and edges
+def test_autograd_function_matches_forces():
+    from paper_1905_02142_gb300.api import SoapGapEnergy
+    P, qs, al, zeta = sparse_model("box64_n6l6")
+    batch = SMALL_BATCH
+    model = model_for(params_dict(P), "fp64", qs, al, zeta)
+    s = structures(batch)
+    out = model.compute(s, energy=True, forces=True)
+    pos = s.pos.clone().requires_grad_(True)
+    w = torch.linspace(0.5, 2.0, s.n_struct, dtype=torch.float64, device=pos.device)
+    e = SoapGapEnergy.apply(pos, model, s)
+    (e * w).sum().backward()
+    atom_w = torch.repeat_interleave(w, torch.as_tensor(np.diff(batch.atom_offs), device=pos.device))
+    assert torch.allclose(pos.grad, -out["forces"] * atom_w[:, None], rtol=1e-10, atol=1e-12)
+    assert torch.allclose(e, out["e_struct"], rtol=1e-12)
+
+
+def test_backward_matches_central_differences_fp64():
+    P, qs, al, zeta = sparse_model("box64_n6l6")
+    batch = synth.concat([synth.random_box(20, side=5.5, dmin=1.2, seed=21, shear=0.1)])
+    model = model_for(params_dict(P), "fp64", qs, al, zeta)
+    s = structures(batch)
+    out = model.compute(s, energy=True, forces=True)
+    f = out["forces"].cpu().numpy()
+    h = 1e-5
+    for atom, comp in [(0, 0), (5, 2), (13, 1)]:
+        vals = []
+        for sgn in (1, -1):
+            pos = batch.pos.copy()
+            pos[atom, comp] += sgn * h
+            b2 = synth.Batch(pos, batch.cell, batch.species, batch.atom_offs)
+            vals.append(float(model.compute(structures(b2), energy=True)["e_struct"].sum()))
+        fd = -(vals[0] - vals[1]) / (2 * h)
+        assert f[atom, comp] == pytest.approx(fd, rel=1e-5, abs=1e-8)
+
+
+def test_compute_host_matches_device():
+    P, qs, al, zeta = sparse_model("box64_n6l6")
+    batch = SMALL_BATCH
+    model = model_for(params_dict(P), "mixed", qs, al, zeta)
+    dev = model.compute(structures(batch), desc=True, energy=True, forces=True, virial=True)
+    host = model.compute_host(batch.pos, batch.cell, batch.species, batch.atom_offs, desc=True,
+                              energy=True, forces=True, virial=True)
+    for k in ("q", "e_struct", "forces", "virial"):
+        assert np.array_equal(dev[k].cpu().numpy(), host[k]), k
+
+
+def test_empty_structures_and_isolated_atoms():
+    P, qs, al, zeta = sparse_model("box64_n6l6")
+    lone = synth.Structure(pos=np.array([[5.0, 5.0, 5.0]]), cell=np.eye(3) * 20.0,
+                           species=np.zeros(1, np.int32))
+    empty = synth.Structure(pos=np.zeros((0, 3)), cell=np.eye(3) * 9.0, species=np.zeros(0, np.int32))
+    box = synth.random_box(16, side=5.0, dmin=1.2, seed=3)
+    batch = synth.concat([empty, lone, box, empty])
+    model = model_for(params_dict(P), "fp64", qs, al, zeta)
+    out = model.compute(structures(batch), desc=True, energy=True, forces=True, virial=True)
+    ref = gap.evaluate(batch, P, qs, al, zeta, W=oracle_W(P.n_max, P.r_cut, P.sigma_r0))
+    assert np.allclose(out["e_struct"].cpu().numpy(), ref["e_struct"], rtol=1e-10, atol=1e-14)
+    assert np.allclose(out["forces"].cpu().numpy(), ref["forces"], rtol=1e-8, atol=1e-12)
+    assert float(out["e_struct"][0]) == 0.0 and float(out["e_struct"][3]) == 0.0
+    assert np.all(out["forces"][0].cpu().numpy() == 0.0)
+
+
+def test_invalid_inputs_are_reported():
+    from paper_1905_02142_gb300.api import SoapGapError
+    P, qs, al, zeta = sparse_model("box64_n6l6")
+    model = model_for(params_dict(P), "mixed", qs, al, zeta)
+    outside = synth.Structure(pos=np.array([[1.0, 1.0, 1.0], [9.5, 1.0, 1.0]]), cell=np.eye(3) * 8.0,
+                              species=np.zeros(2, np.int32))
+    with pytest.raises(SoapGapError) as e:
+        model.compute(structures(synth.concat([outside])), desc=True)
+    assert "outside" in str(e.value)
+    same = synth.Structure(pos=np.array([[1.0, 1.0, 1.0], [1.0, 1.0, 1.0]]), cell=np.eye(3) * 8.0,
+                           species=np.zeros(2, np.int32))
+    with pytest.raises(SoapGapError) as e:
+        model.compute(structures(synth.concat([same])), desc=True)
+    assert "coincide" in str(e.value)
+    # the handle stays usable after an error
+    ok = model.compute(structures(synth.concat([synth.random_box(8, side=5.0, seed=1)])), energy=True)
+    assert torch.isfinite(ok["e_struct"]).all()

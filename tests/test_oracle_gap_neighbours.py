@@ -125,3 +125,21 @@ def test_neighbour_list_symmetric_and_canonical():
     assert np.array_equal(order, np.arange(len(i)))
     d2 = (r[:, 0] * r[:, 0] + r[:, 1] * r[:, 1]) + r[:, 2] * r[:, 2]
     assert d2.max() < 4.2 ** 2 and d2.min() > 0
+
+
+def test_forces_with_self_images_on_the_axes(model):
+    # a cubic cell smaller than r_cut puts periodic self-images exactly on the z axis (the
+    # pole of the spherical harmonics); forces must stay finite and match differences
+    P, qs, al, _ = model
+    s = synth.random_box(3, side=3.2, dmin=1.0, seed=9)
+    b = synth.concat([s])
+    r = gap.evaluate(b, P, qs, al, 2.0)
+    assert np.all(np.isfinite(r["forces"])) and np.all(np.isfinite(r["virial"]))
+    h = 1e-5
+    for atom, comp in [(0, 2), (1, 0)]:
+        vals = []
+        for sgn in (1, -1):
+            pos = b.pos.copy()
+            pos[atom, comp] += sgn * h
+            vals.append(energy(synth.Batch(pos, b.cell, b.species, b.atom_offs), P, qs, al, 2.0))
+        assert r["forces"][atom, comp] == pytest.approx(-(vals[0] - vals[1]) / (2 * h), rel=1e-6, abs=1e-9)
