@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Throughput benchmark: SOAP descriptors + GAP energies, forces and virial (atoms/s).
+
+Default workload: the 100,000-atom periodic box at 0.15 atoms/A^3 (r_cut 5 A, n_max =
+l_max = 10, 4000 sparse environments, zeta 4), one full evaluation per step (neighbour
+list -> descriptors -> energies -> forces and virial), mixed precision.  The FP64 path is
+timed on the same workload beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank evaluates its own copy of the workload (independent problems,
+no collective on the data path: weak scaling); rank 0 prints one JSON line.
+The reference arm (--impl reference) times the FP64 CPU oracle on bounded samples.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "atoms/s for SOAP+GAP energy+forces, mixed vs FP64 GPU path at stated err"
+STATED_ERR = {"p_rel": 1e-5, "energy_rel": 1e-4, "forces_rms_rel": 1e-3,
+              "fp64_p_rel": "1e-11 at n_max<=6; 50 eps sqrt(cond S) above"}
+FP32_PEAK_NOTE = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x SM clock"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="box100k_n10l10")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[4:]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k, v in enumerate(r[3][1:5])
+                          if v.lower() == "active"})
+        busy = [r[0] for r in rows if r[2] > 200.0] or [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+# --------------------------------------------------------------------------- model set-up
+def sparse_set_from_library(model_cls, w, params, device):
+    """Sparse-set descriptors of the workload's separate box, computed by the library."""
+    from paper_1905_02142_gb300.api import Structures
+    sb = w.sparse_box()
+    m = model_cls.from_dict(params, precision="fp64")
+    q = m.compute(Structures.from_batch(sb, device=device), desc=True)["q"].cpu().numpy()
+    m.close()
+    idx = synth.sparse_indices(sb.n_atoms, w.n_sparse, w.sparse_seed)
+    return q[idx], synth.gap_weights(w.n_sparse, w.alpha_seed)
+
+
+def flush_l2(buf):
+    buf.add_(1.0)  # writes (and reads) a buffer larger than the 129 MB L2
+
+
+def algorithmic_flops(stage, n_pairs, n_atoms, w):
+    """Algorithmic FLOPs per launch of a stage (definitions stated in the design doc)."""
+    L = (w.l_max + 1) ** 2
+    n = w.n_max
+    if stage == "pair_forward":
+        return 2.0 * n * L * n_pairs            # c[n][lm] += b_n a_lm
+    if stage == "pair_adjoint":
+        return 4.0 * n * L * n_pairs            # u_lm = G b, u'_lm = G b'
+    if stage in ("gap_forward", "gap_backward"):
+        d = (n * w.n_species) * (n * w.n_species + 1) // 2 * (w.l_max + 1)
+        return 2.0 * n_atoms * w.n_sparse * d
+    return None
+
+
+# --------------------------------------------------------------------------- arms
+def oracle_sample_rate(w, n_sample_atoms: int, seed: int = 11):
+    """FP64 oracle on a bounded sample: a box of n_sample_atoms with the workload's recipe
+    (density, minimum distance, hyperparameters, sparse-set size, zeta); energies, forces
+    and virial through the oracle as it stands.  Returns (atoms/s, seconds, threads)."""
+    import torch
+
+    from oracle import Params, gap
+    P = Params.from_dict(w.params())
+    dens = w.density if w.density else 0.13
+    b = synth.concat([synth.random_box(n_sample_atoms, density=dens, dmin=w.dmin, seed=seed,
+                                       species_probs=w.species_probs)])
+    rng = np.random.default_rng(seed)
+    qs = np.abs(rng.normal(size=(w.n_sparse, P.dim)))
+    qs /= np.linalg.norm(qs, axis=1, keepdims=True)
+    al = synth.gap_weights(w.n_sparse, w.alpha_seed)
+    t0 = time.perf_counter()
+    gap.evaluate(b, P, qs, al, w.zeta)
+    dt = time.perf_counter() - t0
+    return n_sample_atoms / dt, dt, torch.get_num_threads()
+
+
+def run_reference(args, rank, world):
+    w = synth.get_workload(args.workload)
+    if rank != 0:
+        return
+    n_sample = 64
+    rates = []
+    for k in range(args.warmup + args.steps):
+        r, dt, threads = oracle_sample_rate(w, n_sample, seed=100 + k)
+        if k >= args.warmup:
+            rates.append((r, dt))
+    total_atoms = n_sample * len(rates)
+    total_t = sum(dt for _, dt in rates)
+    value = total_atoms / total_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "atoms/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_t / len(rates), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "description": w.description,
+                   "sample": f"{n_sample}-atom box of the same recipe per step"},
+        "cpu_baseline": {"value": value, "unit": "atoms/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{n_sample}-atom box of the workload recipe, per step"},
+        "e2e": {"value": value, "unit": "atoms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1905_02142_gb300.api import SoapGap, Structures
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = synth.get_workload(args.workload)
+    params = w.params()
+    batch = w.structures()
+    s = Structures.from_batch(batch, device=dev)
+    qs, al = sparse_set_from_library(SoapGap, w, params, dev)
+    model = SoapGap.from_dict(params, precision="mixed")
+    model.set_model(qs, al, w.zeta)
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return model.compute(s, energy=True, forces=True, virial=True, timing=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stage_acc = {}
+    launches = 0
+    times = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for _ in range(args.steps):
+            flush_l2(flush)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            for k, v in model.stage_times().items():
+                stage_acc[k] = stage_acc.get(k, 0.0) + v
+            launches += model.launch_count()
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = clk.summary()
+    t_sum = sum(times) / 1e3
+    t_local = torch.tensor([t_sum], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    t_max = float(t_local)
+    n_pairs = model.pair_count()
+    stages = {k: v / args.steps for k, v in stage_acc.items()}
+
+    # e2e: host buffers through the C ABI, copies inside the timed region
+    pos_h = np.ascontiguousarray(batch.pos)
+    e2e_times = []
+    for k in range(args.warmup + max(2, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        model.compute_host(pos_h, batch.cell, batch.species, batch.atom_offs, energy=True,
+                           forces=True, virial=True)
+        if k >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_t = float(np.mean(e2e_times))
+    n = batch.n_atoms
+    h2d = n * (3 * 8 + 4)
+    d2h = n * 4 + batch.n_struct * 8 + n * 24 + batch.n_struct * 72
+
+    # FP64 path on the same workload
+    fp64 = None
+    if args.fp64_steps > 0:
+        m64 = SoapGap.from_dict(params, precision="fp64")
+        m64.set_model(qs, al, w.zeta)
+        m64.compute(s, energy=True, forces=True, virial=True)
+        torch.cuda.synchronize()
+        t64 = []
+        for _ in range(args.fp64_steps):
+            flush_l2(flush)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            m64.compute(s, energy=True, forces=True, virial=True, timing=True)
+            e1.record(stream)
+            e1.synchronize()
+            t64.append(e0.elapsed_time(e1))
+        fp64 = {"value": n * len(t64) / (sum(t64) / 1e3), "unit": "atoms/s",
+                "ms_per_step": float(np.mean(t64)), "steps": len(t64),
+                "stages_ms": {k: round(v, 4) for k, v in m64.stage_times().items()}}
+        m64.close()
+
+    if rank != 0:
+        return
+    # roofline of the dominant stage
+    dom = max((k for k in stages if algorithmic_flops(k, n_pairs, n, w) is not None),
+              key=lambda k: stages[k])
+    flops = algorithmic_flops(dom, n_pairs, n, w)
+    sm_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = flops / (stages[dom] / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": FP32_PEAK_NOTE + f" ({sm_mhz:.0f} MHz)",
+                "flops_per_launch": flops}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, dt, threads = oracle_sample_rate(w, 128)
+        cpu = {"value": rate, "unit": "atoms/s", "cores": threads, "kind": "oracle",
+               "sample": f"128-atom box of the workload recipe, energies+forces+virial, {dt:.1f} s"}
+    line = {
+        "metric": METRIC, "value": world * n / t_max * args.steps, "unit": "atoms/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "description": w.description, "atoms": n,
+                   "pairs": n_pairs, "sparse": w.n_sparse, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "stated_err": STATED_ERR,
+        "stages_ms": {k: round(v, 4) for k, v in stages.items()},
+        "fp64_path": fp64,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": n / e2e_t, "unit": "atoms/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_1905_02142_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

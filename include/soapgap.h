@@ -66,6 +66,11 @@ extern "C" {
 #define SOAPGAP_ENERGY 2u /* write e_atom and e_struct (needs a model)  */
 #define SOAPGAP_FORCES 4u /* write forces (needs a model)               */
 #define SOAPGAP_VIRIAL 8u /* write virial (needs a model)               */
+#define SOAPGAP_TIMING 16u /* record per-stage device times (soapgap_stage_times) */
+
+/* Stages reported by soapgap_stage_times, in this order. */
+#define SOAPGAP_N_STAGES 7 /* neighbours, pair_forward, power_spectrum, gap_forward,
+                              gap_backward, pair_adjoint, finish */
 
 /* Limits: 2 <= n_max <= 12 (the basis degenerates beyond 12, Sec. III.A),
  * 0 <= l_max <= 12, 1 <= n_species <= 8. */
@@ -155,6 +160,14 @@ int soapgap_backward(soapgap_handle* h, const soapgap_batch* batch, const double
 int soapgap_compute_host(soapgap_handle* h, const soapgap_batch* batch, uint32_t flags,
                          void* q, void* pnorm, void* e_atom, double* e_struct, double* forces,
                          double* virial, void* stream);
+
+/* Device time in milliseconds of each stage of the last soapgap_compute call made with
+ * SOAPGAP_TIMING (CUDA events recorded on the caller's stream): ms[SOAPGAP_N_STAGES] host
+ * double; stages that did not run report 0.  SOAPGAP_E_STATE if timing was not on. */
+int soapgap_stage_times(const soapgap_handle* h, double* ms);
+
+/* Number of kernels the last soapgap_compute / soapgap_backward call launched. */
+int soapgap_last_launch_count(const soapgap_handle* h, int64_t* n);
 
 /* Number of neighbour pairs found by the last compute call (diagnostics). */
 int soapgap_last_pair_count(const soapgap_handle* h, int64_t* n_pairs);

@@ -21,6 +21,10 @@ DESC = 1
 ENERGY = 2
 FORCES = 4
 VIRIAL = 8
+TIMING = 16
+N_STAGES = 7
+STAGES = ("neighbours", "pair_forward", "power_spectrum", "gap_forward", "gap_backward",
+          "pair_adjoint", "finish")
 
 # every entry point the header declares: (name, restype, argtypes)
 c_void_p, c_int32, c_int64, c_double, c_uint32 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
@@ -52,6 +56,8 @@ SIGNATURES = {
     "soapgap_compute_host": (ctypes.c_int, [c_void_p, ctypes.POINTER(Batch), c_uint32, c_void_p,
                                             c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                             c_void_p]),
+    "soapgap_stage_times": (ctypes.c_int, [c_void_p, c_void_p]),
+    "soapgap_last_launch_count": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_int64)]),
     "soapgap_last_pair_count": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_int64)]),
     "soapgap_export_pairs": (ctypes.c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
     "soapgap_last_error": (ctypes.c_char_p, [c_void_p]),

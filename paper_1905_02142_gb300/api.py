@@ -116,12 +116,12 @@ class SoapGap:
         self.m = qs.shape[0]
 
     def compute(self, s: Structures, *, desc=False, energy=False, forces=False, virial=False,
-                stream=None):
+                timing=False, stream=None):
         """Run one evaluation; returns a dict of CUDA tensors for the requested outputs."""
         dev = s.pos.device
         n, ns = s.n_atoms, s.n_struct
         flags = (L.DESC if desc else 0) | (L.ENERGY if energy else 0) | \
-            (L.FORCES if forces else 0) | (L.VIRIAL if virial else 0)
+            (L.FORCES if forces else 0) | (L.VIRIAL if virial else 0) | (L.TIMING if timing else 0)
         out = {}
         if desc:
             out["q"] = torch.empty((n, self.dim), dtype=self.dtype, device=dev)
@@ -183,6 +183,18 @@ class SoapGap:
             _ptr(out.get("e_atom")), _ptr(out.get("e_struct")), _ptr(out.get("forces")),
             _ptr(out.get("virial")), st))
         return out
+
+    def stage_times(self) -> dict:
+        """Device milliseconds per stage of the last compute(timing=True) call."""
+        ms = np.zeros(L.N_STAGES)
+        self._check(self.lib.soapgap_stage_times(self.h, ms.ctypes.data))
+        return dict(zip(L.STAGES, ms.tolist()))
+
+    def launch_count(self) -> int:
+        """Kernels launched by the last compute/backward call."""
+        n = ctypes.c_int64()
+        self._check(self.lib.soapgap_last_launch_count(self.h, ctypes.byref(n)))
+        return int(n.value)
 
     def pair_count(self) -> int:
         n = ctypes.c_int64()

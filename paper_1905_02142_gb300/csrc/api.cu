@@ -13,6 +13,8 @@
 #include "soapmath.cuh"
 
 // --------------------------------------------------------------------- helpers
+long long sg_kernel_launches = 0;
+
 int sg_cap_class(int nmax, int lmax) {
   int m = nmax > lmax ? nmax : lmax;
   return m <= 6 ? 0 : (m <= 8 ? 1 : (m <= 10 ? 2 : 3));
@@ -102,7 +104,20 @@ struct soapgap_handle {
   int fw_atoms = -1, fw_struct = -1;
   bool have_forward = false;
   int n_bins = 0;
+  // stage timing: events recorded around the stages of one call on the caller's stream
+  cudaEvent_t ev[10] = {};
+  bool ev_made = false, timed = false;
+  bool stage_ran[SOAPGAP_N_STAGES] = {};
+  long long launches = 0;
 };
+
+// event slots: 0/1 neighbour search before the size read-back, 2/3 the fill after it,
+// then 3..9 bound the stages pair_forward .. finish
+enum { EV_NB0 = 0, EV_NB1, EV_FILL0, EV_FWD0, EV_PS0, EV_GF0, EV_GB0, EV_ADJ0, EV_FIN0, EV_END };
+
+static void mark(soapgap_handle* h, int slot, cudaStream_t st) {
+  if (h->timed) cudaEventRecord(h->ev[slot], st);
+}
 
 static int fail(soapgap_handle* h, int code, const std::string& m) {
   if (h) h->msg = m;
@@ -327,6 +342,7 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
   const bool want_grad = backward || (flags & (SOAPGAP_FORCES | SOAPGAP_VIRIAL)) != 0;
   const size_t es = sizeof(T);
   NbrBuffers nb{};
+  const long long launches0 = sg_kernel_launches;
   if (!backward) {
     int rc = setup_geometry(h, b);
     if (rc != SOAPGAP_OK) return rc;
@@ -347,7 +363,9 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     CK(h, cudaMemcpyAsync(h->atom_offs.p, b->atom_offs_host, sizeof(int64_t) * (size_t)(S + 1),
                           cudaMemcpyHostToDevice, st));
     CK(h, cudaMemsetAsync(h->err.p, 0, sizeof(int), st));
+    mark(h, EV_NB0, st);
     atom_struct_kernel<<<S, 128, 0, st>>>((const int64_t*)h->atom_offs.p, S, (int*)h->atom_struct.p);
+    ++sg_kernel_launches;
   }
   nb.geom = (const StructGeom*)h->geom.p;
   nb.atom_struct = (const int*)h->atom_struct.p;
@@ -364,6 +382,7 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
   if (!backward) {
     CK(h, sg_nbr_bin(b->pos, N, h->n_bins, nb, st));
     CK(h, sg_nbr_count(b->pos, b->species, N, nsp, h->prm.r_cut, nb, st));
+    mark(h, EV_NB1, st);
     CK(h, cudaMemcpyAsync(h->h_count, (int*)h->seg_offs.p + N * nsp, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(h, cudaMemcpyAsync(h->h_err, h->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(h, cudaStreamSynchronize(st));
@@ -390,7 +409,10 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
   CK(h, ensure(h->q, es * N1 * D));
   CK(h, ensure(h->pnorm, es * N1));
   if (!backward) {
+    mark(h, EV_FILL0, st);
     CK(h, sg_nbr_fill<T>(b->pos, b->species, N, nsp, h->prm.r_cut, P, nb, st));
+    mark(h, EV_FWD0, st);
+    h->stage_ran[0] = h->stage_ran[1] = h->stage_ran[2] = true;
     FwdArgs<T> fa{};
     fa.n_atoms = N; fa.nsp = nsp; fa.nmax = h->prm.n_max; fa.lmax = h->prm.l_max;
     fa.species = b->species; fa.seg_offs = nb.seg_offs; fa.pair_r = (const Vec4<T>*)h->pair_r.p;
@@ -399,6 +421,7 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     else { fa.yc = h->yc64; fa.bc = h->bc64; }
     fa.c = (T*)h->c.p;
     CK(h, sg_pair_forward<T>(fa, h->cls, h->mixed, st));
+    mark(h, EV_PS0, st);
     CK(h, sg_power_spectrum<T>((const T*)h->c.p, N, nch, h->prm.l_max, (T*)h->q.p, (T*)h->pnorm.p, st));
     if ((flags & SOAPGAP_DESC) && q_out)
       CK(h, cudaMemcpyAsync(q_out, h->q.p, es * (size_t)N * D, cudaMemcpyDeviceToDevice, st));
@@ -417,14 +440,19 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
       CK(h, ensure(h->dedr, sizeof(Vec4<T>) * Pc));
       CK(h, ensure(h->struct_w, sizeof(double) * (size_t)S));
     }
+    mark(h, EV_GF0, st);
+    h->stage_ran[3] = true;
     CK(h, sg_gap_forward_simt<T>((const T*)h->q.p, (const T*)h->qs.p, (const T*)h->alpha.p, N, M, D,
                                  h->zeta, (T*)h->eps_part.p, tiles, want_grad ? (T*)h->kp.p : nullptr, st));
+    mark(h, EV_GB0, st);
     if (want_grad) {
+      h->stage_ran[4] = h->stage_ran[5] = true;
       CK(h, sg_gap_backward_simt<T>((const T*)h->kp.p, (const T*)h->qs.p, N, M, D, (T*)h->g.p, st));
       if (struct_w_user) {
         CK(h, cudaMemcpyAsync(h->struct_w.p, struct_w_user, sizeof(double) * S, cudaMemcpyDeviceToDevice, st));
       } else {
         fill_ones<<<(S + 255) / 256, 256, 0, st>>>((double*)h->struct_w.p, S);
+        ++sg_kernel_launches;
       }
       AdjArgs<T> aa{};
       aa.n_atoms = N; aa.nsp = nsp; aa.nmax = h->prm.n_max; aa.lmax = h->prm.l_max; aa.dim = D;
@@ -436,11 +464,14 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
       else { aa.yc = h->yc64; aa.bc = h->bc64; }
       aa.c = (const T*)h->c.p; aa.q = (const T*)h->q.p; aa.pnorm = (const T*)h->pnorm.p;
       aa.g = (const T*)h->g.p; aa.dedr = (Vec4<T>*)h->dedr.p; aa.vir_atom = (T*)h->vir_atom.p;
+      mark(h, EV_ADJ0, st);
       cudaError_t e = sg_pair_adjoint<T>(aa, h->cls, h->mixed, st);
       if (e == cudaErrorInvalidConfiguration)
         return fail(h, SOAPGAP_E_UNSUPPORTED, "descriptor too large for the adjoint kernel's shared memory");
       CK(h, e);
     }
+    mark(h, EV_FIN0, st);
+    h->stage_ran[6] = true;
     double* f_out = backward ? grad_pos : ((flags & SOAPGAP_FORCES) ? forces : nullptr);
     double* v_out = (backward || (flags & SOAPGAP_VIRIAL)) ? virial : nullptr;
     double* es_out = backward ? nullptr : e_struct;
@@ -451,8 +482,10 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     if (!backward && e_atom_out)
       CK(h, cudaMemcpyAsync(e_atom_out, h->e_atom.p, es * (size_t)N, cudaMemcpyDeviceToDevice, st));
   }
+  mark(h, EV_END, st);
   CK(h, cudaMemcpyAsync(h->h_err, h->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(h, cudaStreamSynchronize(st));
+  h->launches = sg_kernel_launches - launches0;
   if (*h->h_err) return fail(h, SOAPGAP_E_INVALID_ARG, device_error_text(*h->h_err));
   if (!backward) {
     h->have_forward = want_energy;
@@ -482,8 +515,14 @@ extern "C" int soapgap_compute(soapgap_handle* h, const soapgap_batch* batch, ui
   if (!h) return SOAPGAP_E_INVALID_ARG;
   int rc = check_batch(h, batch);
   if (rc != SOAPGAP_OK) return rc;
-  if (flags & ~(SOAPGAP_DESC | SOAPGAP_ENERGY | SOAPGAP_FORCES | SOAPGAP_VIRIAL))
+  if (flags & ~(SOAPGAP_DESC | SOAPGAP_ENERGY | SOAPGAP_FORCES | SOAPGAP_VIRIAL | SOAPGAP_TIMING))
     return fail(h, SOAPGAP_E_INVALID_ARG, "unknown flag bits");
+  h->timed = (flags & SOAPGAP_TIMING) != 0;
+  for (int k = 0; k < SOAPGAP_N_STAGES; ++k) h->stage_ran[k] = false;
+  if (h->timed && !h->ev_made) {
+    for (int k = 0; k < 10; ++k) CK(h, cudaEventCreate(&h->ev[k]));
+    h->ev_made = true;
+  }
   if ((flags & SOAPGAP_DESC) && !q) return fail(h, SOAPGAP_E_INVALID_ARG, "DESC needs q");
   if ((flags & SOAPGAP_ENERGY) && (!e_struct && !e_atom)) return fail(h, SOAPGAP_E_INVALID_ARG, "ENERGY needs e_struct or e_atom");
   if ((flags & SOAPGAP_FORCES) && !forces) return fail(h, SOAPGAP_E_INVALID_ARG, "FORCES needs forces");
@@ -506,6 +545,7 @@ extern "C" int soapgap_backward(soapgap_handle* h, const soapgap_batch* batch, c
     return fail(h, SOAPGAP_E_STATE, "backward needs a preceding ENERGY evaluation of the same batch");
   if (!dE_dEstruct || !grad_pos) return fail(h, SOAPGAP_E_INVALID_ARG, "backward needs dE_dEstruct and grad_pos");
   cudaStream_t st = (cudaStream_t)stream;
+  h->timed = false;
   if (h->mixed)
     return run<float>(h, batch, 0, nullptr, nullptr, nullptr, nullptr, nullptr, virial, dE_dEstruct, grad_pos, true, st);
   return run<double>(h, batch, 0, nullptr, nullptr, nullptr, nullptr, nullptr, virial, dE_dEstruct, grad_pos, true, st);
@@ -545,6 +585,30 @@ extern "C" int soapgap_compute_host(soapgap_handle* h, const soapgap_batch* batc
   if (forces && (flags & SOAPGAP_FORCES)) CK(h, cudaMemcpyAsync(forces, df, sizeof(double) * 3 * (size_t)N, cudaMemcpyDeviceToHost, st));
   if (virial && (flags & SOAPGAP_VIRIAL)) CK(h, cudaMemcpyAsync(virial, dv, sizeof(double) * 9 * S, cudaMemcpyDeviceToHost, st));
   CK(h, cudaStreamSynchronize(st));
+  return SOAPGAP_OK;
+}
+
+extern "C" int soapgap_stage_times(const soapgap_handle* h, double* ms) {
+  if (!h || !ms) return SOAPGAP_E_INVALID_ARG;
+  if (!h->timed) return SOAPGAP_E_STATE;
+  auto span = [&](int a, int b) {
+    float t = 0.f;
+    return cudaEventElapsedTime(&t, h->ev[a], h->ev[b]) == cudaSuccess ? (double)t : 0.0;
+  };
+  for (int k = 0; k < SOAPGAP_N_STAGES; ++k) ms[k] = 0.0;
+  if (h->stage_ran[0]) ms[0] = span(EV_NB0, EV_NB1) + span(EV_FILL0, EV_FWD0);
+  if (h->stage_ran[1]) ms[1] = span(EV_FWD0, EV_PS0);
+  if (h->stage_ran[2]) ms[2] = span(EV_PS0, h->stage_ran[3] ? EV_GF0 : EV_END);
+  if (h->stage_ran[3]) ms[3] = span(EV_GF0, EV_GB0);
+  if (h->stage_ran[4]) ms[4] = span(EV_GB0, EV_ADJ0);
+  if (h->stage_ran[5]) ms[5] = span(EV_ADJ0, EV_FIN0);
+  if (h->stage_ran[6]) ms[6] = span(h->stage_ran[4] ? EV_FIN0 : EV_GB0, EV_END);
+  return SOAPGAP_OK;
+}
+
+extern "C" int soapgap_last_launch_count(const soapgap_handle* h, int64_t* n) {
+  if (!h || !n) return SOAPGAP_E_INVALID_ARG;
+  *n = h->launches;
   return SOAPGAP_OK;
 }
 
@@ -595,5 +659,7 @@ extern "C" void soapgap_destroy(soapgap_handle* h) {
   if (h->h_err) cudaFreeHost(h->h_err);
   if (h->h_count) cudaFreeHost(h->h_count);
   if (h->h_geom) cudaFreeHost(h->h_geom);
+  if (h->ev_made)
+    for (int k = 0; k < 10; ++k) cudaEventDestroy(h->ev[k]);
   delete h;
 }

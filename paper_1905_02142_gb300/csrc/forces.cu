@@ -71,13 +71,17 @@ cudaError_t sg_finish(int n_atoms, int n_struct, int nsp, const int64_t* atom_of
                       const T* eps_part, int n_tiles, const T* vir_atom, T* e_atom,
                       double* e_struct, double* forces, double* virial, bool sign_force,
                       cudaStream_t st) {
-  if (n_atoms > 0 && ((eps_part && e_atom) || forces))
+  if (n_atoms > 0 && ((eps_part && e_atom) || forces)) {
     atom_finish_kernel<T><<<(n_atoms + 127) / 128, 128, 0, st>>>(
         n_atoms, nsp, seg_offs, rev, dedr, eps_part, n_tiles, e_atom, forces,
         sign_force ? 1.0 : -1.0);
-  if (n_struct > 0 && (e_struct || virial))
+    ++sg_kernel_launches;
+  }
+  if (n_struct > 0 && (e_struct || virial)) {
     struct_finish_kernel<T><<<n_struct, 256, 0, st>>>(atom_offs_dev, e_struct ? e_atom : nullptr,
                                                       virial ? vir_atom : nullptr, e_struct, virial);
+    ++sg_kernel_launches;
+  }
   return cudaGetLastError();
 }
 

@@ -108,6 +108,7 @@ cudaError_t sg_gap_forward_simt(const T* q, const T* qs, const T* alpha, int n, 
   dim3 grid(sg_gap_tiles(m), (n + GB_M - 1) / GB_M);
   gemm_kernel<T, 0><<<grid, 256, 0, st>>>(q, qs, n, m, d, alpha, iz, (T)zeta, eps_part, n_tiles,
                                           kp, m);
+  ++sg_kernel_launches;
   return cudaGetLastError();
 }
 
@@ -117,6 +118,7 @@ cudaError_t sg_gap_backward_simt(const T* kp, const T* qs, int n, int m, int d, 
   if (n == 0) return cudaSuccess;
   dim3 grid((d + GB_N - 1) / GB_N, (n + GB_M - 1) / GB_M);
   gemm_kernel<T, 1><<<grid, 256, 0, st>>>(kp, qs, n, d, m, nullptr, 0, T(0), nullptr, 0, g, d);
+  ++sg_kernel_launches;
   return cudaGetLastError();
 }
 

@@ -5,6 +5,9 @@
 #include <stdint.h>
 #include "common.cuh"
 
+// Kernels launched by this library since load (read around a call to count its launches).
+extern long long sg_kernel_launches;
+
 // Compile-time capacity class of the pair kernels: (n_max, l_max) <= (NC, LC).
 int sg_cap_class(int nmax, int lmax);            // 0..3 -> (6,6) (8,8) (10,10) (12,12)
 int sg_cap_n(int cls);

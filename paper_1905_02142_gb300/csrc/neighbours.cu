@@ -101,6 +101,7 @@ cudaError_t sg_exclusive_scan(const int* in, int* out, int n, int* tmp, cudaStre
   scan_block_sums<<<nb, 256, 0, st>>>(in, n, tmp);
   scan_sums<<<1, 1024, 0, st>>>(tmp, nb);
   scan_apply<<<nb, 256, 0, st>>>(in, out, n, tmp);
+  sg_kernel_launches += 3;
   return cudaGetLastError();
 }
 
@@ -138,11 +139,16 @@ __global__ void bin_fill(const double* __restrict__ pos, int n, NbrBuffers b, fl
 cudaError_t sg_nbr_bin(const double* pos, int n_atoms, int n_bins, const NbrBuffers& b,
                        cudaStream_t st) {
   cudaMemsetAsync(b.bin_count, 0, sizeof(int) * (size_t)n_bins, st);
-  if (n_atoms > 0) bin_assign<<<(n_atoms + 255) / 256, 256, 0, st>>>(pos, n_atoms, b);
+  if (n_atoms > 0) {
+    bin_assign<<<(n_atoms + 255) / 256, 256, 0, st>>>(pos, n_atoms, b);
+    ++sg_kernel_launches;
+  }
   cudaError_t e = sg_exclusive_scan(b.bin_count, b.bin_start, n_bins, b.scan_tmp, st);
   if (e != cudaSuccess) return e;
-  if (n_atoms > 0)
+  if (n_atoms > 0) {
     bin_fill<<<(n_atoms + 255) / 256, 256, 0, st>>>(pos, n_atoms, b, b.binpos);
+    ++sg_kernel_launches;
+  }
   return cudaGetLastError();
 }
 
@@ -260,6 +266,7 @@ cudaError_t sg_nbr_count(const double* pos, const int* species, int n_atoms, int
     const long long blocks = ((long long)n_atoms * 32 + threads - 1) / threads;
     count_kernel<<<(unsigned)blocks, threads, 0, st>>>(pos, species, n_atoms, nsp, rc, b,
                                                       b.binpos);
+    ++sg_kernel_launches;
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -364,6 +371,7 @@ cudaError_t sg_nbr_fill(const double* pos, const int* species, int n_atoms, int 
   Vec4<T>* sorted = reinterpret_cast<Vec4<T>*>(b.pair_r);
   sort_kernel<T><<<(unsigned)sblocks, threads, 0, st>>>((int)nseg, b, unsorted, sorted);
   rev_kernel<<<(unsigned)blocks, threads, 0, st>>>(n_atoms, nsp, species, b);
+  sg_kernel_launches += 3;
   return cudaGetLastError();
 }
 

@@ -175,6 +175,7 @@ static cudaError_t launch_fwd(const FwdArgs<T>& a, cudaStream_t st) {
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
   kern<<<(unsigned)grid, SG_WARPS * 32, smem, st>>>(a);
+  ++sg_kernel_launches;
   return cudaGetLastError();
 }
 

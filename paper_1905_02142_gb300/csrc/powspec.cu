@@ -59,6 +59,7 @@ cudaError_t sg_power_spectrum(const T* c, int n_atoms, int nch, int lmax, T* q, 
     if (e != cudaSuccess) return e;
   }
   kern<<<n_atoms, 128, smem, st>>>(c, nch, lmax, q, pnorm);
+  ++sg_kernel_launches;
   return cudaGetLastError();
 }
 

@@ -50,6 +50,7 @@ cudaError_t sg_build_table(const DevParams& p, const BasisConst<double>& W, int 
     case 2: table_kernel<10, 10><<<blocks, threads, 0, st>>>(p, W, ti, table); break;
     default: table_kernel<12, 12><<<blocks, threads, 0, st>>>(p, W, ti, table); break;
   }
+  ++sg_kernel_launches;
   return cudaGetLastError();
 }
 
@@ -71,5 +72,6 @@ __global__ void central_kernel(DevParams p, BasisConst<double> bc, double* out_n
 cudaError_t sg_central_terms(const DevParams& p, const BasisConst<double>& W, double* out_n,
                              double* out_alpha, cudaStream_t st) {
   central_kernel<<<1, 1, 0, st>>>(p, W, out_n, out_alpha);
+  ++sg_kernel_launches;
   return cudaGetLastError();
 }
