@@ -179,6 +179,26 @@ int soapgap_last_pair_count(const soapgap_handle* h, int64_t* n_pairs);
 int soapgap_export_pairs(soapgap_handle* h, int64_t capacity, int32_t* centre,
                          int32_t* neighbour, int32_t* shift);
 
+/* GAP local energies eps_i = sum_s alpha_s (q_i . q_s)^zeta for callers that cannot
+ * allocate device memory.  The paper has no counterpart: this is a service of the library.
+ * Who needs it: applications that own all device memory through their own pool and forbid
+ * other allocations, and loops that cannot accept the device-wide synchronisation that
+ * cudaMalloc/cudaFree may cause.  The call allocates nothing (no cudaMalloc, cudaFree or
+ * allocating library routine): its scratch, n * ceil(m/64) floats of per-tile partial
+ * sums, lives in a fixed 16 MiB array in the library's device memory, which every GPU
+ * that loads the library keeps until the process exits.
+ *   q [n][d], q_sparse [m][d], alpha [m], e_atom [n]: DEVICE float (MIXED layout of q);
+ *   zeta > 0; work is enqueued on `stream` (a cudaStream_t, NULL = default stream).
+ * Returns SOAPGAP_E_CAPACITY, before any device work, when n * ceil(m/64) > 4194304.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents (each call writes
+ * every entry it reads, so nothing needs clearing); calls that overlap on the GPU, on
+ * different streams of the same device, race on it. */
+int soapgap_gap_energy_noalloc(const float* q, const float* q_sparse, const float* alpha,
+                               int32_t n, int32_t m, int32_t d, double zeta, float* e_atom,
+                               void* stream);
+
 /* Message describing the last error on h ("" if none); valid until the next call. */
 const char* soapgap_last_error(const soapgap_handle* h);
 

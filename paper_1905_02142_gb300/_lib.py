@@ -60,6 +60,8 @@ SIGNATURES = {
     "soapgap_last_launch_count": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_int64)]),
     "soapgap_last_pair_count": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_int64)]),
     "soapgap_export_pairs": (ctypes.c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
+    "soapgap_gap_energy_noalloc": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int32,
+                                                  c_int32, c_double, c_void_p, c_void_p]),
     "soapgap_last_error": (ctypes.c_char_p, [c_void_p]),
     "soapgap_destroy": (None, [c_void_p]),
 }
