@@ -15,6 +15,7 @@ The reference arm (--impl reference) times the FP64 CPU oracle on bounded sample
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -43,6 +44,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="box100k_n10l10")
+    ap.add_argument("--atoms", type=int, default=0,
+                    help="override the atom count of a single-box workload (same recipe); for "
+                         "profiling captures that must stay small")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -189,6 +193,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     w = synth.get_workload(args.workload)
+    if args.atoms and w.kind == "box":
+        w = dataclasses.replace(w, n_atoms=args.atoms, name=f"{w.name}@{args.atoms}atoms")
     params = w.params()
     batch = w.structures()
     s = Structures.from_batch(batch, device=dev)

@@ -166,6 +166,13 @@ int soapgap_compute_host(soapgap_handle* h, const soapgap_batch* batch, uint32_t
  * double; stages that did not run report 0.  SOAPGAP_E_STATE if timing was not on. */
 int soapgap_stage_times(const soapgap_handle* h, double* ms);
 
+/* Diagnostic: C = A B^T on the tensor cores with the library's tcgen05 GEMM (the kernel
+ * behind the mixed-precision GAP products).  A [m][k], B [n][k] DEVICE FP16 row-major
+ * (k a multiple of 64; rows 16-byte aligned), C [m][n] DEVICE float.  Uses the handle's
+ * error word; synchronises `stream`. */
+int soapgap_tc_gemm_f16(soapgap_handle* h, const void* a, int32_t m, const void* b, int32_t n,
+                        int32_t k, float* c, void* stream);
+
 /* Number of kernels the last soapgap_compute / soapgap_backward call launched. */
 int soapgap_last_launch_count(const soapgap_handle* h, int64_t* n);
 

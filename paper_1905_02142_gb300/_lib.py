@@ -56,6 +56,8 @@ SIGNATURES = {
     "soapgap_compute_host": (ctypes.c_int, [c_void_p, ctypes.POINTER(Batch), c_uint32, c_void_p,
                                             c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                             c_void_p]),
+    "soapgap_tc_gemm_f16": (ctypes.c_int, [c_void_p, c_void_p, c_int32, c_void_p, c_int32, c_int32,
+                                           c_void_p, c_void_p]),
     "soapgap_stage_times": (ctypes.c_int, [c_void_p, c_void_p]),
     "soapgap_last_launch_count": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_int64)]),
     "soapgap_last_pair_count": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_int64)]),

@@ -87,6 +87,10 @@ struct soapgap_handle {
   double zeta = 0;
   Buf qs, alpha;
   bool has_model = false;
+  // tensor-core GAP operands of the sparse set (mixed path)
+  Buf tc_B, tc_BT, tc_cols, tc_qbar;
+  GapTcModel tcm{};
+  Buf A16, nrm, uq, r_part, kp16;
   // workspace
   Buf geom, atom_offs, atom_struct, atom_bin, atom_slot, bin_count, bin_start, bin_atoms, binpos;
   Buf seg_count, seg_offs, scan_tmp, key_tmp, r_tmp, key, pair_j, pair_r, rev, dedr;
@@ -246,6 +250,67 @@ extern "C" int soapgap_set_model(soapgap_handle* h, const double* q_sparse, cons
     for (int i = 0; i < m; ++i) b[i] = (float)alpha[i];
     CK(h, cudaMemcpy(h->qs.p, a.data(), nq * es, cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->alpha.p, b.data(), (size_t)m * es, cudaMemcpyHostToDevice));
+    // Tensor-core operands (FP64 on the host, then rounded): centre on the sparse mean,
+    // scale each centred row to unit norm, split it into FP16 hi + lo.
+    const int D = h->D, dp = (D + 63) / 64 * 64, mp = (m + 255) / 256 * 256;
+    std::vector<double> qbar(D, 0.0);
+    for (int s = 0; s < m; ++s)
+      for (int k = 0; k < D; ++k) qbar[k] += q_sparse[(size_t)s * D + k];
+    for (int k = 0; k < D; ++k) qbar[k] /= m;
+    double c0 = 0.0;
+    for (int k = 0; k < D; ++k) c0 += qbar[k] * qbar[k];
+    std::vector<__half> B((size_t)mp * 3 * dp, __float2half_rn(0.f)), BT((size_t)dp * mp, __float2half_rn(0.f));
+    std::vector<float> cols(4 * (size_t)mp, 0.f), qb(dp, 0.f);  // float4 per column
+    double kappa = 0.0;
+    std::vector<double> nrm(m);
+    std::vector<double> u(D);
+    for (int s = 0; s < m; ++s) {
+      double ss = 0.0, t = 0.0;
+      for (int k = 0; k < D; ++k) {
+        const double x = q_sparse[(size_t)s * D + k] - qbar[k];
+        ss += x * x;
+        t += x * qbar[k];
+      }
+      nrm[s] = std::sqrt(ss);
+      cols[4 * (size_t)s] = (float)(c0 + t);
+      cols[4 * (size_t)s + 1] = (float)nrm[s];
+      cols[4 * (size_t)s + 2] = (float)alpha[s];
+      kappa = std::max(kappa, std::fabs(zeta * alpha[s]) * nrm[s]);
+      const double inv = nrm[s] > 0 ? 1.0 / nrm[s] : 0.0;
+      __half* row = B.data() + (size_t)s * 3 * dp;
+      for (int k = 0; k < D; ++k) {
+        const double uk = (q_sparse[(size_t)s * D + k] - qbar[k]) * inv;
+        const __half hi = __float2half_rn((float)uk);
+        const __half lo = __float2half_rn((float)(uk - (double)__half2float(hi)));
+        row[k] = hi;
+        row[dp + k] = lo;
+        row[2 * dp + k] = hi;
+        BT[(size_t)k * mp + s] = hi;
+      }
+    }
+    if (!(kappa > 0)) kappa = 1.0;
+    for (int s = 0; s < m; ++s) cols[4 * (size_t)s + 3] = (float)(zeta * alpha[s] * nrm[s] / kappa);
+    for (int k = 0; k < D; ++k) qb[k] = (float)qbar[k];
+    CK(h, ensure(h->tc_B, B.size() * sizeof(__half)));
+    CK(h, ensure(h->tc_BT, BT.size() * sizeof(__half)));
+    CK(h, ensure(h->tc_cols, cols.size() * sizeof(float)));
+    CK(h, ensure(h->tc_qbar, qb.size() * sizeof(float)));
+    CK(h, cudaMemcpy(h->tc_B.p, B.data(), B.size() * sizeof(__half), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->tc_BT.p, BT.data(), BT.size() * sizeof(__half), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->tc_cols.p, cols.data(), cols.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->tc_qbar.p, qb.data(), qb.size() * sizeof(float), cudaMemcpyHostToDevice));
+    GapTcModel& t = h->tcm;
+    t.d = D;
+    t.dp = dp;
+    t.mp = mp;
+    t.izeta = (zeta >= 1.0 && zeta == (double)(int)zeta) ? (int)zeta : 0;
+    t.c0 = (float)c0;
+    t.zeta = (float)zeta;
+    t.kappa = (float)kappa;
+    t.B = (const __half*)h->tc_B.p;
+    t.BT = (const __half*)h->tc_BT.p;
+    t.col = (const float4*)h->tc_cols.p;
+    t.qbar = (const float*)h->tc_qbar.p;
   } else {
     CK(h, cudaMemcpy(h->qs.p, q_sparse, nq * es, cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->alpha.p, alpha, (size_t)m * es, cudaMemcpyHostToDevice));
@@ -302,7 +367,9 @@ static int setup_geometry(soapgap_handle* h, const soapgap_batch* b) {
       H += std::sqrt(c[3 * k] * c[3 * k] + c[3 * k + 1] * c[3 * k + 1] + c[3 * k + 2] * c[3 * k + 2]);
     }
     const double X = H * (mmax + 3), u = std::ldexp(1.0, -24);
-    g.margin = (float)(2.0 * (2.0 * std::sqrt(3.0) * 5.0 * rc * X * u + 4.0 * rc * rc * u) + 1e-30);
+    // |error| of each FP32 separation component <= 10 u X (rounded positions, FP32 shift from
+    // rounded lattice vectors, two additions); the margin bounds the error of d2 twice over
+    g.margin = (float)(2.0 * (2.0 * std::sqrt(3.0) * 10.0 * rc * X * u + 4.0 * rc * rc * u) + 1e-30);
     g.bin_off = bins;
     g.atom_off = (int)b->atom_offs_host[s];
     g.n_atoms = na;
@@ -329,6 +396,7 @@ static std::string device_error_text(int code) {
   if (code & SG_ERR_COINCIDENT) m += "two atoms coincide (zero separation); ";
   if (code & SG_ERR_PAIR_CAPACITY) m += "pair buffer overflow; ";
   if (code & SG_ERR_NO_REVERSE) m += "pair list not symmetric; ";
+  if (code & SG_ERR_TIMEOUT) m += "a tensor-core pipeline wait timed out; ";
   return m;
 }
 
@@ -430,11 +498,11 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
   }
   if (want_energy || backward) {
     const int M = h->M;
-    const int tiles = sg_gap_tiles(M);
+    const int tiles = h->mixed ? sg_gap_tc_tiles(h->tcm.mp) : sg_gap_tiles(M);
     CK(h, ensure(h->eps_part, es * N1 * tiles));
     CK(h, ensure(h->e_atom, es * N1));
     if (want_grad) {
-      CK(h, ensure(h->kp, es * N1 * M));
+      if (!h->mixed) CK(h, ensure(h->kp, es * N1 * M));
       CK(h, ensure(h->g, es * N1 * D));
       CK(h, ensure(h->vir_atom, es * N1 * 9));
       CK(h, ensure(h->dedr, sizeof(Vec4<T>) * Pc));
@@ -442,12 +510,31 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     }
     mark(h, EV_GF0, st);
     h->stage_ran[3] = true;
-    CK(h, sg_gap_forward_simt<T>((const T*)h->q.p, (const T*)h->qs.p, (const T*)h->alpha.p, N, M, D,
-                                 h->zeta, (T*)h->eps_part.p, tiles, want_grad ? (T*)h->kp.p : nullptr, st));
+    if constexpr (sizeof(T) == 4) {
+      // tensor cores: centred, norm-scaled FP16 split operands (see gap_tc.cu)
+      const GapTcModel& tm = h->tcm;
+      CK(h, ensure(h->A16, sizeof(__half) * N1 * 3 * tm.dp));
+      CK(h, ensure(h->nrm, sizeof(float) * N1));
+      CK(h, ensure(h->uq, sizeof(float) * N1));
+      CK(h, ensure(h->r_part, sizeof(float) * N1 * tiles));
+      if (want_grad) CK(h, ensure(h->kp16, sizeof(__half) * N1 * tm.mp));
+      CK(h, sg_gap_tc_prepare((const float*)h->q.p, N, D, tm.dp, tm.qbar, (__half*)h->A16.p,
+                              (float*)h->nrm.p, (float*)h->uq.p, st));
+      CK(h, sg_gap_tc_forward(tm, (const __half*)h->A16.p, (const float*)h->nrm.p, (const float*)h->uq.p, N,
+                              (float*)h->eps_part.p, (float*)h->r_part.p,
+                              want_grad ? (__half*)h->kp16.p : nullptr, (int*)h->err.p, st));
+    } else {
+      CK(h, sg_gap_forward_simt<T>((const T*)h->q.p, (const T*)h->qs.p, (const T*)h->alpha.p, N, M, D,
+                                   h->zeta, (T*)h->eps_part.p, tiles, want_grad ? (T*)h->kp.p : nullptr, st));
+    }
     mark(h, EV_GB0, st);
     if (want_grad) {
       h->stage_ran[4] = h->stage_ran[5] = true;
-      CK(h, sg_gap_backward_simt<T>((const T*)h->kp.p, (const T*)h->qs.p, N, M, D, (T*)h->g.p, st));
+      if constexpr (sizeof(T) == 4)
+        CK(h, sg_gap_tc_backward(h->tcm, (const __half*)h->kp16.p, (const float*)h->r_part.p, N,
+                                 (float*)h->g.p, (int*)h->err.p, st));
+      else
+        CK(h, sg_gap_backward_simt<T>((const T*)h->kp.p, (const T*)h->qs.p, N, M, D, (T*)h->g.p, st));
       if (struct_w_user) {
         CK(h, cudaMemcpyAsync(h->struct_w.p, struct_w_user, sizeof(double) * S, cudaMemcpyDeviceToDevice, st));
       } else {
@@ -588,6 +675,18 @@ extern "C" int soapgap_compute_host(soapgap_handle* h, const soapgap_batch* batc
   return SOAPGAP_OK;
 }
 
+extern "C" int soapgap_tc_gemm_f16(soapgap_handle* h, const void* a, int32_t m, const void* b, int32_t n,
+                                   int32_t k, float* c, void* stream) {
+  if (!h || !a || !b || !c || m < 1 || n < 1 || k < 64 || k % 64 != 0) return SOAPGAP_E_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(h, cudaMemsetAsync(h->err.p, 0, sizeof(int), st));
+  CK(h, sg_tc_gemm_store((const __half*)a, m, (const __half*)b, n, k, c, (int*)h->err.p, st));
+  CK(h, cudaMemcpyAsync(h->h_err, h->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  if (*h->h_err) return fail(h, SOAPGAP_E_CUDA, device_error_text(*h->h_err));
+  return SOAPGAP_OK;
+}
+
 extern "C" int soapgap_stage_times(const soapgap_handle* h, double* ms) {
   if (!h || !ms) return SOAPGAP_E_INVALID_ARG;
   if (!h->timed) return SOAPGAP_E_STATE;
@@ -647,7 +746,8 @@ extern "C" const char* soapgap_last_error(const soapgap_handle* h) {
 
 extern "C" void soapgap_destroy(soapgap_handle* h) {
   if (!h) return;
-  Buf* bufs[] = {&h->table, &h->qs, &h->alpha, &h->geom, &h->atom_offs, &h->atom_struct,
+  Buf* bufs[] = {&h->tc_B, &h->tc_BT, &h->tc_cols, &h->tc_qbar, &h->A16, &h->nrm, &h->uq,
+                 &h->r_part, &h->kp16, &h->table, &h->qs, &h->alpha, &h->geom, &h->atom_offs, &h->atom_struct,
                  &h->atom_bin, &h->atom_slot, &h->bin_count, &h->bin_start, &h->bin_atoms,
                  &h->binpos, &h->seg_count, &h->seg_offs, &h->scan_tmp, &h->key_tmp, &h->r_tmp,
                  &h->key, &h->pair_j, &h->pair_r, &h->rev, &h->dedr, &h->c, &h->q, &h->pnorm,

@@ -15,6 +15,7 @@
 #define SG_ERR_PAIR_CAPACITY 4
 #define SG_ERR_NO_REVERSE 8
 #define SG_ERR_BIN_CAPACITY 16
+#define SG_ERR_TIMEOUT 32
 
 // Hyperparameters in device form (Eq. 15, Sec. III.A-B).
 struct DevParams {

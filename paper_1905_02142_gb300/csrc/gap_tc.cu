@@ -1,0 +1,489 @@
+// GAP model on the tensor cores (mixed-precision path): tcgen05.mma with FP16 operands
+// staged by TMA in 128B-swizzled shared memory and FP32 accumulators in tensor memory.
+//
+//   eps_i = sum_s alpha_s (q_i . q_s)^zeta      (Sec. IV.A with the SOAP kernel of Sec. I)
+//   g_i   = dE/dq_i = sum_s zeta alpha_s (q_i . q_s)^(zeta-1) q_s
+//
+// The dot products q_i.q_s lie close together (0.86..1.0 on carbon-like boxes) and the
+// alpha_s have random signs, so eps_i is a strong cancellation: plain BF16 operands lose
+// ~6e-2 of it and plain FP16 ~5e-3.  The products are therefore split as
+//   q = qbar + n u,  qbar = mean of the sparse rows, n = |q - qbar|, |u| = 1,
+//   q_i.q_s = qbar.qbar + qbar.(q_i - qbar) + qbar.(q_s - qbar) + n_i n_s (u_i . u_s),
+// with the rank-one terms in FP32 and u_i.u_s on the tensor cores as hi*hi + hi*lo + lo*hi
+// of an FP16 hi/lo split (one GEMM over K = 3 D: A = [hi|hi|lo], B = [hi|lo|hi]); relative
+// error ~2e-7 on eps.  The backward product needs less: g_i = r_i qbar + kappa kp'_i U with
+// r_i = sum_s zeta alpha_s S^(zeta-1) in FP32, kp'_is = zeta alpha_s n_s S^(zeta-1) / kappa in
+// FP16 and U the unit sparse rows in FP16 (single pass).
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int BM = 128, BK = 64;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after ~1 s of SM clock so that a broken pipeline reports an
+// error instead of hanging the GPU.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > 2000000000LL) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major tile, rows of 128 B, 128-byte swizzle, 8-row
+// groups 1024 B apart (SBO), leading offset unused for this layout, descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+// Instruction descriptor, kind::f16: D = F32, A = B = F16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(int m, int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+        "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+        "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+        "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ------------------------------------------------------------------ epilogues
+struct EpiStore {  // C = A B^T (diagnostic)
+  int rows, cols;
+  float* c;
+  __device__ void begin(int) {}
+  __device__ void apply(int row, int col0, const uint32_t* v) {
+    if (row >= rows) return;
+    for (int j = 0; j < 32; ++j)
+      if (col0 + j < cols) c[(size_t)row * cols + col0 + j] = __uint_as_float(v[j]);
+  }
+  __device__ void end(int, int) {}
+};
+
+// s^(Z-1) for a compile-time integer Z >= 1
+template <int Z>
+__device__ __forceinline__ float pow_zm1(float s) {
+  float o = 1.f;
+#pragma unroll
+  for (int k = 1; k < Z; ++k) o *= s;
+  return o;
+}
+
+struct EpiGapFwd {
+  int rows, ld_kp, n_tiles, izeta;
+  float zeta;
+  const float *u, *nrm;              // [N]
+  const float4* col;                 // [Mp] (qbar.qbar + qbar.(q_s-qbar), n_s, alpha_s, f_s)
+  float *eps_part, *r_part;          // [N][n_tiles]
+  __half* kp;                        // [N][ld_kp] or null
+  float eps, r, ui, ni;
+  __device__ void begin(int row) {
+    eps = 0.f;
+    r = 0.f;
+    ui = row < rows ? u[row] : 0.f;
+    ni = row < rows ? nrm[row] : 0.f;
+  }
+  // S^(zeta-1) for one output, zeta fixed at compile time (Z > 0) or general (Z = 0)
+  template <int Z>
+  __device__ __forceinline__ void run(int col0, const uint32_t* v, __half2* out) {
+#pragma unroll
+    for (int j = 0; j < 32; j += 2) {
+      float kv[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float4 c = __ldg(col + col0 + j + h);
+        const float S = fmaf(ni * c.y, __uint_as_float(v[j + h]), ui + c.x);
+        const float sz1 = Z > 0 ? pow_zm1<Z>(S) : powf(fmaxf(S, 0.f), zeta - 1.f);
+        eps = fmaf(c.z, sz1 * S, eps);
+        r = fmaf(zeta * c.z, sz1, r);
+        kv[h] = c.w * sz1;
+      }
+      out[j / 2] = __floats2half2_rn(kv[0], kv[1]);
+    }
+  }
+  __device__ void apply(int row, int col0, const uint32_t* v) {
+    if (row >= rows) return;
+    __align__(16) __half2 out[16];
+    switch (izeta) {
+      case 1: run<1>(col0, v, out); break;
+      case 2: run<2>(col0, v, out); break;
+      case 3: run<3>(col0, v, out); break;
+      case 4: run<4>(col0, v, out); break;
+      default: run<0>(col0, v, out); break;
+    }
+    if (kp) {
+      uint4* dst = reinterpret_cast<uint4*>(kp + (size_t)row * ld_kp + col0);
+      const uint4* src = reinterpret_cast<const uint4*>(out);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) dst[k] = src[k];
+    }
+  }
+  __device__ void end(int row, int slot) {
+    if (row >= rows) return;
+    eps_part[(size_t)row * n_tiles + slot] = eps;
+    r_part[(size_t)row * n_tiles + slot] = r;
+  }
+};
+
+struct EpiGapBwd {
+  int rows, d, n_tiles;
+  float kappa;
+  const float* qbar;    // [Dp]
+  const float* r_part;  // [N][n_tiles]
+  float* g;             // [N][d]
+  float r;
+  __device__ void begin(int row) {
+    r = 0.f;
+    if (row < rows)
+      for (int t = 0; t < n_tiles; ++t) r += r_part[(size_t)row * n_tiles + t];
+  }
+  __device__ void apply(int row, int col0, const uint32_t* v) {
+    if (row >= rows) return;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int k = col0 + j;
+      if (k < d) g[(size_t)row * d + k] = fmaf(r, __ldg(qbar + k), kappa * __uint_as_float(v[j]));
+    }
+  }
+  __device__ void end(int, int) {}
+};
+
+// ------------------------------------------------------------------ the GEMM
+// Persistent, warp-specialised: one CTA per SM walks the output tiles (row-major over
+// [M/BM] x [N/BN], so CTAs running together share A rows in L2).
+//   warp 0, lane 0 : TMA producer, STAGES-deep ring of A/B tiles (full/empty mbarriers)
+//   warp 1, lane 0 : MMA issuer, accumulates each tile into one of two TMEM buffers
+//   warps 2..      : epilogue, EPI_WARPS warps; warp w reads TMEM lanes 32*(w%4) .. +31 and
+//                    a 1/(EPI_WARPS/4) share of the columns; it releases the buffer when done
+// so the epilogue of one tile overlaps the MMAs of the next.
+template <int BN, int STAGES, int EPI_WARPS, class Epi>
+__global__ void __launch_bounds__(32 * (2 + EPI_WARPS), 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               int num_kb, int m_tiles, int n_tiles, Epi epi, int* err) {
+  constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+  constexpr int HALVES = EPI_WARPS / 4;           // column groups per tile
+  constexpr int COLS = BN / HALVES;               // columns per epilogue warp
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_BYTES;
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t tfull_bar[2];
+  __shared__ __align__(8) uint64_t tempty_bar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int total = m_tiles * n_tiles;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull_bar[b], 1);
+      mbar_init(&tempty_bar[b], EPI_WARPS);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"((uint32_t)(2 * BN))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      int issued[STAGES];
+      for (int s = 0; s < STAGES; ++s) issued[s] = 0;
+      for (int t = blockIdx.x; t < total && !abort_flag; t += gridDim.x) {
+        const int m0 = (t / n_tiles) * BM, n0 = (t % n_tiles) * BN;
+        for (int kb = 0; kb < num_kb; ++kb, ++it) {
+          const int s = it % STAGES, round = it / STAGES;
+          if (round > 0 && !mbar_wait(&empty_bar[s], (round - 1) & 1)) {
+            abort_flag = 1;
+            break;
+          }
+          mbar_expect_tx(&full_bar[s], A_BYTES + B_BYTES);
+          tma_load_2d(sA + s * A_BYTES, &tmA, kb * BK, m0, &full_bar[s]);
+          tma_load_2d(sB + s * B_BYTES, &tmB, kb * BK, n0, &full_bar[s]);
+          ++issued[s];
+        }
+      }
+      // every copy started here has landed before the block may exit
+      for (int s = 0; s < STAGES; ++s)
+        if (issued[s] > 0 && !mbar_wait(&full_bar[s], (issued[s] - 1) & 1)) abort_flag = 1;
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_f16(BM, BN);
+      int it = 0, lt = 0;
+      for (int t = blockIdx.x; t < total && !abort_flag; t += gridDim.x, ++lt) {
+        const int b = lt & 1, use = lt >> 1;
+        if (use > 0 && !mbar_wait(&tempty_bar[b], (use - 1) & 1)) {
+          abort_flag = 1;
+          break;
+        }
+        fence_after();
+        const uint32_t acc = tmem + (uint32_t)(b * BN);
+        bool ok = true;
+        for (int kb = 0; kb < num_kb; ++kb, ++it) {
+          const int s = it % STAGES, round = it / STAGES;
+          if (!mbar_wait(&full_bar[s], round & 1)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k)
+            mma_f16(acc, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32), idesc, (kb | k) != 0);
+          mma_commit(&empty_bar[s]);
+        }
+        if (!ok) {
+          abort_flag = 1;
+          break;
+        }
+        mma_commit(&tfull_bar[b]);
+      }
+    }
+    __syncwarp();
+  } else {
+    const int ew = warp - 2;                 // 0 .. EPI_WARPS-1
+    const int lg = warp & 3;                 // TMEM lane group this warp may access
+    const int half = ew / 4;                 // column group
+    int lt = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++lt) {
+      const int b = lt & 1, use = lt >> 1;
+      const bool ready = __all_sync(0xffffffffu, mbar_wait(&tfull_bar[b], use & 1) && !abort_flag);
+      if (!ready) {
+        if (lane == 0) {
+          abort_flag = 1;
+          atomicOr(err, SG_ERR_TIMEOUT);
+        }
+        break;
+      }
+      fence_after();
+      const int m0 = (t / n_tiles) * BM, n0 = (t % n_tiles) * BN;
+      const int row = m0 + lg * 32 + lane;
+      epi.begin(row);
+#pragma unroll 1
+      for (int c = 0; c < COLS / 32; ++c) {
+        uint32_t v[32];
+        const int col = half * COLS + c * 32;
+        tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + col), v);
+        epi.apply(row, n0 + col, v);
+      }
+      epi.end(row, (t % n_tiles) * HALVES + half);
+      fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty_bar[b])) : "memory");
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN))
+                 : "memory");
+}
+
+template <int BN, int STAGES>
+constexpr size_t smem_bytes() {
+  return (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 1024;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2D FP16 row-major matrix [rows][cols] (cols a multiple of 64), tiles of box_rows x 64.
+bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int STAGES, int EPI_WARPS, class Epi>
+cudaError_t launch_gemm(const void* A, int a_rows, const void* B, int b_rows, int k, Epi epi, int* err,
+                        cudaStream_t st) {
+  if (k % BK != 0 || a_rows <= 0 || b_rows <= 0) return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, a_rows, k, BM) || !make_map(&mb, B, b_rows, k, BN)) return cudaErrorInvalidValue;
+  auto kern = tc_gemm_kernel<BN, STAGES, EPI_WARPS, Epi>;
+  constexpr size_t smem = smem_bytes<BN, STAGES>();
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int m_tiles = (a_rows + BM - 1) / BM, n_tiles = (b_rows + BN - 1) / BN;
+  const int grid = std::min(sms, m_tiles * n_tiles);
+  kern<<<grid, 32 * (2 + EPI_WARPS), smem, st>>>(ma, mb, k / BK, m_tiles, n_tiles, epi, err);
+  ++sg_kernel_launches;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ operand preparation
+// one warp per atom: u = (q - qbar)/|q - qbar| as FP16 hi/lo, A row = [hi | hi | lo]
+__global__ void prep_atoms_kernel(const float* __restrict__ q, int n, int d, int dp,
+                                  const float* __restrict__ qbar, __half* A, float* nrm, float* uq) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  const float* qi = q + (size_t)i * d;
+  float ss = 0.f, dq = 0.f;
+  for (int k = lane; k < d; k += 32) {
+    const float t = qi[k] - qbar[k];
+    ss = fmaf(t, t, ss);
+    dq = fmaf(t, qbar[k], dq);
+  }
+  ss = warp_sum(ss);
+  dq = warp_sum(dq);
+  const float nn = sqrtf(ss);
+  const float inv = nn > 0.f ? 1.f / nn : 0.f;
+  __half* row = A + (size_t)i * 3 * dp;
+  for (int k = lane; k < dp; k += 32) {
+    const float uk = k < d ? (qi[k] - qbar[k]) * inv : 0.f;
+    const __half hi = __float2half_rn(uk);
+    const __half lo = __float2half_rn(uk - __half2float(hi));
+    row[k] = hi;
+    row[dp + k] = hi;
+    row[2 * dp + k] = lo;
+  }
+  if (lane == 0) {
+    nrm[i] = nn;
+    uq[i] = dq;
+  }
+}
+
+}  // namespace
+
+// partial-sum slots per row of the forward epilogue: two column halves per 256-wide tile
+int sg_gap_tc_tiles(int mp) { return (mp + 255) / 256 * 2; }
+
+cudaError_t sg_gap_tc_prepare(const float* q, int n, int d, int dp, const float* qbar, __half* A, float* nrm,
+                              float* uq, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  prep_atoms_kernel<<<(n * 32 + 127) / 128, 128, 0, st>>>(q, n, d, dp, qbar, A, nrm, uq);
+  ++sg_kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t sg_gap_tc_forward(const GapTcModel& md, const __half* A, const float* nrm, const float* uq, int n,
+                              float* eps_part, float* r_part, __half* kp, int* err, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  EpiGapFwd e{};
+  e.rows = n;
+  e.ld_kp = md.mp;
+  e.n_tiles = sg_gap_tc_tiles(md.mp);
+  e.izeta = md.izeta;
+  e.zeta = md.zeta;
+  e.u = uq;
+  e.nrm = nrm;
+  e.col = md.col;
+  e.eps_part = eps_part;
+  e.r_part = r_part;
+  e.kp = kp;
+  return launch_gemm<256, 4, 8>(A, n, md.B, md.mp, 3 * md.dp, e, err, st);
+}
+
+cudaError_t sg_gap_tc_backward(const GapTcModel& md, const __half* kp, const float* r_part, int n, float* g,
+                               int* err, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  EpiGapBwd e{};
+  e.rows = n;
+  e.d = md.d;
+  e.n_tiles = sg_gap_tc_tiles(md.mp);
+  e.kappa = md.kappa;
+  e.qbar = md.qbar;
+  e.r_part = r_part;
+  e.g = g;
+  return launch_gemm<128, 6, 4>(kp, n, md.BT, md.dp, md.mp, e, err, st);
+}
+
+cudaError_t sg_tc_gemm_store(const __half* A, int m, const __half* B, int nn, int k, float* C, int* err,
+                             cudaStream_t st) {
+  EpiStore e{m, nn, C};
+  return launch_gemm<128, 6, 4>(A, m, B, nn, k, e, err, st);
+}

@@ -1,6 +1,7 @@
 // Launch interfaces between the C-ABI layer (api.cu) and the kernel translation units.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include "common.cuh"
@@ -94,6 +95,27 @@ int sg_gap_tiles(int m);
 template <typename T>
 cudaError_t sg_gap_backward_simt(const T* kp, const T* qs, int n, int m, int d, T* g,
                                  cudaStream_t st);
+
+// ---------------------------------------------------------------- gap_tc.cu
+// Sparse-set side of the tensor-core GAP kernels (built by soapgap_set_model).
+struct GapTcModel {
+  int d, dp, mp, izeta;   // D, D padded to 64, M padded to 256, integer zeta (0: not integer)
+  float c0, zeta, kappa;  // qbar.qbar, zeta, backward scale
+  const __half* B;        // [mp][3 dp]  unit centred sparse rows as [hi | lo | hi]
+  const __half* BT;       // [dp][mp]    the same rows transposed, hi only
+  const float4* col;      // [mp]: (qbar.qbar + qbar.(q_s - qbar), |q_s - qbar|, alpha_s,
+                          //        zeta alpha_s |q_s - qbar| / kappa), zero beyond M
+  const float* qbar;      // [dp]
+};
+int sg_gap_tc_tiles(int m);
+cudaError_t sg_gap_tc_prepare(const float* q, int n, int d, int dp, const float* qbar, __half* A,
+                              float* nrm, float* uq, cudaStream_t st);
+cudaError_t sg_gap_tc_forward(const GapTcModel& md, const __half* A, const float* nrm, const float* uq,
+                              int n, float* eps_part, float* r_part, __half* kp, int* err, cudaStream_t st);
+cudaError_t sg_gap_tc_backward(const GapTcModel& md, const __half* kp, const float* r_part, int n,
+                               float* g, int* err, cudaStream_t st);
+cudaError_t sg_tc_gemm_store(const __half* A, int m, const __half* B, int n, int k, float* C, int* err,
+                             cudaStream_t st);
 
 // ---------------------------------------------------------------- pair_adj.cu
 template <typename T> struct AdjArgs {

@@ -159,10 +159,20 @@ __device__ __forceinline__ bool lex_positive(int s1, int s2, int s3) {
   return s1 > 0 || (s1 == 0 && (s2 > 0 || (s2 == 0 && s3 > 0)));
 }
 
+// FP64 shift vector s = (S1*h1 + S2*h2) + S3*h3, fixed order, no FMA
+__device__ __forceinline__ void shift_vec(const StructGeom& g, int S1, int S2, int S3, double s[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    s[c] = __dadd_rn(__dadd_rn(__dmul_rn((double)S1, g.h[c]), __dmul_rn((double)S2, g.h[3 + c])),
+                     __dmul_rn((double)S3, g.h[6 + c]));
+}
+
 // exact FP64 separation (fixed operation order, no FMA) in canonical orientation
 __device__ __forceinline__ void exact_sep(const double* __restrict__ pos, int i, int j,
-                                         const double s[3], bool canon, double r[3],
-                                         double& d2) {
+                                         const StructGeom& g, int S1, int S2, int S3, bool canon,
+                                         double r[3], double& d2) {
+  double s[3];
+  shift_vec(g, S1, S2, S3, s);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     double xi = pos[3 * i + c], xj = pos[3 * j + c];
@@ -172,7 +182,9 @@ __device__ __forceinline__ void exact_sep(const double* __restrict__ pos, int i,
 }
 
 // Visit every kept pair of atom i; lanes of the warp take candidates in parallel.
-// fn(lane_has_pair, j, S1, S2, S3, r[3], d2) is called by all lanes together.
+// fn(lane_has_pair, j, S1, S2, S3, r[3], d2) is called by all lanes together; d2 < 0 marks a
+// pair kept by the FP32 test whose exact FP64 separation has not been computed.
+// The FP32 shift uses the FP32 lattice vectors; the rounding margin covers that too.
 template <typename Fn>
 __device__ __forceinline__ void visit_pairs(const double* __restrict__ pos, const float4* binpos,
                                             int i, double rc, const NbrBuffers& b, Fn&& fn) {
@@ -190,12 +202,10 @@ __device__ __forceinline__ void visit_pairs(const double* __restrict__ pos, cons
       const int t1 = c1 + d1, S2 = floor_div(t1, g.nb[1]), b1 = t1 - S2 * g.nb[1];
       for (int d2i = -g.m[2]; d2i <= g.m[2]; ++d2i) {
         const int t2 = c2 + d2i, S3 = floor_div(t2, g.nb[2]), b2 = t2 - S3 * g.nb[2];
-        double s[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-          s[c] = __dadd_rn(__dadd_rn(__dmul_rn((double)S1, g.h[c]), __dmul_rn((double)S2, g.h[3 + c])),
-                           __dmul_rn((double)S3, g.h[6 + c]));
-        const float sx = (float)s[0], sy = (float)s[1], sz = (float)s[2];
+        const float f1 = (float)S1, f2 = (float)S2, f3 = (float)S3;
+        const float sx = __fadd_rn(__fadd_rn(__fmul_rn(f1, g.h32[0]), __fmul_rn(f2, g.h32[3])), __fmul_rn(f3, g.h32[6]));
+        const float sy = __fadd_rn(__fadd_rn(__fmul_rn(f1, g.h32[1]), __fmul_rn(f2, g.h32[4])), __fmul_rn(f3, g.h32[7]));
+        const float sz = __fadd_rn(__fadd_rn(__fmul_rn(f1, g.h32[2]), __fmul_rn(f2, g.h32[5])), __fmul_rn(f3, g.h32[8]));
         const int tb = g.bin_off + (b0 * g.nb[1] + b1) * g.nb[2] + b2;
         const int beg = b.bin_start[tb], end = b.bin_start[tb + 1];
         const bool zero_shift = (S1 == 0 && S2 == 0 && S3 == 0);
@@ -219,7 +229,7 @@ __device__ __forceinline__ void visit_pairs(const double* __restrict__ pos, cons
               if (near_cut || near_zero || d2f < rc2f) {
                 if (near_cut || near_zero) {
                   const bool canon = (j > i) || (j == i && lexpos);
-                  exact_sep(pos, i, j, s, canon, r, d2);
+                  exact_sep(pos, i, j, g, S1, S2, S3, canon, r, d2);
                   keep = d2 < rc2;
                   if (keep && d2 == 0.0) atomicOr(b.err, SG_ERR_COINCIDENT);
                 } else {
@@ -229,7 +239,7 @@ __device__ __forceinline__ void visit_pairs(const double* __restrict__ pos, cons
               }
             }
           }
-          fn(keep, j, S1, S2, S3, s, r, d2);
+          fn(keep, j, S1, S2, S3, r, d2);
         }
       }
     }
@@ -246,7 +256,7 @@ __global__ void count_kernel(const double* __restrict__ pos, const int* __restri
 #pragma unroll
   for (int s = 0; s < SG_MAX_SPECIES; ++s) cnt[s] = 0;
   visit_pairs(pos, binpos, i, rc, b,
-              [&](bool keep, int j, int, int, int, const double*, const double*, double) {
+              [&](bool keep, int j, int, int, int, const double*, double) {
                 if (keep) {
                   const int sj = species[j];
 #pragma unroll
@@ -289,8 +299,7 @@ __global__ void fill_kernel(const double* __restrict__ pos, const int* __restric
   int next[SG_MAX_SPECIES];
   for (int s = 0; s < nsp; ++s) next[s] = b.seg_offs[i * nsp + s];
   visit_pairs(pos, binpos, i, rc, b,
-              [&](bool keep, int j, int S1, int S2, int S3, const double* s, const double* r0,
-                  double d2) {
+              [&](bool keep, int j, int S1, int S2, int S3, const double* r0, double d2) {
                 int sj = keep ? species[j] : -1;
                 for (int sp = 0; sp < nsp; ++sp) {
                   const unsigned mask = __ballot_sync(0xffffffffu, keep && sj == sp);
@@ -299,12 +308,14 @@ __global__ void fill_kernel(const double* __restrict__ pos, const int* __restric
                     double r[3] = {r0[0], r0[1], r0[2]};
                     if (d2 < 0.0) {
                       const bool canon = (j > i) || (j == i && lex_positive(S1, S2, S3));
-                      exact_sep(pos, i, j, s, canon, r, d2);
+                      exact_sep(pos, i, j, b.geom[b.atom_struct[i]], S1, S2, S3, canon, r, d2);
                     }
                     if (at < cap) {
                       b.key_tmp[at] = pair_key(j, S1, S2, S3);
                       Vec4<T> v;
-                      v.x = (T)r[0]; v.y = (T)r[1]; v.z = (T)r[2]; v.w = (T)sqrt(d2);
+                      v.x = (T)r[0]; v.y = (T)r[1]; v.z = (T)r[2];
+                      if constexpr (sizeof(T) == 4) v.w = sqrtf((float)d2);  // FP32 length, mixed path
+                      else v.w = sqrt(d2);
                       rout[at] = v;
                     } else {
                       atomicOr(b.err, SG_ERR_PAIR_CAPACITY);
