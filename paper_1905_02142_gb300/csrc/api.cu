@@ -92,9 +92,11 @@ struct soapgap_handle {
   GapTcModel tcm{};
   Buf A16, nrm, uq, r_part, kp16;
   // workspace
-  Buf geom, atom_offs, atom_struct, atom_bin, atom_slot, bin_count, bin_start, bin_atoms, binpos;
+  Buf geom, atom_offs, atom_struct, atom_bin, atom_bin4, atom_slot, bin_count, bin_start, bin_atoms, binpos,
+      binpos_lo, atom_hi, atom_lo;
   Buf seg_count, seg_offs, scan_tmp, key_tmp, r_tmp, key, pair_j, pair_r, rev, dedr;
-  Buf c, q, pnorm, e_atom, eps_part, kp, g, vir_atom, struct_w, err, cen_tmp;
+  Buf c, q, pnorm, e_atom, eps_part, kp, g, vir_atom, struct_w, err, cen_tmp, finish_part;
+  int finish_chunks = 1;
   Buf host_in_pos, host_in_species, host_q, host_pnorm, host_e_atom, host_e_struct, host_forces,
       host_virial;
   int* h_err = nullptr;           // pinned
@@ -332,11 +334,15 @@ static int setup_geometry(soapgap_handle* h, const soapgap_batch* b) {
     h->h_geom_cap = S;
   }
   const double rc = h->prm.r_cut;
-  int bins = 0;
+  int bins = 0, max_atoms = 0;
   for (int s = 0; s < S; ++s) {
     StructGeom& g = h->h_geom[s];
     const double* c = b->cell_host + 9 * s;
-    for (int k = 0; k < 9; ++k) { g.h[k] = c[k]; g.h32[k] = (float)c[k]; }
+    for (int k = 0; k < 9; ++k) {
+      g.h[k] = c[k];
+      g.h32[k] = (float)c[k];
+      g.h32lo[k] = (float)(c[k] - (double)g.h32[k]);
+    }
     const double det = c[0] * (c[4] * c[8] - c[5] * c[7]) - c[1] * (c[3] * c[8] - c[5] * c[6]) +
                        c[2] * (c[3] * c[7] - c[4] * c[6]);
     if (!(std::fabs(det) > 0) || !std::isfinite(det))
@@ -370,12 +376,14 @@ static int setup_geometry(soapgap_handle* h, const soapgap_batch* b) {
     // |error| of each FP32 separation component <= 10 u X (rounded positions, FP32 shift from
     // rounded lattice vectors, two additions); the margin bounds the error of d2 twice over
     g.margin = (float)(2.0 * (2.0 * std::sqrt(3.0) * 10.0 * rc * X * u + 4.0 * rc * rc * u) + 1e-30);
+    max_atoms = std::max(max_atoms, na);
     g.bin_off = bins;
     g.atom_off = (int)b->atom_offs_host[s];
     g.n_atoms = na;
     bins += g.nb[0] * g.nb[1] * g.nb[2];
   }
   h->n_bins = bins;
+  h->finish_chunks = sg_finish_chunks(max_atoms);
   return SOAPGAP_OK;
 }
 
@@ -419,9 +427,13 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     CK(h, ensure(h->atom_offs, sizeof(int64_t) * (size_t)(S + 1)));
     CK(h, ensure(h->atom_struct, sizeof(int) * (size_t)std::max(N, 1)));
     CK(h, ensure(h->atom_bin, sizeof(int) * (size_t)std::max(N, 1)));
+    CK(h, ensure(h->atom_bin4, sizeof(int4) * (size_t)std::max(N, 1)));
     CK(h, ensure(h->atom_slot, sizeof(int) * (size_t)std::max(N, 1)));
     CK(h, ensure(h->bin_atoms, sizeof(int) * (size_t)std::max(N, 1)));
     CK(h, ensure(h->binpos, sizeof(float4) * (size_t)std::max(N, 1)));
+    CK(h, ensure(h->binpos_lo, sizeof(float4) * (size_t)std::max(N, 1)));
+    CK(h, ensure(h->atom_hi, sizeof(float4) * (size_t)std::max(N, 1)));
+    CK(h, ensure(h->atom_lo, sizeof(float4) * (size_t)std::max(N, 1)));
     CK(h, ensure(h->bin_count, sizeof(int) * (size_t)(h->n_bins + 1)));
     CK(h, ensure(h->bin_start, sizeof(int) * (size_t)(h->n_bins + 1)));
     CK(h, ensure(h->seg_count, sizeof(int) * (size_t)std::max(nseg, 1)));
@@ -438,11 +450,15 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
   nb.geom = (const StructGeom*)h->geom.p;
   nb.atom_struct = (const int*)h->atom_struct.p;
   nb.atom_bin = (int*)h->atom_bin.p;
+  nb.atom_bin4 = (int4*)h->atom_bin4.p;
   nb.atom_slot = (int*)h->atom_slot.p;
   nb.bin_count = (int*)h->bin_count.p;
   nb.bin_start = (int*)h->bin_start.p;
   nb.bin_atoms = (int*)h->bin_atoms.p;
   nb.binpos = (float4*)h->binpos.p;
+  nb.binpos_lo = (float4*)h->binpos_lo.p;
+  nb.atom_hi = (float4*)h->atom_hi.p;
+  nb.atom_lo = (float4*)h->atom_lo.p;
   nb.seg_count = (int*)h->seg_count.p;
   nb.seg_offs = (int*)h->seg_offs.p;
   nb.scan_tmp = (int*)h->scan_tmp.p;
@@ -562,10 +578,11 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     double* f_out = backward ? grad_pos : ((flags & SOAPGAP_FORCES) ? forces : nullptr);
     double* v_out = (backward || (flags & SOAPGAP_VIRIAL)) ? virial : nullptr;
     double* es_out = backward ? nullptr : e_struct;
+    CK(h, ensure(h->finish_part, sizeof(double) * 10 * (size_t)S * h->finish_chunks));
     CK(h, sg_finish<T>(N, S, nsp, (const int64_t*)h->atom_offs.p, nb.seg_offs, (const int*)h->rev.p,
                        (const Vec4<T>*)h->dedr.p, (const T*)h->eps_part.p, tiles,
                        v_out ? (const T*)h->vir_atom.p : nullptr, (T*)h->e_atom.p, es_out, f_out,
-                       v_out, !backward, st));
+                       v_out, !backward, h->finish_chunks, (double*)h->finish_part.p, st));
     if (!backward && e_atom_out)
       CK(h, cudaMemcpyAsync(e_atom_out, h->e_atom.p, es * (size_t)N, cudaMemcpyDeviceToDevice, st));
   }
@@ -748,10 +765,11 @@ extern "C" void soapgap_destroy(soapgap_handle* h) {
   if (!h) return;
   Buf* bufs[] = {&h->tc_B, &h->tc_BT, &h->tc_cols, &h->tc_qbar, &h->A16, &h->nrm, &h->uq,
                  &h->r_part, &h->kp16, &h->table, &h->qs, &h->alpha, &h->geom, &h->atom_offs, &h->atom_struct,
-                 &h->atom_bin, &h->atom_slot, &h->bin_count, &h->bin_start, &h->bin_atoms,
-                 &h->binpos, &h->seg_count, &h->seg_offs, &h->scan_tmp, &h->key_tmp, &h->r_tmp,
+                 &h->atom_bin, &h->atom_bin4, &h->atom_slot, &h->bin_count, &h->bin_start, &h->bin_atoms,
+                 &h->binpos, &h->binpos_lo, &h->atom_hi, &h->atom_lo, &h->seg_count, &h->seg_offs, &h->scan_tmp, &h->key_tmp, &h->r_tmp,
                  &h->key, &h->pair_j, &h->pair_r, &h->rev, &h->dedr, &h->c, &h->q, &h->pnorm,
                  &h->e_atom, &h->eps_part, &h->kp, &h->g, &h->vir_atom, &h->struct_w, &h->err,
+                 &h->finish_part,
                  &h->cen_tmp, &h->host_in_pos, &h->host_in_species, &h->host_q, &h->host_pnorm,
                  &h->host_e_atom, &h->host_e_struct, &h->host_forces, &h->host_virial};
   for (Buf* b : bufs)

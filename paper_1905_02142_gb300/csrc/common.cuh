@@ -31,6 +31,7 @@ struct StructGeom {
   double h[9];     // rows = lattice vectors
   double hinv[9];  // inverse (fractional = x @ hinv)
   float h32[9];
+  float h32lo[9];  // h - (double)h32, so that h = h32 + h32lo to ~2^-48
   int nb[3];       // bins along each lattice direction
   int m[3];        // bin offsets searched: -m..m
   int bin_off;     // first bin of this structure in the flattened bin arrays

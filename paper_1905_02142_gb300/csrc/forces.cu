@@ -10,34 +10,46 @@ __global__ void atom_finish_kernel(int n, int nsp, const int* __restrict__ seg_o
                                    const int* __restrict__ rev, const Vec4<T>* __restrict__ dedr,
                                    const T* __restrict__ eps_part, int n_tiles, T* e_atom,
                                    double* forces, double fsign) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per atom: lanes stride over the atom's pairs (coalesced), FP64 warp sums
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (i >= n) return;
   if (eps_part && e_atom) {
     double e = 0;
-    for (int t = 0; t < n_tiles; ++t) e += (double)eps_part[(size_t)i * n_tiles + t];
-    e_atom[i] = (T)e;
+    for (int t = lane; t < n_tiles; t += 32) e += (double)eps_part[(size_t)i * n_tiles + t];
+    e = warp_sum(e);
+    if (lane == 0) e_atom[i] = (T)e;
   }
   if (forces) {
-    double f[3] = {0, 0, 0};
+    double f0 = 0, f1 = 0, f2 = 0;
     const int beg = seg_offs[i * nsp], end = seg_offs[(i + 1) * nsp];
-    for (int p = beg; p < end; ++p) {
+    for (int p = beg + lane; p < end; p += 32) {
       const Vec4<T> a = dedr[p], b = dedr[rev[p]];
-      f[0] += (double)a.x - (double)b.x;
-      f[1] += (double)a.y - (double)b.y;
-      f[2] += (double)a.z - (double)b.z;
+      f0 += (double)a.x - (double)b.x;
+      f1 += (double)a.y - (double)b.y;
+      f2 += (double)a.z - (double)b.z;
     }
-    forces[3 * i] = fsign * f[0];
-    forces[3 * i + 1] = fsign * f[1];
-    forces[3 * i + 2] = fsign * f[2];
+    f0 = warp_sum(f0);
+    f1 = warp_sum(f1);
+    f2 = warp_sum(f2);
+    if (lane == 0) {
+      forces[3 * i] = fsign * f0;
+      forces[3 * i + 1] = fsign * f1;
+      forces[3 * i + 2] = fsign * f2;
+    }
   }
 }
 
+#define FINISH_CHUNK 2048
+
+// Partial sums of (e_atom, virial) over chunk blockIdx.y of structure blockIdx.x; a fixed
+// order of sums in both levels keeps the result deterministic.
 template <typename T>
-__global__ void struct_finish_kernel(const int64_t* __restrict__ offs, const T* __restrict__ e_atom,
-                                     const T* __restrict__ vir_atom, double* e_struct,
-                                     double* virial) {
-  const int s = blockIdx.x;
-  const int64_t a = offs[s], b = offs[s + 1];
+__global__ void struct_partial_kernel(const int64_t* __restrict__ offs, const T* __restrict__ e_atom,
+                                      const T* __restrict__ vir_atom, double* part, int chunks) {
+  const int s = blockIdx.x, c = blockIdx.y;
+  const int64_t a = offs[s] + (int64_t)c * FINISH_CHUNK;
+  const int64_t b = min(offs[s + 1], a + FINISH_CHUNK);
   double acc[10];
 #pragma unroll
   for (int t = 0; t < 10; ++t) acc[t] = 0;
@@ -57,12 +69,25 @@ __global__ void struct_finish_kernel(const int64_t* __restrict__ offs, const T* 
   if (threadIdx.x < 10) {
     double v = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
-    if (threadIdx.x == 0) {
-      if (e_struct) e_struct[s] = v;
-    } else if (virial) {
-      virial[(size_t)s * 9 + threadIdx.x - 1] = v;
-    }
+    part[((size_t)s * chunks + c) * 10 + threadIdx.x] = v;
   }
+}
+
+__global__ void struct_total_kernel(int n_struct, int chunks, const double* __restrict__ part,
+                                    double* e_struct, double* virial) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_struct) return;
+  double acc[10];
+  for (int t = 0; t < 10; ++t) acc[t] = 0;
+  for (int c = 0; c < chunks; ++c)
+    for (int t = 0; t < 10; ++t) acc[t] += part[((size_t)s * chunks + c) * 10 + t];
+  if (e_struct) e_struct[s] = acc[0];
+  if (virial)
+    for (int t = 0; t < 9; ++t) virial[(size_t)s * 9 + t] = acc[1 + t];
+}
+
+int sg_finish_chunks(int max_struct_atoms) {
+  return max_struct_atoms <= 0 ? 1 : (max_struct_atoms + FINISH_CHUNK - 1) / FINISH_CHUNK;
 }
 
 template <typename T>
@@ -70,24 +95,25 @@ cudaError_t sg_finish(int n_atoms, int n_struct, int nsp, const int64_t* atom_of
                       const int* seg_offs, const int* rev, const Vec4<T>* dedr,
                       const T* eps_part, int n_tiles, const T* vir_atom, T* e_atom,
                       double* e_struct, double* forces, double* virial, bool sign_force,
-                      cudaStream_t st) {
+                      int chunks, double* part, cudaStream_t st) {
   if (n_atoms > 0 && ((eps_part && e_atom) || forces)) {
-    atom_finish_kernel<T><<<(n_atoms + 127) / 128, 128, 0, st>>>(
+    atom_finish_kernel<T><<<(n_atoms * 32 + 255) / 256, 256, 0, st>>>(
         n_atoms, nsp, seg_offs, rev, dedr, eps_part, n_tiles, e_atom, forces,
         sign_force ? 1.0 : -1.0);
     ++sg_kernel_launches;
   }
   if (n_struct > 0 && (e_struct || virial)) {
-    struct_finish_kernel<T><<<n_struct, 256, 0, st>>>(atom_offs_dev, e_struct ? e_atom : nullptr,
-                                                      virial ? vir_atom : nullptr, e_struct, virial);
-    ++sg_kernel_launches;
+    struct_partial_kernel<T><<<dim3(n_struct, chunks), 256, 0, st>>>(
+        atom_offs_dev, e_struct ? e_atom : nullptr, virial ? vir_atom : nullptr, part, chunks);
+    struct_total_kernel<<<(n_struct + 127) / 128, 128, 0, st>>>(n_struct, chunks, part, e_struct, virial);
+    sg_kernel_launches += 2;
   }
   return cudaGetLastError();
 }
 
 template cudaError_t sg_finish<float>(int, int, int, const int64_t*, const int*, const int*,
                                       const Vec4<float>*, const float*, int, const float*, float*,
-                                      double*, double*, double*, bool, cudaStream_t);
+                                      double*, double*, double*, bool, int, double*, cudaStream_t);
 template cudaError_t sg_finish<double>(int, int, int, const int64_t*, const int*, const int*,
                                        const Vec4<double>*, const double*, int, const double*,
-                                       double*, double*, double*, double*, bool, cudaStream_t);
+                                       double*, double*, double*, double*, bool, int, double*, cudaStream_t);

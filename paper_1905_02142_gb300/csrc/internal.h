@@ -36,7 +36,8 @@ cudaError_t sg_central_terms(const DevParams& p, const BasisConst<double>& W, do
 struct NbrBuffers {
   const StructGeom* geom;    // [S]
   const int* atom_struct;    // [N]
-  int* atom_bin;             // [N]
+  int* atom_bin;             // [N] flattened bin index
+  int4* atom_bin4;           // [N] bin coordinates within the structure's grid, and the index
   int* atom_slot;            // [N]
   int* bin_count;            // [nbins]
   int* bin_start;            // [nbins + 1]
@@ -44,6 +45,9 @@ struct NbrBuffers {
   int* seg_count;            // [N*nsp]
   int* seg_offs;             // [N*nsp + 1]
   float4* binpos;            // [N] FP32 positions in bin order, .w = atom index
+  float4* binpos_lo;         // [N] x - (double)binpos.xyz in bin order (double-float low words)
+  float4* atom_hi;           // [N] FP32 positions, atom order
+  float4* atom_lo;           // [N] their low words
   unsigned long long* key_tmp;  // [cap]
   void* r_tmp;               // [cap] Vec4<T>, unsorted
   unsigned long long* key;   // [cap]
@@ -141,9 +145,11 @@ template <typename T> cudaError_t sg_pair_adjoint(const AdjArgs<T>& a, int cls, 
                                                   cudaStream_t st);
 
 // ---------------------------------------------------------------- forces.cu
+// chunks per structure of the two-level per-structure sums (part: [S][chunks][10] doubles)
+int sg_finish_chunks(int max_struct_atoms);
 template <typename T>
 cudaError_t sg_finish(int n_atoms, int n_struct, int nsp, const int64_t* atom_offs_dev,
                       const int* seg_offs, const int* rev, const Vec4<T>* dedr,
                       const T* eps_part, int n_tiles, const T* vir_atom, T* e_atom,
                       double* e_struct, double* forces, double* virial, bool sign_force,
-                      cudaStream_t st);
+                      int chunks, double* part, cudaStream_t st);

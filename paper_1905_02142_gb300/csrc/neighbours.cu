@@ -124,6 +124,7 @@ __global__ void bin_assign(const double* __restrict__ pos, int n, NbrBuffers b) 
   if (bad) atomicOr(b.err, SG_ERR_OUTSIDE_CELL);
   int id = g.bin_off + (bi[0] * g.nb[1] + bi[1]) * g.nb[2] + bi[2];
   b.atom_bin[i] = id;
+  b.atom_bin4[i] = make_int4(bi[0], bi[1], bi[2], id);
   b.atom_slot[i] = atomicAdd(&b.bin_count[id], 1);
 }
 
@@ -132,8 +133,13 @@ __global__ void bin_fill(const double* __restrict__ pos, int n, NbrBuffers b, fl
   if (i >= n) return;
   int at = b.bin_start[b.atom_bin[i]] + b.atom_slot[i];
   b.bin_atoms[at] = i;
-  binpos[at] = make_float4((float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2],
-                           __int_as_float(i));
+  const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+  const float xh = (float)x, yh = (float)y, zh = (float)z;
+  const float4 lo = make_float4((float)(x - (double)xh), (float)(y - (double)yh), (float)(z - (double)zh), 0.f);
+  binpos[at] = make_float4(xh, yh, zh, __int_as_float(i));
+  b.binpos_lo[at] = lo;
+  b.atom_hi[i] = make_float4(xh, yh, zh, 0.f);
+  b.atom_lo[i] = lo;
 }
 
 cudaError_t sg_nbr_bin(const double* pos, int n_atoms, int n_bins, const NbrBuffers& b,
@@ -153,38 +159,65 @@ cudaError_t sg_nbr_bin(const double* pos, int n_atoms, int n_bins, const NbrBuff
 }
 
 // ---------------------------------------------------------------- pair search
-__device__ __forceinline__ int floor_div(int a, int n) { return a >= 0 ? a / n : -((-a + n - 1) / n); }
-
 __device__ __forceinline__ bool lex_positive(int s1, int s2, int s3) {
   return s1 > 0 || (s1 == 0 && (s2 > 0 || (s2 == 0 && s3 > 0)));
 }
 
-// FP64 shift vector s = (S1*h1 + S2*h2) + S3*h3, fixed order, no FMA
-__device__ __forceinline__ void shift_vec(const StructGeom& g, int S1, int S2, int S3, double s[3]) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-    s[c] = __dadd_rn(__dadd_rn(__dmul_rn((double)S1, g.h[c]), __dmul_rn((double)S2, g.h[3 + c])),
-                     __dmul_rn((double)S3, g.h[6 + c]));
+// ---- double-float (hi + lo FP32) arithmetic, exact error terms by TwoSum / TwoProd
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (a_hi + a_lo) + (b_hi + b_lo), renormalised
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& sh, float& sl) {
+  float s, e;
+  two_sum(ah, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(al, bl));
+  two_sum(s, e, sh, sl);
+}
+// image shift S.h in double-float from the split lattice vectors (S integer, |S| < 2^8)
+__device__ __forceinline__ void df_shift(const StructGeom& g, float f1, float f2, float f3, int c, float& sh,
+                                         float& sl) {
+  float ph = __fmul_rn(f1, g.h32[c]), pl = __fmaf_rn(f1, g.h32[c], -ph);  // exact product
+  pl = __fmaf_rn(f1, g.h32lo[c], pl);
+  float qh = __fmul_rn(f2, g.h32[3 + c]), ql = __fmaf_rn(f2, g.h32[3 + c], -qh);
+  ql = __fmaf_rn(f2, g.h32lo[3 + c], ql);
+  float rh = __fmul_rn(f3, g.h32[6 + c]), rl = __fmaf_rn(f3, g.h32[6 + c], -rh);
+  rl = __fmaf_rn(f3, g.h32lo[6 + c], rl);
+  float th, tl;
+  df_add(ph, pl, qh, ql, th, tl);
+  df_add(th, tl, rh, rl, sh, sl);
 }
 
-// exact FP64 separation (fixed operation order, no FMA) in canonical orientation
-__device__ __forceinline__ void exact_sep(const double* __restrict__ pos, int i, int j,
-                                         const StructGeom& g, int S1, int S2, int S3, bool canon,
-                                         double r[3], double& d2) {
-  double s[3];
-  shift_vec(g, S1, S2, S3, s);
+// bin coordinate t (possibly outside [0, n)) -> periodic bin and image index, no division
+__device__ __forceinline__ void wrap(int t, int n, int& bin, int& S, float& Sf) {
+  S = 0;
+  while (t < 0) { t += n; --S; }
+  while (t >= n) { t -= n; ++S; }
+  bin = t;
+  Sf = (float)S;
+}
+
+// exact FP64 separation (fixed operation order, no FMA) in canonical orientation, from the
+// FP64 shift s = (S1*h1 + S2*h2) + S3*h3
+__device__ __forceinline__ void exact_sep(const double* __restrict__ pos, int i, int j, const double s[3],
+                                         bool canon, double r[3], double& d2) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    double xi = pos[3 * i + c], xj = pos[3 * j + c];
+    const double xi = pos[3 * i + c], xj = pos[3 * j + c];
     r[c] = canon ? __dsub_rn(__dadd_rn(xj, s[c]), xi) : -__dsub_rn(__dadd_rn(xi, -s[c]), xj);
   }
   d2 = __dadd_rn(__dadd_rn(__dmul_rn(r[0], r[0]), __dmul_rn(r[1], r[1])), __dmul_rn(r[2], r[2]));
 }
 
 // Visit every kept pair of atom i; lanes of the warp take candidates in parallel.
-// fn(lane_has_pair, j, S1, S2, S3, r[3], d2) is called by all lanes together; d2 < 0 marks a
-// pair kept by the FP32 test whose exact FP64 separation has not been computed.
-// The FP32 shift uses the FP32 lattice vectors; the rounding margin covers that too.
+// fn(lane_has_pair, j, k, S1, S2, S3, f1, f2, f3, s[3], r[3], d2) is called by all lanes
+// together (k: the candidate's slot in bin order, f = (float)S), with the
+// FP64 shift s of this image; d2 < 0 marks a pair kept by the FP32 test whose exact FP64
+// separation has not been computed.  The FP32 test uses FP32 positions and the FP32
+// lattice vectors; the rounding margin covers both.  FP64 work (slow on this GPU) is done
+// only where needed: the shift once per image by one lane, separations for kept pairs.
 template <typename Fn>
 __device__ __forceinline__ void visit_pairs(const double* __restrict__ pos, const float4* binpos,
                                             int i, double rc, const NbrBuffers& b, Fn&& fn) {
@@ -194,15 +227,19 @@ __device__ __forceinline__ void visit_pairs(const double* __restrict__ pos, cons
   const float rc2f = (float)rc2;
   const float margin = g.margin;
   const float xi = (float)pos[3 * i], yi = (float)pos[3 * i + 1], zi = (float)pos[3 * i + 2];
-  const int bin = b.atom_bin[i] - g.bin_off;
-  const int c0 = bin / (g.nb[1] * g.nb[2]), c1 = (bin / g.nb[2]) % g.nb[1], c2 = bin % g.nb[2];
+  const int4 cb = b.atom_bin4[i];
   for (int d0 = -g.m[0]; d0 <= g.m[0]; ++d0) {
-    const int t0 = c0 + d0, S1 = floor_div(t0, g.nb[0]), b0 = t0 - S1 * g.nb[0];
+    int b0, S1;
+    float f1;
+    wrap(cb.x + d0, g.nb[0], b0, S1, f1);
     for (int d1 = -g.m[1]; d1 <= g.m[1]; ++d1) {
-      const int t1 = c1 + d1, S2 = floor_div(t1, g.nb[1]), b1 = t1 - S2 * g.nb[1];
+      int b1, S2;
+      float f2;
+      wrap(cb.y + d1, g.nb[1], b1, S2, f2);
       for (int d2i = -g.m[2]; d2i <= g.m[2]; ++d2i) {
-        const int t2 = c2 + d2i, S3 = floor_div(t2, g.nb[2]), b2 = t2 - S3 * g.nb[2];
-        const float f1 = (float)S1, f2 = (float)S2, f3 = (float)S3;
+        int b2, S3;
+        float f3;
+        wrap(cb.z + d2i, g.nb[2], b2, S3, f3);
         const float sx = __fadd_rn(__fadd_rn(__fmul_rn(f1, g.h32[0]), __fmul_rn(f2, g.h32[3])), __fmul_rn(f3, g.h32[6]));
         const float sy = __fadd_rn(__fadd_rn(__fmul_rn(f1, g.h32[1]), __fmul_rn(f2, g.h32[4])), __fmul_rn(f3, g.h32[7]));
         const float sz = __fadd_rn(__fadd_rn(__fmul_rn(f1, g.h32[2]), __fmul_rn(f2, g.h32[5])), __fmul_rn(f3, g.h32[8]));
@@ -210,11 +247,12 @@ __device__ __forceinline__ void visit_pairs(const double* __restrict__ pos, cons
         const int beg = b.bin_start[tb], end = b.bin_start[tb + 1];
         const bool zero_shift = (S1 == 0 && S2 == 0 && S3 == 0);
         const bool lexpos = lex_positive(S1, S2, S3);
+        double s[3] = {0.0, 0.0, 0.0};
+        bool have_s = false;
         for (int base = beg; base < end; base += 32) {
           const int k = base + lane;
-          bool keep = false;
           int j = -1;
-          double r[3] = {0, 0, 0}, d2 = 0;
+          bool cand = false, exact = false;
           if (k < end) {
             const float4 pj = binpos[k];
             j = __float_as_int(pj.w);
@@ -224,27 +262,54 @@ __device__ __forceinline__ void visit_pairs(const double* __restrict__ pos, cons
               const float dy = __fsub_rn(__fadd_rn(pj.y, sy), yi);
               const float dz = __fsub_rn(__fadd_rn(pj.z, sz), zi);
               const float d2f = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-              const bool near_cut = fabsf(d2f - rc2f) <= margin;
-              const bool near_zero = d2f <= margin;
-              if (near_cut || near_zero || d2f < rc2f) {
-                if (near_cut || near_zero) {
-                  const bool canon = (j > i) || (j == i && lexpos);
-                  exact_sep(pos, i, j, g, S1, S2, S3, canon, r, d2);
-                  keep = d2 < rc2;
-                  if (keep && d2 == 0.0) atomicOr(b.err, SG_ERR_COINCIDENT);
-                } else {
-                  keep = true;
-                  d2 = -1.0;  // exact value computed on demand by the caller
-                }
-              }
+              exact = fabsf(d2f - rc2f) <= margin || d2f <= margin;
+              cand = exact || d2f < rc2f;
             }
           }
-          fn(keep, j, S1, S2, S3, r, d2);
+          if (!have_s && __any_sync(0xffffffffu, exact || (cand && Fn::kNeedsShift))) {
+            if (lane == 0) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c)
+                s[c] = __dadd_rn(__dadd_rn(__dmul_rn((double)S1, g.h[c]), __dmul_rn((double)S2, g.h[3 + c])),
+                                 __dmul_rn((double)S3, g.h[6 + c]));
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) s[c] = __shfl_sync(0xffffffffu, s[c], 0);
+            have_s = true;
+          }
+          bool keep = false;
+          double r[3] = {0, 0, 0}, d2 = -1.0;
+          if (cand) {
+            if (exact) {
+              const bool canon = (j > i) || (j == i && lexpos);
+              exact_sep(pos, i, j, s, canon, r, d2);
+              keep = d2 < rc2;
+              if (keep && d2 == 0.0) atomicOr(b.err, SG_ERR_COINCIDENT);
+            } else {
+              keep = true;  // exact value computed on demand by the caller
+            }
+          }
+          fn(keep, j, k, S1, S2, S3, f1, f2, f3, s, r, d2);
         }
       }
     }
   }
 }
+
+// per-lane pair counts by neighbour species
+struct Count {
+  static constexpr bool kNeedsShift = false;
+  int* cnt;
+  const int* species;
+  __device__ void operator()(bool keep, int j, int, int, int, int, float, float, float, const double*,
+                             const double*, double) const {
+    if (keep) {
+      const int sj = species[j];
+#pragma unroll
+      for (int s = 0; s < SG_MAX_SPECIES; ++s) cnt[s] += (s == sj);
+    }
+  }
+};
 
 __global__ void count_kernel(const double* __restrict__ pos, const int* __restrict__ species,
                              int n, int nsp, double rc, NbrBuffers b, const float4* binpos) {
@@ -255,14 +320,7 @@ __global__ void count_kernel(const double* __restrict__ pos, const int* __restri
   int cnt[SG_MAX_SPECIES];
 #pragma unroll
   for (int s = 0; s < SG_MAX_SPECIES; ++s) cnt[s] = 0;
-  visit_pairs(pos, binpos, i, rc, b,
-              [&](bool keep, int j, int, int, int, const double*, double) {
-                if (keep) {
-                  const int sj = species[j];
-#pragma unroll
-                  for (int s = 0; s < SG_MAX_SPECIES; ++s) cnt[s] += (s == sj);
-                }
-              });
+  visit_pairs(pos, binpos, i, rc, b, Count{cnt, species});
   for (int s = 0; s < nsp; ++s) {
     int v = warp_sum(cnt[s]);
     if (lane == 0) b.seg_count[i * nsp + s] = v;
@@ -288,6 +346,78 @@ __device__ __forceinline__ unsigned long long pair_key(int j, int s1, int s2, in
          ((unsigned long long)(s2 + 128) << 8) | (unsigned long long)(s3 + 128);
 }
 
+// writes each kept pair at its place in the (centre, species) segment
+template <typename T>
+struct Fill {
+  // FP64 work is slow on this GPU (a warp instruction holds the FP64 pipe whatever its
+  // active lanes): the FP32 path builds kept separations in double-float arithmetic and
+  // needs the FP64 shift only for candidates within the rounding margin.
+  static constexpr bool kNeedsShift = sizeof(T) == 8;
+  int i, nsp, lane;
+  long long cap;
+  int* next;
+  const double* pos;
+  const int* species;
+  const NbrBuffers* b;
+  Vec4<T>* rout;
+  __device__ void operator()(bool keep, int j, int k, int S1, int S2, int S3, float f1, float f2, float f3,
+                             const double* s, const double* r0, double d2) const {
+    const int sj = keep ? species[j] : -1;
+    for (int sp = 0; sp < nsp; ++sp) {
+      const unsigned mask = __ballot_sync(0xffffffffu, keep && sj == sp);
+      if (keep && sj == sp) {
+        const int at = next[sp] + __popc(mask & ((1u << lane) - 1u));
+        const bool canon = (j > i) || (j == i && lex_positive(S1, S2, S3));
+        Vec4<T> v;
+        if constexpr (sizeof(T) == 4) {
+          if (d2 >= 0.0) {
+            v.x = (float)r0[0];
+            v.y = (float)r0[1];
+            v.z = (float)r0[2];
+          } else {
+            // canonical r = (x_j + s) - x_i, else r = -((x_i - s) - x_j): exact antisymmetry
+            const float4 jh = b->binpos[k], jl = b->binpos_lo[k];
+            const float4 ih = b->atom_hi[i], il = b->atom_lo[i];
+            const StructGeom& g = b->geom[b->atom_struct[i]];
+            const float sg = canon ? 1.f : -1.f;
+            const float ah[3] = {canon ? jh.x : ih.x, canon ? jh.y : ih.y, canon ? jh.z : ih.z};
+            const float al[3] = {canon ? jl.x : il.x, canon ? jl.y : il.y, canon ? jl.z : il.z};
+            const float bh[3] = {canon ? ih.x : jh.x, canon ? ih.y : jh.y, canon ? ih.z : jh.z};
+            const float bl[3] = {canon ? il.x : jl.x, canon ? il.y : jl.y, canon ? il.z : jl.z};
+            float out[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              float sh, sl, th, tl, uh, ul;
+              df_shift(g, sg * f1, sg * f2, sg * f3, c, sh, sl);
+              df_add(ah[c], al[c], sh, sl, th, tl);
+              df_add(th, tl, -bh[c], -bl[c], uh, ul);
+              out[c] = sg * __fadd_rn(uh, ul);
+            }
+            v.x = out[0];
+            v.y = out[1];
+            v.z = out[2];
+          }
+          v.w = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
+        } else {
+          double r[3] = {r0[0], r0[1], r0[2]};
+          if (d2 < 0.0) exact_sep(pos, i, j, s, canon, r, d2);
+          v.x = r[0];
+          v.y = r[1];
+          v.z = r[2];
+          v.w = sqrt(d2);
+        }
+        if (at < cap) {
+          b->key_tmp[at] = pair_key(j, S1, S2, S3);
+          rout[at] = v;
+        } else {
+          atomicOr(b->err, SG_ERR_PAIR_CAPACITY);
+        }
+      }
+      next[sp] += __popc(mask);
+    }
+  }
+};
+
 template <typename T>
 __global__ void fill_kernel(const double* __restrict__ pos, const int* __restrict__ species,
                             int n, int nsp, double rc, long long cap, NbrBuffers b,
@@ -298,32 +428,7 @@ __global__ void fill_kernel(const double* __restrict__ pos, const int* __restric
   const int i = warp;
   int next[SG_MAX_SPECIES];
   for (int s = 0; s < nsp; ++s) next[s] = b.seg_offs[i * nsp + s];
-  visit_pairs(pos, binpos, i, rc, b,
-              [&](bool keep, int j, int S1, int S2, int S3, const double* r0, double d2) {
-                int sj = keep ? species[j] : -1;
-                for (int sp = 0; sp < nsp; ++sp) {
-                  const unsigned mask = __ballot_sync(0xffffffffu, keep && sj == sp);
-                  if (keep && sj == sp) {
-                    const int at = next[sp] + __popc(mask & ((1u << lane) - 1u));
-                    double r[3] = {r0[0], r0[1], r0[2]};
-                    if (d2 < 0.0) {
-                      const bool canon = (j > i) || (j == i && lex_positive(S1, S2, S3));
-                      exact_sep(pos, i, j, b.geom[b.atom_struct[i]], S1, S2, S3, canon, r, d2);
-                    }
-                    if (at < cap) {
-                      b.key_tmp[at] = pair_key(j, S1, S2, S3);
-                      Vec4<T> v;
-                      v.x = (T)r[0]; v.y = (T)r[1]; v.z = (T)r[2];
-                      if constexpr (sizeof(T) == 4) v.w = sqrtf((float)d2);  // FP32 length, mixed path
-                      else v.w = sqrt(d2);
-                      rout[at] = v;
-                    } else {
-                      atomicOr(b.err, SG_ERR_PAIR_CAPACITY);
-                    }
-                  }
-                  next[sp] += __popc(mask);
-                }
-              });
+  visit_pairs(pos, binpos, i, rc, b, Fill<T>{i, nsp, lane, cap, next, pos, species, &b, rout});
 }
 
 // rank sort inside each (centre, species) segment, then keys -> j and sorted vectors

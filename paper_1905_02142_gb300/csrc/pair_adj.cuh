@@ -47,7 +47,8 @@ __device__ __forceinline__ void pair_index(int pc, int nch, int& c1, int& c2) {
   c2 = c + rem;
 }
 
-template <typename T, int NC, int LC, bool TABLE>
+// EXACT: n_max == NC and l_max == LC, so the runtime size guards compile away.
+template <typename T, int NC, int LC, bool TABLE, bool EXACT>
 __global__ void __launch_bounds__(SG_WARPS * 32)
 pair_adj_kernel(const AdjArgs<T> a, int smem_per_warp) {
   constexpr int NP = (NC + 3) / 4 * 4;
@@ -152,15 +153,34 @@ pair_adj_kernel(const AdjArgs<T> a, int smem_per_warp) {
         T srad = 0, hx = 0, hy = 0, hz = 0;
         for_each_ylm_grad<T, LC>(ux, uy, uz, a.yc,
             [&](int l, int m, T y, T gx, T gy, T gz) {
-              if (l > a.lmax) return;
+              if (!EXACT && l > a.lmax) return;
               const T* grow = Gsp + (size_t)lm_index(l, m) * NP;
-              T u0 = 0, u1 = 0;
+              T gr[NP];
+              if constexpr (sizeof(T) == 4) {
 #pragma unroll
-              for (int n = 0; n < NC; ++n) {
-                const T gv = grow[n];
-                u0 = fma(gv, bn[n], u0);
-                u1 = fma(gv, dbn[n], u1);
+                for (int n = 0; n < NP; n += 4) {
+                  const float4 g4 = *reinterpret_cast<const float4*>(grow + n);
+                  gr[n] = g4.x; gr[n + 1] = g4.y; gr[n + 2] = g4.z; gr[n + 3] = g4.w;
+                }
+              } else {
+#pragma unroll
+                for (int n = 0; n < NP; n += 2) {
+                  const double2 g2 = *reinterpret_cast<const double2*>(grow + n);
+                  gr[n] = g2.x; gr[n + 1] = g2.y;
+                }
               }
+              T u0 = 0, u1 = 0, v0 = 0, v1 = 0;  // two chains each, halving the FMA latency chain
+#pragma unroll
+              for (int n = 0; n < NC; n += 2) {
+                u0 = fma(gr[n], bn[n], u0);
+                u1 = fma(gr[n], dbn[n], u1);
+                if (n + 1 < NC) {
+                  v0 = fma(gr[n + 1], bn[n + 1], v0);
+                  v1 = fma(gr[n + 1], dbn[n + 1], v1);
+                }
+              }
+              u0 += v0;
+              u1 += v1;
               srad = fma(fma(u1, il[l], u0 * dil[l]), y, srad);
               const T wv = u0 * il[l];
               hx = fma(wv, gx, hx);
@@ -190,8 +210,8 @@ pair_adj_kernel(const AdjArgs<T> a, int smem_per_warp) {
   }
 }
 
-template <typename T, int NC, int LC, bool TABLE>
-static cudaError_t launch_adj(const AdjArgs<T>& a, cudaStream_t st) {
+template <typename T, int NC, int LC, bool TABLE, bool EXACT>
+static cudaError_t launch_adj_v(const AdjArgs<T>& a, cudaStream_t st) {
   constexpr int NP = (NC + 3) / 4 * 4;
   const int L = (a.lmax + 1) * (a.lmax + 1);
   const int nch = a.nsp * a.nmax;
@@ -199,7 +219,7 @@ static cudaError_t launch_adj(const AdjArgs<T>& a, cudaStream_t st) {
   per_warp = (per_warp + 3) / 4 * 4;
   const size_t smem = (size_t)SG_WARPS * per_warp * sizeof(T);
   if (smem > 220 * 1024) return cudaErrorInvalidConfiguration;
-  auto kern = pair_adj_kernel<T, NC, LC, TABLE>;
+  auto kern = pair_adj_kernel<T, NC, LC, TABLE, EXACT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
@@ -214,6 +234,12 @@ static cudaError_t launch_adj(const AdjArgs<T>& a, cudaStream_t st) {
   kern<<<(unsigned)grid, SG_WARPS * 32, smem, st>>>(a, per_warp);
   ++sg_kernel_launches;
   return cudaGetLastError();
+}
+
+template <typename T, int NC, int LC, bool TABLE>
+static cudaError_t launch_adj(const AdjArgs<T>& a, cudaStream_t st) {
+  if (a.nmax == NC && a.lmax == LC) return launch_adj_v<T, NC, LC, TABLE, true>(a, st);
+  return launch_adj_v<T, NC, LC, TABLE, false>(a, st);
 }
 
 template <typename T>

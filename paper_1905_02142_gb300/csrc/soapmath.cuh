@@ -225,56 +225,51 @@ __device__ __forceinline__ void for_each_ylm(T x, T y, T z, const YlmCoef<T>& yc
 
 // Same traversal with the gradient of the polynomial extension P_lm(x, y, z) with respect
 // to u (its projection on the tangent plane, divided by r, is grad_r Y_lm(r_hat)).
+// Column m of N~ and column m+1 (for dN~_l^m/dz) are both run as scalar recursions in l,
+// so that with the loops unrolled every index is a compile-time constant.
 template <typename T, int LC, typename F>
 __device__ __forceinline__ void for_each_ylm_grad(T x, T y, T z, const YlmCoef<T>& yc, F&& f) {
   T cm = 1, sm = 0, cmm1 = 0, smm1 = 0;
-  T nxt[LC + 2];  // column m+1 of N~ (index l)
-  T cur[LC + 2];  // column m
-  // column 0
-#pragma unroll
-  for (int l = 0; l <= LC + 1; ++l) cur[l] = 0;
-  {
-    T p2 = 0, p1 = yc.seed[0];
-#pragma unroll
-    for (int l = 0; l <= LC; ++l) {
-      T pl = (l == 0) ? p1 : (l == 1 ? yc.s1[0] * z * p1 : yc.a[l][0] * z * p1 - yc.b[l][0] * p2);
-      if (l > 0) { p2 = p1; p1 = pl; }
-      cur[l] = pl;
-    }
-  }
 #pragma unroll
   for (int m = 0; m <= LC; ++m) {
-    // column m+1
-#pragma unroll
-    for (int l = 0; l <= LC + 1; ++l) nxt[l] = 0;
-    if (m + 1 <= LC) {
-      T p2 = 0, p1 = yc.seed[m + 1];
-#pragma unroll
-      for (int l = m + 1; l <= LC; ++l) {
-        T pl = (l == m + 1) ? p1 : (l == m + 2 ? yc.s1[m + 1] * z * p1 : yc.a[l][m + 1] * z * p1 - yc.b[l][m + 1] * p2);
-        if (l > m + 1) { p2 = p1; p1 = pl; }
-        nxt[l] = pl;
-      }
-    }
     if (m > 0) {
-      T c2 = x * cm - y * sm;
-      T s2 = x * sm + y * cm;
-      cmm1 = cm; smm1 = sm;
-      cm = c2; sm = s2;
+      const T c2 = x * cm - y * sm;
+      const T s2 = x * sm + y * cm;
+      cmm1 = cm;
+      smm1 = sm;
+      cm = c2;
+      sm = s2;
     }
+    T a2 = 0, a1 = yc.seed[m];                        // column m
+    T b2 = 0, b1 = (m + 1 <= LC) ? yc.seed[m + 1] : T(0);  // column m+1
 #pragma unroll
     for (int l = m; l <= LC; ++l) {
-      T pl = cur[l];
-      T dz = yc.d[l][m] * nxt[l];  // dN~_l^m/dz
+      T pl;
+      if (l == m) {
+        pl = a1;
+      } else {
+        pl = (l == m + 1) ? yc.s1[m] * z * a1 : yc.a[l][m] * z * a1 - yc.b[l][m] * a2;
+        a2 = a1;
+        a1 = pl;
+      }
+      T ql = T(0);
+      if (m + 1 <= LC && l >= m + 1) {
+        if (l == m + 1) {
+          ql = b1;
+        } else {
+          ql = (l == m + 2) ? yc.s1[m + 1] * z * b1 : yc.a[l][m + 1] * z * b1 - yc.b[l][m + 1] * b2;
+          b2 = b1;
+          b1 = ql;
+        }
+      }
+      const T dz = yc.d[l][m] * ql;  // dN~_l^m/dz
       if (m == 0) {
         f(l, 0, pl, T(0), T(0), dz);
       } else {
-        T fm = (T)m * pl;
+        const T fm = (T)m * pl;
         f(l, m, pl * cm, fm * cmm1, -fm * smm1, dz * cm);
         f(l, -m, pl * sm, fm * smm1, fm * cmm1, dz * sm);
       }
     }
-#pragma unroll
-    for (int l = 0; l <= LC + 1; ++l) cur[l] = nxt[l];
   }
 }
