@@ -13,6 +13,8 @@
 // where P_lm is the polynomial extension of Y_lm off the sphere.  The radial derivatives
 // come from the table (Hermite derivative) or from forward-mode duals through Eq. 04.
 #pragma once
+#include <algorithm>
+
 #include "internal.h"
 #include "soapmath.cuh"
 
@@ -40,28 +42,50 @@ __device__ __forceinline__ void table_interp_d(const float* __restrict__ tab, co
   }
 }
 
-__device__ __forceinline__ void pair_index(int pc, int nch, int& c1, int& c2) {
-  int c = 0, rem = pc;
-  while (rem >= nch - c) { rem -= nch - c; ++c; }
-  c1 = c;
-  c2 = c + rem;
-}
+// Coefficients of the normalised real-harmonic recursion, staged in shared memory so that
+// the (l, m) loops below can run rolled (small code, no instruction-cache pressure).
+template <typename T> struct YlmShared {
+  T seed[SG_MAX_LMAX + 2], s1[SG_MAX_LMAX + 2];
+  T a[SG_MAX_LMAX + 1][SG_MAX_LMAX + 2], b[SG_MAX_LMAX + 1][SG_MAX_LMAX + 2];
+  T d[SG_MAX_LMAX + 1][SG_MAX_LMAX + 2];
+};
 
-// EXACT: n_max == NC and l_max == LC, so the runtime size guards compile away.
+// EXACT: n_max == NC and l_max == LC (no runtime size guards in the channel loops).
 template <typename T, int NC, int LC, bool TABLE, bool EXACT>
 __global__ void __launch_bounds__(SG_WARPS * 32)
 pair_adj_kernel(const AdjArgs<T> a, int smem_per_warp) {
   constexpr int NP = (NC + 3) / 4 * 4;
+  constexpr int LP = LC + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  YlmShared<T>& ys = *reinterpret_cast<YlmShared<T>*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  T* base_s = reinterpret_cast<T*>(smem_raw) + (size_t)warp * smem_per_warp;
+  T* base_s = reinterpret_cast<T*>(smem_raw + (sizeof(YlmShared<T>) + 15) / 16 * 16) + (size_t)warp * smem_per_warp;
   const int L = (a.lmax + 1) * (a.lmax + 1);
   const int nch = a.nsp * a.nmax;
   const int D = a.dim;
-  T* Gs = base_s;                          // [nsp][L][NP]
-  T* cs = Gs + (size_t)a.nsp * L * NP;     // [nch][L]
-  T* hs = cs + (size_t)nch * L;            // [D]
+  const int lp1 = a.lmax + 1;
+  T* Gs = base_s;                          // [nsp][L][NP]   dE/dc, one row of NP per (s, lm)
+  T* scratch = Gs + (size_t)a.nsp * L * NP;
+  T* cs = scratch;                         // prologue: [nch][L] coefficients
+  T* hs = cs + (size_t)nch * L;            //           [D] dE/dp
+  T* il_s = scratch;                       // pair loop: [LP][32] ilexp, then [LP][32] d/dr
+  T* dil_s = scratch + LP * 32;
   const T FOUR_PI = (T)12.566370614359172;
+  const T SQRT2 = (T)1.4142135623730951;
+
+  // recursion coefficients -> shared memory (once per block)
+  for (int k = threadIdx.x; k <= SG_MAX_LMAX; k += blockDim.x) {
+    ys.seed[k] = a.yc.seed[k];
+    ys.s1[k] = a.yc.s1[k];
+  }
+  if (threadIdx.x == 0) { ys.seed[SG_MAX_LMAX + 1] = T(0); ys.s1[SG_MAX_LMAX + 1] = T(0); }
+  for (int k = threadIdx.x; k < (SG_MAX_LMAX + 1) * (SG_MAX_LMAX + 2); k += blockDim.x) {
+    const int l = k / (SG_MAX_LMAX + 2), m = k - l * (SG_MAX_LMAX + 2);
+    ys.a[l][m] = m <= SG_MAX_LMAX ? a.yc.a[l][m] : T(0);
+    ys.b[l][m] = m <= SG_MAX_LMAX ? a.yc.b[l][m] : T(0);
+    ys.d[l][m] = m <= SG_MAX_LMAX ? a.yc.d[l][m] : T(0);
+  }
+  __syncthreads();
 
   for (int atom = blockIdx.x * SG_WARPS + warp; atom < a.n_atoms; atom += gridDim.x * SG_WARPS) {
     // ---- prologue: dE/dc in shared memory
@@ -76,25 +100,31 @@ pair_adj_kernel(const AdjArgs<T> a, int smem_per_warp) {
     const T* ci = a.c + (size_t)atom * nch * L;
     for (int k = lane; k < nch * L; k += 32) cs[k] = ci[k];
     __syncwarp();
-    const int lp1 = a.lmax + 1;
-    const T SQRT2 = (T)1.4142135623730951;
-    for (int k = lane; k < nch * L; k += 32) {
-      const int c1 = k / L, lm = k - c1 * L;
-      int l = 0;
-      while ((l + 1) * (l + 1) <= lm) ++l;
-      T acc = 0;
-      for (int c2 = 0; c2 < nch; ++c2) {
-        const int lo = c1 < c2 ? c1 : c2, hi = c1 < c2 ? c2 : c1;
-        const int pc = lo * nch - lo * (lo - 1) / 2 + (hi - lo);
-        const T hv = hs[pc * lp1 + l];
-        const T mcoef = (c1 == c2) ? T(2) * hv : SQRT2 * hv;
-        acc += mcoef * cs[c2 * L + lm];
+    // G[c1][lm] = sum_c2 M_l[c1][c2] c[c2][lm]; packed pair (c1<=c2) index = rowoff(c1) + c2
+    for (int lm = lane; lm < L; lm += 32) {
+      const int l = (int)sqrtf((float)lm + 0.5f);
+      for (int s = 0; s < a.nsp; ++s) {
+        T acc[NC];
+#pragma unroll
+        for (int n = 0; n < NC; ++n) acc[n] = T(0);
+        for (int c2 = 0; c2 < nch; ++c2) {
+          const T cv = cs[c2 * L + lm];
+          const int roff2 = c2 * nch - c2 * (c2 + 1) / 2;  // pc(c2, c1) = roff2 + c1 for c1 >= c2
+#pragma unroll
+          for (int n = 0; n < NC; ++n) {
+            if (EXACT || n < a.nmax) {
+              const int c1 = s * a.nmax + n;
+              const int pc = c1 >= c2 ? roff2 + c1 : c1 * nch - c1 * (c1 + 1) / 2 + c2;
+              const T hv = hs[pc * lp1 + l];
+              acc[n] = fma(c1 == c2 ? T(2) * hv : SQRT2 * hv, cv, acc[n]);
+            }
+          }
+        }
+        T* grow = Gs + ((size_t)s * L + lm) * NP;
+#pragma unroll
+        for (int n = 0; n < NP; ++n) grow[n] = (n < NC && (EXACT || n < a.nmax)) ? acc[n] : T(0);
       }
-      const int s = c1 / a.nmax, n = c1 - s * a.nmax;
-      Gs[((size_t)s * L + lm) * NP + n] = acc;
     }
-    for (int k = lane; k < a.nsp * L; k += 32)
-      for (int n = a.nmax; n < NP; ++n) Gs[(size_t)k * NP + n] = T(0);
     __syncwarp();
     if constexpr (!TABLE) {
       // G_alpha = W^T G_n (lane-local per (s, lm) row)
@@ -113,7 +143,7 @@ pair_adj_kernel(const AdjArgs<T> a, int smem_per_warp) {
       __syncwarp();
     }
 
-    // ---- pairs
+    // ---- pairs: one lane per pair; the (l, m) loop runs rolled
     T vir[9];
 #pragma unroll
     for (int t = 0; t < 9; ++t) vir[t] = 0;
@@ -121,18 +151,26 @@ pair_adj_kernel(const AdjArgs<T> a, int smem_per_warp) {
       const int beg = a.seg_offs[atom * a.nsp + s];
       const int end = a.seg_offs[atom * a.nsp + s + 1];
       const T* Gsp = Gs + (size_t)s * L * NP;
-      for (int pidx = beg + lane; pidx < end; pidx += 32) {
-        const Vec4<T> v = a.pair_r[pidx];
-        const T r = v.w, inv = T(1) / r;
-        const T ux = v.x * inv, uy = v.y * inv, uz = v.z * inv;
-        T bn[NC], dbn[NC], il[LC + 1], dil[LC + 1];
+      for (int pbase = beg; pbase < end; pbase += 32) {
+        const int pidx = pbase + lane;
+        const bool valid = pidx < end;
+        __syncwarp();
+        T bn[NC], dbn[NC];
+        T ux = 0, uy = 0, uz = 1, r = 1, inv = 1;
+        Vec4<T> v{};
+        if (valid) {
+          v = a.pair_r[pidx];
+          r = v.w;
+          inv = T(1) / r;
+          ux = v.x * inv; uy = v.y * inv; uz = v.z * inv;
+        }
         if constexpr (TABLE) {
           float f[NC + LC + 1], df[NC + LC + 1];
           table_interp_d<NC, LC>(a.table, a.ti, (float)r, f, df);
 #pragma unroll
           for (int n = 0; n < NC; ++n) { bn[n] = f[n]; dbn[n] = df[n]; }
 #pragma unroll
-          for (int l = 0; l <= LC; ++l) { il[l] = f[NC + l]; dil[l] = df[NC + l]; }
+          for (int l = 0; l <= LC; ++l) { il_s[l * 32 + lane] = f[NC + l]; dil_s[l * 32 + lane] = df[NC + l]; }
         } else {
           using Dd = Dual<double>;
           Dd rd((double)r, 1.0);
@@ -146,59 +184,102 @@ pair_adj_kernel(const AdjArgs<T> a, int smem_per_warp) {
 #pragma unroll
           for (int l = 0; l <= LC; ++l) {
             const T wl = (l <= a.lmax) ? FOUR_PI * (T)(a.p.eq08 ? (2.0 * l + 1.0) : 1.0) : T(0);
-            il[l] = wl * (T)ild[l].v;
-            dil[l] = wl * (T)ild[l].d;
+            il_s[l * 32 + lane] = wl * (T)ild[l].v;
+            dil_s[l * 32 + lane] = wl * (T)ild[l].d;
           }
         }
         T srad = 0, hx = 0, hy = 0, hz = 0;
-        for_each_ylm_grad<T, LC>(ux, uy, uz, a.yc,
-            [&](int l, int m, T y, T gx, T gy, T gz) {
-              if (!EXACT && l > a.lmax) return;
-              const T* grow = Gsp + (size_t)lm_index(l, m) * NP;
-              T gr[NP];
-              if constexpr (sizeof(T) == 4) {
+        // one (l, m) term: u = G.b, u' = G.b'; radial and angular contributions
+        auto term = [&](int lm, T il, T dil, T y, T gx, T gy, T gz) {
+          const T* grow = Gsp + (size_t)lm * NP;
+          T gr[NP];
+          if constexpr (sizeof(T) == 4) {
 #pragma unroll
-                for (int n = 0; n < NP; n += 4) {
-                  const float4 g4 = *reinterpret_cast<const float4*>(grow + n);
-                  gr[n] = g4.x; gr[n + 1] = g4.y; gr[n + 2] = g4.z; gr[n + 3] = g4.w;
-                }
+            for (int n = 0; n < NP; n += 4) {
+              const float4 g4 = *reinterpret_cast<const float4*>(grow + n);
+              gr[n] = g4.x; gr[n + 1] = g4.y; gr[n + 2] = g4.z; gr[n + 3] = g4.w;
+            }
+          } else {
+#pragma unroll
+            for (int n = 0; n < NP; n += 2) {
+              const double2 g2 = *reinterpret_cast<const double2*>(grow + n);
+              gr[n] = g2.x; gr[n + 1] = g2.y;
+            }
+          }
+          T u0 = 0, u1 = 0, v0 = 0, v1 = 0;
+#pragma unroll
+          for (int n = 0; n < NC; n += 2) {
+            u0 = fma(gr[n], bn[n], u0);
+            u1 = fma(gr[n], dbn[n], u1);
+            if (n + 1 < NC) {
+              v0 = fma(gr[n + 1], bn[n + 1], v0);
+              v1 = fma(gr[n + 1], dbn[n + 1], v1);
+            }
+          }
+          u0 += v0;
+          u1 += v1;
+          srad = fma(fma(u1, il, u0 * dil), y, srad);
+          const T wv = u0 * il;
+          hx = fma(wv, gx, hx);
+          hy = fma(wv, gy, hy);
+          hz = fma(wv, gz, hz);
+        };
+        T cm = 1, sm = 0, cmm1 = 0, smm1 = 0;
+        const int lmax = EXACT ? LC : a.lmax;
+#pragma unroll 1
+        for (int m = 0; m <= lmax; ++m) {
+          if (m > 0) {
+            const T c2 = ux * cm - uy * sm;
+            const T s2 = ux * sm + uy * cm;
+            cmm1 = cm; smm1 = sm;
+            cm = c2; sm = s2;
+          }
+          T a2 = 0, a1 = ys.seed[m];          // column m of N~ (recursion in l)
+          T b2 = 0, b1 = ys.seed[m + 1];      // column m+1 (zero seed past the end)
+          const T fm = (T)m;
+#pragma unroll 1
+          for (int l = m; l <= lmax; ++l) {
+            T pl, ql = T(0);
+            if (l == m) {
+              pl = a1;
+            } else {
+              pl = (l == m + 1) ? ys.s1[m] * uz * a1 : ys.a[l][m] * uz * a1 - ys.b[l][m] * a2;
+              a2 = a1;
+              a1 = pl;
+              if (l == m + 1) {
+                ql = b1;
               } else {
-#pragma unroll
-                for (int n = 0; n < NP; n += 2) {
-                  const double2 g2 = *reinterpret_cast<const double2*>(grow + n);
-                  gr[n] = g2.x; gr[n + 1] = g2.y;
-                }
+                ql = (l == m + 2) ? ys.s1[m + 1] * uz * b1 : ys.a[l][m + 1] * uz * b1 - ys.b[l][m + 1] * b2;
+                b2 = b1;
+                b1 = ql;
               }
-              T u0 = 0, u1 = 0, v0 = 0, v1 = 0;  // two chains each, halving the FMA latency chain
+            }
+            const T dz = ys.d[l][m] * ql;
+            const T il = il_s[l * 32 + lane], dil = dil_s[l * 32 + lane];
+            const int l0 = l * l + l;
+            if (m == 0) {
+              term(l0, il, dil, pl, T(0), T(0), dz);
+            } else {
+              const T pm = fm * pl;
+              term(l0 + m, il, dil, pl * cm, pm * cmm1, -pm * smm1, dz * cm);
+              term(l0 - m, il, dil, pl * sm, pm * smm1, pm * cmm1, dz * sm);
+            }
+          }
+        }
+        if (valid) {
+          const T hdot = hx * ux + hy * uy + hz * uz;
+          Vec4<T> o;
+          o.x = ux * srad + (hx - hdot * ux) * inv;
+          o.y = uy * srad + (hy - hdot * uy) * inv;
+          o.z = uz * srad + (hz - hdot * uz) * inv;
+          o.w = T(0);
+          a.dedr[pidx] = o;
+          const T gvec[3] = {o.x, o.y, o.z}, rvec[3] = {v.x, v.y, v.z};
 #pragma unroll
-              for (int n = 0; n < NC; n += 2) {
-                u0 = fma(gr[n], bn[n], u0);
-                u1 = fma(gr[n], dbn[n], u1);
-                if (n + 1 < NC) {
-                  v0 = fma(gr[n + 1], bn[n + 1], v0);
-                  v1 = fma(gr[n + 1], dbn[n + 1], v1);
-                }
-              }
-              u0 += v0;
-              u1 += v1;
-              srad = fma(fma(u1, il[l], u0 * dil[l]), y, srad);
-              const T wv = u0 * il[l];
-              hx = fma(wv, gx, hx);
-              hy = fma(wv, gy, hy);
-              hz = fma(wv, gz, hz);
-            });
-        const T hdot = hx * ux + hy * uy + hz * uz;
-        Vec4<T> o;
-        o.x = ux * srad + (hx - hdot * ux) * inv;
-        o.y = uy * srad + (hy - hdot * uy) * inv;
-        o.z = uz * srad + (hz - hdot * uz) * inv;
-        o.w = T(0);
-        a.dedr[pidx] = o;
-        const T gvec[3] = {o.x, o.y, o.z}, rvec[3] = {v.x, v.y, v.z};
+          for (int p = 0; p < 3; ++p)
 #pragma unroll
-        for (int p = 0; p < 3; ++p)
-#pragma unroll
-          for (int q2 = 0; q2 < 3; ++q2) vir[3 * p + q2] -= gvec[p] * rvec[q2];
+            for (int q2 = 0; q2 < 3; ++q2) vir[3 * p + q2] -= gvec[p] * rvec[q2];
+        }
       }
     }
 #pragma unroll
@@ -215,9 +296,10 @@ static cudaError_t launch_adj_v(const AdjArgs<T>& a, cudaStream_t st) {
   constexpr int NP = (NC + 3) / 4 * 4;
   const int L = (a.lmax + 1) * (a.lmax + 1);
   const int nch = a.nsp * a.nmax;
-  int per_warp = a.nsp * L * NP + nch * L + a.dim;
+  const int scratch = std::max(nch * L + a.dim, 2 * (LC + 1) * 32);
+  int per_warp = a.nsp * L * NP + scratch;
   per_warp = (per_warp + 3) / 4 * 4;
-  const size_t smem = (size_t)SG_WARPS * per_warp * sizeof(T);
+  const size_t smem = (sizeof(YlmShared<T>) + 15) / 16 * 16 + (size_t)SG_WARPS * per_warp * sizeof(T);
   if (smem > 220 * 1024) return cudaErrorInvalidConfiguration;
   auto kern = pair_adj_kernel<T, NC, LC, TABLE, EXACT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
