@@ -206,7 +206,8 @@ extern "C" int soapgap_create(const soapgap_params* params, soapgap_handle** out
       double ht = std::min(0.02, smin / 25.0);
       h->ti.K = (int)std::ceil(p.r_cut / ht);
       h->ti.h = p.r_cut / h->ti.K;
-      h->ti.fp = (h->NC + h->LC + 1 + 3) / 4 * 4;
+      h->ti.inv_h = (float)(1.0 / h->ti.h);
+      h->ti.fp = (h->NC + 3) / 4 * 4 + (h->LC + 1 + 3) / 4 * 4;  // TableDims<NC, LC>::FP
       e = ensure(h->table, (size_t)(h->ti.K + 1) * 2 * h->ti.fp * sizeof(float));
       if (e == cudaSuccess) e = sg_build_table(h->dp, h->bc64, h->cls, h->ti, (float*)h->table.p, 0);
       if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -559,6 +560,7 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
       }
       AdjArgs<T> aa{};
       aa.n_atoms = N; aa.nsp = nsp; aa.nmax = h->prm.n_max; aa.lmax = h->prm.l_max; aa.dim = D;
+      aa.n_pairs = h->last_pairs;
       aa.species = b->species; aa.atom_struct = (const int*)h->atom_struct.p;
       aa.struct_w = (const double*)h->struct_w.p; aa.seg_offs = nb.seg_offs;
       aa.pair_r = (const Vec4<T>*)h->pair_r.p; aa.table = (const float*)h->table.p; aa.ti = h->ti;

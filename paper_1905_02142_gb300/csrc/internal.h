@@ -23,6 +23,7 @@ struct TableInfo {
   int K;         // intervals
   int fp;        // floats per half-node (values, then h*derivatives): padded NC+LC+1
   double h;      // node spacing
+  float inv_h;   // 1 / h (rounded to float)
 };
 // Builds, for r_k = k h (k = 0..K), b_n(r) in the orthonormal basis (n < nmax, padded to NC),
 // 4 pi ilexp_l(z(r)) [x (2l+1) with eq08] (l <= lmax, padded to LC+1), and h * d/dr of each.
@@ -124,6 +125,7 @@ cudaError_t sg_tc_gemm_store(const __half* A, int m, const __half* B, int n, int
 // ---------------------------------------------------------------- pair_adj.cu
 template <typename T> struct AdjArgs {
   int n_atoms, nsp, nmax, lmax, dim;
+  long long n_pairs;
   const int* species;
   const int* atom_struct;
   const double* struct_w;   // [S] dE/dE_struct
@@ -143,6 +145,8 @@ template <typename T> struct AdjArgs {
 };
 template <typename T> cudaError_t sg_pair_adjoint(const AdjArgs<T>& a, int cls, bool table,
                                                   cudaStream_t st);
+// mixed-precision (table) adjoint with the per-atom contraction on tensor cores
+cudaError_t sg_pair_adjoint_mma(const AdjArgs<float>& a, int cls, cudaStream_t st);
 
 // ---------------------------------------------------------------- forces.cu
 // chunks per structure of the two-level per-structure sums (part: [S][chunks][10] doubles)

@@ -1,5 +1,6 @@
-// Adjoint pair kernel: dE/dq -> dE/dp -> dE/dc -> dE/dr_ij for every pair, recomputing
-// the pair's radial and angular terms instead of storing dc/dr.
+// Adjoint pair kernel of the FP64 path: dE/dq -> dE/dp -> dE/dc -> dE/dr_ij for every
+// pair, recomputing the pair's radial and angular terms instead of storing dc/dr.  (The
+// mixed-precision path runs the same mathematics in pair_adj_mma.cu.)
 //
 // Per atom (one warp):
 //   h      = dE/dp = (g - q (q.g)) / |p|                          (q = p/|p|, Sec. I)
@@ -11,36 +12,12 @@
 //   dE/dr_vec = r_hat sum_lm (u'_lm il_l + u_lm il_l') Y_lm
 //             + (1/r)(I - r_hat r_hat^T) sum_lm u_lm il_l grad_u P_lm
 // where P_lm is the polynomial extension of Y_lm off the sphere.  The radial derivatives
-// come from the table (Hermite derivative) or from forward-mode duals through Eq. 04.
+// come from forward-mode duals through Eq. 04.
 #pragma once
 #include <algorithm>
 
 #include "internal.h"
 #include "soapmath.cuh"
-
-template <int NC, int LC>
-__device__ __forceinline__ void table_interp_d(const float* __restrict__ tab, const TableInfo& ti,
-                                               float r, float* f, float* df) {
-  constexpr int F = NC + LC + 1;
-  float x = r * (float)(1.0 / ti.h);
-  int k = (int)x;
-  k = k < 0 ? 0 : (k >= ti.K ? ti.K - 1 : k);
-  float t = x - (float)k;
-  const float* n0 = tab + (size_t)k * 2 * ti.fp;
-  const float* n1 = n0 + 2 * ti.fp;
-  float t2 = t * t;
-  float h00 = (2.f * t - 3.f) * t2 + 1.f, h10 = ((t - 2.f) * t + 1.f) * t;
-  float h01 = (3.f - 2.f * t) * t2, h11 = (t - 1.f) * t2;
-  float d00 = 6.f * t * (t - 1.f), d10 = (3.f * t - 4.f) * t + 1.f, d11 = (3.f * t - 2.f) * t;
-  float invh = (float)(1.0 / ti.h);
-#pragma unroll
-  for (int j = 0; j < F; ++j) {
-    float v0 = __ldg(n0 + j), g0 = __ldg(n0 + ti.fp + j);
-    float v1 = __ldg(n1 + j), g1 = __ldg(n1 + ti.fp + j);
-    f[j] = h00 * v0 + h10 * g0 + h01 * v1 + h11 * g1;
-    df[j] = (d00 * (v0 - v1) + d10 * g0 + d11 * g1) * invh;
-  }
-}
 
 // Coefficients of the normalised real-harmonic recursion, staged in shared memory so that
 // the (l, m) loops below can run rolled (small code, no instruction-cache pressure).
@@ -51,7 +28,7 @@ template <typename T> struct YlmShared {
 };
 
 // EXACT: n_max == NC and l_max == LC (no runtime size guards in the channel loops).
-template <typename T, int NC, int LC, bool TABLE, bool EXACT>
+template <typename T, int NC, int LC, bool EXACT>
 __global__ void __launch_bounds__(SG_WARPS * 32)
 pair_adj_kernel(const AdjArgs<T> a, int smem_per_warp) {
   constexpr int NP = (NC + 3) / 4 * 4;
@@ -126,7 +103,7 @@ pair_adj_kernel(const AdjArgs<T> a, int smem_per_warp) {
       }
     }
     __syncwarp();
-    if constexpr (!TABLE) {
+    {
       // G_alpha = W^T G_n (lane-local per (s, lm) row)
       for (int k = lane; k < a.nsp * L; k += 32) {
         T gn[NC];
@@ -164,14 +141,7 @@ pair_adj_kernel(const AdjArgs<T> a, int smem_per_warp) {
           inv = T(1) / r;
           ux = v.x * inv; uy = v.y * inv; uz = v.z * inv;
         }
-        if constexpr (TABLE) {
-          float f[NC + LC + 1], df[NC + LC + 1];
-          table_interp_d<NC, LC>(a.table, a.ti, (float)r, f, df);
-#pragma unroll
-          for (int n = 0; n < NC; ++n) { bn[n] = f[n]; dbn[n] = df[n]; }
-#pragma unroll
-          for (int l = 0; l <= LC; ++l) { il_s[l * 32 + lane] = f[NC + l]; dil_s[l * 32 + lane] = df[NC + l]; }
-        } else {
+        {
           using Dd = Dual<double>;
           Dd rd((double)r, 1.0);
           Dd ba[NC];
@@ -291,7 +261,7 @@ pair_adj_kernel(const AdjArgs<T> a, int smem_per_warp) {
   }
 }
 
-template <typename T, int NC, int LC, bool TABLE, bool EXACT>
+template <typename T, int NC, int LC, bool EXACT>
 static cudaError_t launch_adj_v(const AdjArgs<T>& a, cudaStream_t st) {
   constexpr int NP = (NC + 3) / 4 * 4;
   const int L = (a.lmax + 1) * (a.lmax + 1);
@@ -301,7 +271,7 @@ static cudaError_t launch_adj_v(const AdjArgs<T>& a, cudaStream_t st) {
   per_warp = (per_warp + 3) / 4 * 4;
   const size_t smem = (sizeof(YlmShared<T>) + 15) / 16 * 16 + (size_t)SG_WARPS * per_warp * sizeof(T);
   if (smem > 220 * 1024) return cudaErrorInvalidConfiguration;
-  auto kern = pair_adj_kernel<T, NC, LC, TABLE, EXACT>;
+  auto kern = pair_adj_kernel<T, NC, LC, EXACT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
@@ -318,32 +288,25 @@ static cudaError_t launch_adj_v(const AdjArgs<T>& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <typename T, int NC, int LC, bool TABLE>
+template <typename T, int NC, int LC>
 static cudaError_t launch_adj(const AdjArgs<T>& a, cudaStream_t st) {
-  if (a.nmax == NC && a.lmax == LC) return launch_adj_v<T, NC, LC, TABLE, true>(a, st);
-  return launch_adj_v<T, NC, LC, TABLE, false>(a, st);
+  if (a.nmax == NC && a.lmax == LC) return launch_adj_v<T, NC, LC, true>(a, st);
+  return launch_adj_v<T, NC, LC, false>(a, st);
 }
 
 template <typename T>
 cudaError_t sg_pair_adjoint(const AdjArgs<T>& a, int cls, bool table, cudaStream_t st) {
   if (a.n_atoms == 0) return cudaSuccess;
   if (table) {
-    if constexpr (sizeof(T) == 4) {
-      switch (cls) {
-        case 0: return launch_adj<T, 6, 6, true>(a, st);
-        case 1: return launch_adj<T, 8, 8, true>(a, st);
-        case 2: return launch_adj<T, 10, 10, true>(a, st);
-        default: return launch_adj<T, 12, 12, true>(a, st);
-      }
-    }
+    if constexpr (sizeof(T) == 4) return sg_pair_adjoint_mma(a, cls, st);
     return cudaErrorInvalidValue;
   }
   if constexpr (sizeof(T) == 8) {
     switch (cls) {
-      case 0: return launch_adj<T, 6, 6, false>(a, st);
-      case 1: return launch_adj<T, 8, 8, false>(a, st);
-      case 2: return launch_adj<T, 10, 10, false>(a, st);
-      default: return launch_adj<T, 12, 12, false>(a, st);
+      case 0: return launch_adj<T, 6, 6>(a, st);
+      case 1: return launch_adj<T, 8, 8>(a, st);
+      case 2: return launch_adj<T, 10, 10>(a, st);
+      default: return launch_adj<T, 12, 12>(a, st);
     }
   }
   return cudaErrorInvalidValue;

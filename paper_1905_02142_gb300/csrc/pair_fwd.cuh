@@ -13,30 +13,7 @@
 #pragma once
 #include "internal.h"
 #include "soapmath.cuh"
-
-template <int NC, int LC, bool DERIV>
-__device__ __forceinline__ void table_interp(const float* __restrict__ tab, const TableInfo& ti,
-                                             float r, float* f, float* df) {
-  constexpr int F = NC + LC + 1;
-  float x = r * (float)(1.0 / ti.h);
-  int k = (int)x;
-  k = k < 0 ? 0 : (k >= ti.K ? ti.K - 1 : k);
-  float t = x - (float)k;
-  const float* n0 = tab + (size_t)k * 2 * ti.fp;
-  const float* n1 = n0 + 2 * ti.fp;
-  float t2 = t * t;
-  float h00 = (2.f * t - 3.f) * t2 + 1.f, h10 = ((t - 2.f) * t + 1.f) * t;
-  float h01 = (3.f - 2.f * t) * t2, h11 = (t - 1.f) * t2;
-  float d00 = 6.f * t * (t - 1.f), d10 = (3.f * t - 4.f) * t + 1.f, d11 = (3.f * t - 2.f) * t;
-  float invh = (float)(1.0 / ti.h);
-#pragma unroll
-  for (int j = 0; j < F; ++j) {
-    float v0 = __ldg(n0 + j), g0 = __ldg(n0 + ti.fp + j);
-    float v1 = __ldg(n1 + j), g1 = __ldg(n1 + ti.fp + j);
-    f[j] = h00 * v0 + h10 * g0 + h01 * v1 + h11 * g1;
-    if (DERIV) df[j] = (d00 * (v0 - v1) + d10 * g0 + d11 * g1) * invh;
-  }
-}
+#include "table.cuh"
 
 template <typename T> __device__ __forceinline__ T sq(T x) { return x * x; }
 

@@ -1,0 +1,55 @@
+// Cubic-Hermite interpolation of the radial table (mixed-precision path).
+//
+// Node k (r_k = k h) holds two half-nodes of TableDims::FP floats: the values, then h times
+// the r-derivatives.  Within a half-node the NC radial coefficients b_n come first, padded
+// to a multiple of 4, then the LC + 1 angular factors 4 pi ilexp_l, also padded to 4, so that
+// both groups are read with 16-byte loads.  Node k + 1 follows node k directly: the two
+// nodes of an interval are 4 FP contiguous floats.
+#pragma once
+#include "internal.h"
+
+template <int NC, int LC> struct TableDims {
+  static constexpr int NCP = (NC + 3) / 4 * 4;      // b_n slots
+  static constexpr int LPP = (LC + 1 + 3) / 4 * 4;  // ilexp_l slots
+  static constexpr int FP = NCP + LPP;              // floats per half-node
+};
+
+// f[0..NC) = b_n(r), f[NC..NC+LC] = 4 pi ilexp_l(r); df = d/dr of the same (if DERIV).
+template <int NC, int LC, bool DERIV>
+__device__ __forceinline__ void table_interp(const float* __restrict__ tab, const TableInfo& ti,
+                                             float r, float* f, float* df) {
+  using TD = TableDims<NC, LC>;
+  constexpr int Q = TD::FP / 4;  // float4 per half-node
+  const float x = r * ti.inv_h;
+  int k = (int)x;
+  k = k < 0 ? 0 : (k >= ti.K ? ti.K - 1 : k);
+  const float t = x - (float)k;
+  const float4* n0 = reinterpret_cast<const float4*>(tab) + (size_t)k * 2 * Q;
+  const float t2 = t * t;
+  const float h00 = (2.f * t - 3.f) * t2 + 1.f, h10 = ((t - 2.f) * t + 1.f) * t;
+  const float h01 = (3.f - 2.f * t) * t2, h11 = (t - 1.f) * t2;
+  const float d00 = 6.f * t * (t - 1.f), d10 = (3.f * t - 4.f) * t + 1.f, d11 = (3.f * t - 2.f) * t;
+  const float invh = ti.inv_h;
+  float4 v0[Q], g0[Q], v1[Q], g1[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    v0[q] = __ldg(n0 + q);
+    g0[q] = __ldg(n0 + Q + q);
+    v1[q] = __ldg(n0 + 2 * Q + q);
+    g1[q] = __ldg(n0 + 3 * Q + q);
+  }
+#pragma unroll
+  for (int j = 0; j < TD::FP; ++j) {
+    int o;  // logical output index, or -1 for a padding slot
+    if (j < TD::NCP) o = j < NC ? j : -1;
+    else o = (j - TD::NCP) <= LC ? NC + (j - TD::NCP) : -1;
+    if (o < 0) continue;
+    const int q = j >> 2, c = j & 3;
+    const float a0 = c == 0 ? v0[q].x : c == 1 ? v0[q].y : c == 2 ? v0[q].z : v0[q].w;
+    const float b0 = c == 0 ? g0[q].x : c == 1 ? g0[q].y : c == 2 ? g0[q].z : g0[q].w;
+    const float a1 = c == 0 ? v1[q].x : c == 1 ? v1[q].y : c == 2 ? v1[q].z : v1[q].w;
+    const float b1 = c == 0 ? g1[q].x : c == 1 ? g1[q].y : c == 2 ? g1[q].z : g1[q].w;
+    f[o] = h00 * a0 + h10 * b0 + h01 * a1 + h11 * b1;
+    if (DERIV) df[o] = (d00 * (a0 - a1) + d10 * b0 + d11 * b1) * invh;
+  }
+}

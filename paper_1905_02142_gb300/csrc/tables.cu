@@ -10,6 +10,7 @@
 // accuracy in W (cond(S) grows like a Hilbert matrix), which the FP64 nodes avoid.
 #include "internal.h"
 #include "soapmath.cuh"
+#include "table.cuh"
 
 template <int NC, int LC>
 __global__ void table_kernel(DevParams p, BasisConst<double> bc, TableInfo ti, float* table) {
@@ -36,8 +37,8 @@ __global__ void table_kernel(DevParams p, BasisConst<double> bc, TableInfo ti, f
   const double FOUR_PI = 12.566370614359172;
   for (int l = 0; l <= p.lmax; ++l) {
     double w = FOUR_PI * (p.eq08 ? (2.0 * l + 1.0) : 1.0);
-    v[NC + l] = (float)(w * il[l].v);
-    dv[NC + l] = (float)(ti.h * w * il[l].d);
+    v[TableDims<NC, LC>::NCP + l] = (float)(w * il[l].v);
+    dv[TableDims<NC, LC>::NCP + l] = (float)(ti.h * w * il[l].d);
   }
 }
 
