@@ -5,37 +5,70 @@
 // E_struct and the virial are summed per structure in FP64.
 #include "internal.h"
 
+// Accumulator of the per-atom sums: FP64 for the FP64 path; for FP32 inputs a double-float
+// pair (hi, lo) updated with the exact two-sum, which keeps close to FP64 accuracy without
+// FP64 instructions (those are slow on this GPU).
+template <typename T> struct SumAcc {
+  double v = 0;
+  __device__ void add(T x) { v += (double)x; }
+  __device__ void warp_reduce() { v = warp_sum(v); }
+  __device__ double value() const { return v; }
+};
+template <> struct SumAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ void add2(float xh, float xl) {
+    const float s = hi + xh;
+    const float bp = s - hi;
+    const float e = (hi - (s - bp)) + (xh - bp);
+    hi = s;
+    lo += e + xl;
+  }
+  __device__ void add(float x) { add2(x, 0.f); }
+  __device__ void warp_reduce() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+      const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+      add2(oh, ol);
+    }
+  }
+  __device__ double value() const { return (double)hi + (double)lo; }
+};
+
 template <typename T>
 __global__ void atom_finish_kernel(int n, int nsp, const int* __restrict__ seg_offs,
                                    const int* __restrict__ rev, const Vec4<T>* __restrict__ dedr,
                                    const T* __restrict__ eps_part, int n_tiles, T* e_atom,
                                    double* forces, double fsign) {
-  // one warp per atom: lanes stride over the atom's pairs (coalesced), FP64 warp sums
+  // one warp per atom: lanes stride over the atom's pairs (coalesced), then warp sums
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= n) return;
   if (eps_part && e_atom) {
-    double e = 0;
-    for (int t = lane; t < n_tiles; t += 32) e += (double)eps_part[(size_t)i * n_tiles + t];
-    e = warp_sum(e);
-    if (lane == 0) e_atom[i] = (T)e;
+    SumAcc<T> e;
+    for (int t = lane; t < n_tiles; t += 32) e.add(eps_part[(size_t)i * n_tiles + t]);
+    e.warp_reduce();
+    if (lane == 0) e_atom[i] = (T)e.value();
   }
   if (forces) {
-    double f0 = 0, f1 = 0, f2 = 0;
+    SumAcc<T> f0, f1, f2;
     const int beg = seg_offs[i * nsp], end = seg_offs[(i + 1) * nsp];
     for (int p = beg + lane; p < end; p += 32) {
       const Vec4<T> a = dedr[p], b = dedr[rev[p]];
-      f0 += (double)a.x - (double)b.x;
-      f1 += (double)a.y - (double)b.y;
-      f2 += (double)a.z - (double)b.z;
+      f0.add(a.x);
+      f0.add(-b.x);
+      f1.add(a.y);
+      f1.add(-b.y);
+      f2.add(a.z);
+      f2.add(-b.z);
     }
-    f0 = warp_sum(f0);
-    f1 = warp_sum(f1);
-    f2 = warp_sum(f2);
+    f0.warp_reduce();
+    f1.warp_reduce();
+    f2.warp_reduce();
     if (lane == 0) {
-      forces[3 * i] = fsign * f0;
-      forces[3 * i + 1] = fsign * f1;
-      forces[3 * i + 2] = fsign * f2;
+      forces[3 * i] = fsign * f0.value();
+      forces[3 * i + 1] = fsign * f1.value();
+      forces[3 * i + 2] = fsign * f2.value();
     }
   }
 }

@@ -1,50 +1,58 @@
-// Power spectrum and normalised descriptor (Eq. 09 and Sec. I), one block per atom.
+// Power spectrum and normalised descriptor (Eq. 09 and Sec. I), one warp per atom.
 //   p[c1][c2][l] = sum_{m=-l..l} c[c1][lm] c[c2][lm]   (real Y_lm: same value as Eq. 09)
 //   packed entry (c1 <= c2, l) = p times sqrt(2) when c1 != c2;  q = p / |p|.
+#include <algorithm>
+
 #include "internal.h"
 
 template <typename T>
-__global__ void powspec_kernel(const T* __restrict__ c, int nch, int lmax, T* q, T* pnorm) {
+__global__ void powspec_kernel(const T* __restrict__ c, int n_atoms, int nch, int lmax,
+                               int per_warp, T* q, T* pnorm) {
+  // one warp per atom: c staged in shared memory, each lane owns whole channel pairs
+  // (c1 <= c2) and all their l, the unnormalised p stays in shared memory until |p| is known
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* cs = reinterpret_cast<T*>(smem_raw);
-  __shared__ T red[32];
-  const int atom = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* cs = reinterpret_cast<T*>(smem_raw) + (size_t)warp * per_warp;
   const int L = (lmax + 1) * (lmax + 1);
   const int lp1 = lmax + 1;
   const int npair = nch * (nch + 1) / 2;
   const int D = npair * lp1;
-  const T* ci = c + (size_t)atom * nch * L;
-  for (int k = threadIdx.x; k < nch * L; k += blockDim.x) cs[k] = ci[k];
-  __syncthreads();
-  T* qi = q + (size_t)atom * D;
-  T ss = 0;
+  T* ps = cs + nch * L;
   const T SQRT2 = (T)1.4142135623730951;
-  for (int k = threadIdx.x; k < D; k += blockDim.x) {
-    const int pc = k / lp1, l = k - pc * lp1;
-    int c1 = 0, rem = pc;
-    while (rem >= nch - c1) { rem -= nch - c1; ++c1; }
-    const int c2 = c1 + rem;
-    const T* a = cs + c1 * L + l * l;
-    const T* b = cs + c2 * L + l * l;
-    T v = 0;
-    for (int m = 0; m < 2 * l + 1; ++m) v = fma(a[m], b[m], v);
-    if (c1 != c2) v *= SQRT2;
-    qi[k] = v;
-    ss += v * v;
+  const int wpb = blockDim.x >> 5;
+  for (int atom = blockIdx.x * wpb + warp; atom < n_atoms; atom += gridDim.x * wpb) {
+    const T* ci = c + (size_t)atom * nch * L;
+    __syncwarp();
+    for (int k = lane; k < nch * L; k += 32) cs[k] = __ldg(ci + k);
+    __syncwarp();
+    T ss = 0;
+    for (int pc = lane; pc < npair; pc += 32) {
+      int c1 = 0, rem = pc;
+      while (rem >= nch - c1) {
+        rem -= nch - c1;
+        ++c1;
+      }
+      const int c2 = c1 + rem;
+      const T* a = cs + c1 * L;
+      const T* b = cs + c2 * L;
+      const T f = c1 != c2 ? SQRT2 : T(1);
+      T* out = ps + pc * lp1;
+      for (int l = 0; l <= lmax; ++l) {
+        T v = 0;
+        for (int m = l * l; m < (l + 1) * (l + 1); ++m) v = fma(a[m], b[m], v);
+        v *= f;
+        out[l] = v;
+        ss += v * v;
+      }
+    }
+    ss = warp_sum(ss);
+    const T norm = sqrt(ss);
+    if (lane == 0) pnorm[atom] = norm;
+    const T inv = T(1) / norm;
+    __syncwarp();
+    T* qi = q + (size_t)atom * D;
+    for (int k = lane; k < D; k += 32) qi[k] = ps[k] * inv;
   }
-  ss = warp_sum(ss);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    T t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : T(0);
-    t = warp_sum(t);
-    if (threadIdx.x == 0) red[0] = t;
-  }
-  __syncthreads();
-  const T norm = sqrt(red[0]);
-  if (threadIdx.x == 0) pnorm[atom] = norm;
-  const T inv = T(1) / norm;
-  for (int k = threadIdx.x; k < D; k += blockDim.x) qi[k] *= inv;
 }
 
 template <typename T>
@@ -52,13 +60,24 @@ cudaError_t sg_power_spectrum(const T* c, int n_atoms, int nch, int lmax, T* q, 
                               cudaStream_t st) {
   if (n_atoms == 0) return cudaSuccess;
   const int L = (lmax + 1) * (lmax + 1);
-  const size_t smem = (size_t)nch * L * sizeof(T);
+  const int D = nch * (nch + 1) / 2 * (lmax + 1);
+  const int per_warp = (nch * L + D + 3) / 4 * 4;
+  const size_t warp_bytes = (size_t)per_warp * sizeof(T);
+  int wpb = (int)std::min<size_t>(4, (200 * 1024) / warp_bytes);
+  if (wpb < 1) return cudaErrorInvalidConfiguration;
+  const size_t smem = warp_bytes * wpb;
   auto kern = powspec_kernel<T>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  kern<<<n_atoms, 128, smem, st>>>(c, nch, lmax, q, pnorm);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpb * 32, smem);
+  if (per_sm < 1) per_sm = 1;
+  long long grid = (long long)sms * per_sm;
+  const long long need = (n_atoms + wpb - 1) / wpb;
+  if (grid > need) grid = need;
+  kern<<<(unsigned)grid, wpb * 32, smem, st>>>(c, n_atoms, nch, lmax, per_warp, q, pnorm);
   ++sg_kernel_launches;
   return cudaGetLastError();
 }
