@@ -93,8 +93,8 @@ struct soapgap_handle {
   Buf A16, nrm, uq, r_part, kp16;
   // workspace
   Buf geom, atom_offs, atom_struct, atom_bin, atom_bin4, atom_slot, bin_count, bin_start, bin_atoms, binpos,
-      binpos_lo, atom_hi, atom_lo;
-  Buf seg_count, seg_offs, scan_tmp, key_tmp, r_tmp, key, pair_j, pair_r, rev, dedr;
+      atom_hi, atom_lo;
+  Buf seg_count, seg_offs, scan_tmp, key_tmp, key, pair_j, pair_r, rev, dedr;
   Buf c, q, pnorm, e_atom, eps_part, kp, g, vir_atom, struct_w, err, cen_tmp, finish_part;
   int finish_chunks = 1;
   Buf host_in_pos, host_in_species, host_q, host_pnorm, host_e_atom, host_e_struct, host_forces,
@@ -432,7 +432,6 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     CK(h, ensure(h->atom_slot, sizeof(int) * (size_t)std::max(N, 1)));
     CK(h, ensure(h->bin_atoms, sizeof(int) * (size_t)std::max(N, 1)));
     CK(h, ensure(h->binpos, sizeof(float4) * (size_t)std::max(N, 1)));
-    CK(h, ensure(h->binpos_lo, sizeof(float4) * (size_t)std::max(N, 1)));
     CK(h, ensure(h->atom_hi, sizeof(float4) * (size_t)std::max(N, 1)));
     CK(h, ensure(h->atom_lo, sizeof(float4) * (size_t)std::max(N, 1)));
     CK(h, ensure(h->bin_count, sizeof(int) * (size_t)(h->n_bins + 1)));
@@ -457,7 +456,6 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
   nb.bin_start = (int*)h->bin_start.p;
   nb.bin_atoms = (int*)h->bin_atoms.p;
   nb.binpos = (float4*)h->binpos.p;
-  nb.binpos_lo = (float4*)h->binpos_lo.p;
   nb.atom_hi = (float4*)h->atom_hi.p;
   nb.atom_lo = (float4*)h->atom_lo.p;
   nb.seg_count = (int*)h->seg_count.p;
@@ -477,13 +475,11 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
   const long long P = h->last_pairs;
   const size_t Pc = (size_t)std::max(P, 1LL);
   CK(h, ensure(h->key_tmp, 8 * Pc));
-  CK(h, ensure(h->r_tmp, sizeof(Vec4<T>) * Pc));
   CK(h, ensure(h->key, 8 * Pc));
   CK(h, ensure(h->pair_j, 4 * Pc));
   CK(h, ensure(h->pair_r, sizeof(Vec4<T>) * Pc));
   CK(h, ensure(h->rev, 4 * Pc));
   nb.key_tmp = (unsigned long long*)h->key_tmp.p;
-  nb.r_tmp = h->r_tmp.p;
   nb.key = (unsigned long long*)h->key.p;
   nb.pair_j = (int*)h->pair_j.p;
   nb.pair_r = h->pair_r.p;
@@ -768,7 +764,7 @@ extern "C" void soapgap_destroy(soapgap_handle* h) {
   Buf* bufs[] = {&h->tc_B, &h->tc_BT, &h->tc_cols, &h->tc_qbar, &h->A16, &h->nrm, &h->uq,
                  &h->r_part, &h->kp16, &h->table, &h->qs, &h->alpha, &h->geom, &h->atom_offs, &h->atom_struct,
                  &h->atom_bin, &h->atom_bin4, &h->atom_slot, &h->bin_count, &h->bin_start, &h->bin_atoms,
-                 &h->binpos, &h->binpos_lo, &h->atom_hi, &h->atom_lo, &h->seg_count, &h->seg_offs, &h->scan_tmp, &h->key_tmp, &h->r_tmp,
+                 &h->binpos, &h->atom_hi, &h->atom_lo, &h->seg_count, &h->seg_offs, &h->scan_tmp, &h->key_tmp,
                  &h->key, &h->pair_j, &h->pair_r, &h->rev, &h->dedr, &h->c, &h->q, &h->pnorm,
                  &h->e_atom, &h->eps_part, &h->kp, &h->g, &h->vir_atom, &h->struct_w, &h->err,
                  &h->finish_part,

@@ -46,11 +46,9 @@ struct NbrBuffers {
   int* seg_count;            // [N*nsp]
   int* seg_offs;             // [N*nsp + 1]
   float4* binpos;            // [N] FP32 positions in bin order, .w = atom index
-  float4* binpos_lo;         // [N] x - (double)binpos.xyz in bin order (double-float low words)
   float4* atom_hi;           // [N] FP32 positions, atom order
   float4* atom_lo;           // [N] their low words
   unsigned long long* key_tmp;  // [cap]
-  void* r_tmp;               // [cap] Vec4<T>, unsorted
   unsigned long long* key;   // [cap]
   int* pair_j;               // [cap]
   void* pair_r;              // [cap] Vec4<T>

@@ -137,7 +137,6 @@ __global__ void bin_fill(const double* __restrict__ pos, int n, NbrBuffers b, fl
   const float xh = (float)x, yh = (float)y, zh = (float)z;
   const float4 lo = make_float4((float)(x - (double)xh), (float)(y - (double)yh), (float)(z - (double)zh), 0.f);
   binpos[at] = make_float4(xh, yh, zh, __int_as_float(i));
-  b.binpos_lo[at] = lo;
   b.atom_hi[i] = make_float4(xh, yh, zh, 0.f);
   b.atom_lo[i] = lo;
 }
@@ -236,15 +235,22 @@ __device__ __forceinline__ void visit_pairs(const double* __restrict__ pos, cons
       int b1, S2;
       float f2;
       wrap(cb.y + d1, g.nb[1], b1, S2, f2);
-      for (int d2i = -g.m[2]; d2i <= g.m[2]; ++d2i) {
-        int b2, S3;
-        float f3;
-        wrap(cb.z + d2i, g.nb[2], b2, S3, f3);
+      // bins cb.z - m .. cb.z + m are contiguous in bin order within one z-image: sweep
+      // each image's run of bins as one candidate range
+      const int zlo = cb.z - g.m[2], zhi = cb.z + g.m[2];
+      int S3 = 0, t0 = zlo;
+      while (t0 < 0) { t0 += g.nb[2]; --S3; }
+      while (t0 >= g.nb[2]) { t0 -= g.nb[2]; ++S3; }
+      for (int t = zlo; t <= zhi; ++S3, t0 = 0) {
+        // run: z-bins t0 .. t1 of image S3, covering t .. t + (t1 - t0)
+        const int t1 = min(g.nb[2] - 1, t0 + (zhi - t));
+        t += t1 - t0 + 1;
+        const float f3 = (float)S3;
         const float sx = __fadd_rn(__fadd_rn(__fmul_rn(f1, g.h32[0]), __fmul_rn(f2, g.h32[3])), __fmul_rn(f3, g.h32[6]));
         const float sy = __fadd_rn(__fadd_rn(__fmul_rn(f1, g.h32[1]), __fmul_rn(f2, g.h32[4])), __fmul_rn(f3, g.h32[7]));
         const float sz = __fadd_rn(__fadd_rn(__fmul_rn(f1, g.h32[2]), __fmul_rn(f2, g.h32[5])), __fmul_rn(f3, g.h32[8]));
-        const int tb = g.bin_off + (b0 * g.nb[1] + b1) * g.nb[2] + b2;
-        const int beg = b.bin_start[tb], end = b.bin_start[tb + 1];
+        const int tb = g.bin_off + (b0 * g.nb[1] + b1) * g.nb[2];
+        const int beg = b.bin_start[tb + t0], end = b.bin_start[tb + t1 + 1];
         const bool zero_shift = (S1 == 0 && S2 == 0 && S3 == 0);
         const bool lexpos = lex_positive(S1, S2, S3);
         double s[3] = {0.0, 0.0, 0.0};
@@ -346,105 +352,107 @@ __device__ __forceinline__ unsigned long long pair_key(int j, int s1, int s2, in
          ((unsigned long long)(s2 + 128) << 8) | (unsigned long long)(s3 + 128);
 }
 
-// writes each kept pair at its place in the (centre, species) segment
-template <typename T>
+// writes each kept pair's key at its place in the (centre, species) segment; the separation
+// vectors are computed after the per-segment sort, one pair per lane
 struct Fill {
-  // FP64 work is slow on this GPU (a warp instruction holds the FP64 pipe whatever its
-  // active lanes): the FP32 path builds kept separations in double-float arithmetic and
-  // needs the FP64 shift only for candidates within the rounding margin.
-  static constexpr bool kNeedsShift = sizeof(T) == 8;
-  int i, nsp, lane;
+  static constexpr bool kNeedsShift = false;
+  int nsp, lane;
   long long cap;
   int* next;
-  const double* pos;
   const int* species;
   const NbrBuffers* b;
-  Vec4<T>* rout;
-  __device__ void operator()(bool keep, int j, int k, int S1, int S2, int S3, float f1, float f2, float f3,
-                             const double* s, const double* r0, double d2) const {
+  __device__ void operator()(bool keep, int j, int, int S1, int S2, int S3, float, float, float,
+                             const double*, const double*, double) const {
     const int sj = keep ? species[j] : -1;
     for (int sp = 0; sp < nsp; ++sp) {
       const unsigned mask = __ballot_sync(0xffffffffu, keep && sj == sp);
       if (keep && sj == sp) {
         const int at = next[sp] + __popc(mask & ((1u << lane) - 1u));
-        const bool canon = (j > i) || (j == i && lex_positive(S1, S2, S3));
-        Vec4<T> v;
-        if constexpr (sizeof(T) == 4) {
-          if (d2 >= 0.0) {
-            v.x = (float)r0[0];
-            v.y = (float)r0[1];
-            v.z = (float)r0[2];
-          } else {
-            // canonical r = (x_j + s) - x_i, else r = -((x_i - s) - x_j): exact antisymmetry
-            const float4 jh = b->binpos[k], jl = b->binpos_lo[k];
-            const float4 ih = b->atom_hi[i], il = b->atom_lo[i];
-            const StructGeom& g = b->geom[b->atom_struct[i]];
-            const float sg = canon ? 1.f : -1.f;
-            const float ah[3] = {canon ? jh.x : ih.x, canon ? jh.y : ih.y, canon ? jh.z : ih.z};
-            const float al[3] = {canon ? jl.x : il.x, canon ? jl.y : il.y, canon ? jl.z : il.z};
-            const float bh[3] = {canon ? ih.x : jh.x, canon ? ih.y : jh.y, canon ? ih.z : jh.z};
-            const float bl[3] = {canon ? il.x : jl.x, canon ? il.y : jl.y, canon ? il.z : jl.z};
-            float out[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              float sh, sl, th, tl, uh, ul;
-              df_shift(g, sg * f1, sg * f2, sg * f3, c, sh, sl);
-              df_add(ah[c], al[c], sh, sl, th, tl);
-              df_add(th, tl, -bh[c], -bl[c], uh, ul);
-              out[c] = sg * __fadd_rn(uh, ul);
-            }
-            v.x = out[0];
-            v.y = out[1];
-            v.z = out[2];
-          }
-          v.w = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
-        } else {
-          double r[3] = {r0[0], r0[1], r0[2]};
-          if (d2 < 0.0) exact_sep(pos, i, j, s, canon, r, d2);
-          v.x = r[0];
-          v.y = r[1];
-          v.z = r[2];
-          v.w = sqrt(d2);
-        }
-        if (at < cap) {
-          b->key_tmp[at] = pair_key(j, S1, S2, S3);
-          rout[at] = v;
-        } else {
-          atomicOr(b->err, SG_ERR_PAIR_CAPACITY);
-        }
+        if (at < cap) b->key_tmp[at] = pair_key(j, S1, S2, S3);
+        else atomicOr(b->err, SG_ERR_PAIR_CAPACITY);
       }
       next[sp] += __popc(mask);
     }
   }
 };
 
-template <typename T>
 __global__ void fill_kernel(const double* __restrict__ pos, const int* __restrict__ species,
                             int n, int nsp, double rc, long long cap, NbrBuffers b,
-                            const float4* binpos, Vec4<T>* rout) {
+                            const float4* binpos) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n) return;
   const int i = warp;
   int next[SG_MAX_SPECIES];
   for (int s = 0; s < nsp; ++s) next[s] = b.seg_offs[i * nsp + s];
-  visit_pairs(pos, binpos, i, rc, b, Fill<T>{i, nsp, lane, cap, next, pos, species, &b, rout});
+  visit_pairs(pos, binpos, i, rc, b, Fill{nsp, lane, cap, next, species, &b});
 }
 
-// rank sort inside each (centre, species) segment, then keys -> j and sorted vectors
+// Separation r = x_j + S.h - x_i of pair (i, j, S), exactly antisymmetric under
+// (i, j, S) -> (j, i, -S): computed in the canonical orientation (j > i, or j = i with S
+// lexicographically positive) and negated otherwise.
+//   FP32 path: double-float sum of the split positions and the split shift, rounded once;
+//   FP64 path: fixed-order FP64 operations without FMA.
 template <typename T>
-__global__ void sort_kernel(int nseg, NbrBuffers b, const Vec4<T>* rin, Vec4<T>* rout) {
+__device__ __forceinline__ Vec4<T> pair_vector(const double* __restrict__ pos, const NbrBuffers& b,
+                                               int i, int j, int S1, int S2, int S3) {
+  const StructGeom& g = b.geom[b.atom_struct[i]];
+  const bool canon = (j > i) || (j == i && lex_positive(S1, S2, S3));
+  Vec4<T> v;
+  if constexpr (sizeof(T) == 4) {
+    const int pa = canon ? j : i, pb = canon ? i : j;
+    const float4 ah4 = b.atom_hi[pa], al4 = b.atom_lo[pa];
+    const float4 bh4 = b.atom_hi[pb], bl4 = b.atom_lo[pb];
+    const float sg = canon ? 1.f : -1.f;
+    const float ah[3] = {ah4.x, ah4.y, ah4.z}, al[3] = {al4.x, al4.y, al4.z};
+    const float bh[3] = {bh4.x, bh4.y, bh4.z}, bl[3] = {bl4.x, bl4.y, bl4.z};
+    float out[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float sh, sl, th, tl, uh, ul;
+      df_shift(g, sg * (float)S1, sg * (float)S2, sg * (float)S3, c, sh, sl);
+      df_add(ah[c], al[c], sh, sl, th, tl);
+      df_add(th, tl, -bh[c], -bl[c], uh, ul);
+      out[c] = sg * __fadd_rn(uh, ul);
+    }
+    v.x = out[0];
+    v.y = out[1];
+    v.z = out[2];
+    v.w = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
+  } else {
+    double s[3], r[3], d2;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      s[c] = __dadd_rn(__dadd_rn(__dmul_rn((double)S1, g.h[c]), __dmul_rn((double)S2, g.h[3 + c])),
+                       __dmul_rn((double)S3, g.h[6 + c]));
+    exact_sep(pos, i, j, s, canon, r, d2);
+    v.x = r[0];
+    v.y = r[1];
+    v.z = r[2];
+    v.w = sqrt(d2);
+  }
+  return v;
+}
+
+// rank sort inside each (centre, species) segment, then keys -> j and separation vectors
+template <typename T>
+__global__ void sort_kernel(int nseg, int nsp, const double* __restrict__ pos, NbrBuffers b,
+                            Vec4<T>* rout) {
   const int seg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (seg >= nseg) return;
+  const int i = seg / nsp;
   const int beg = b.seg_offs[seg], end = b.seg_offs[seg + 1];
   for (int e = beg + lane; e < end; e += 32) {
     const unsigned long long k = b.key_tmp[e];
     int rank = 0;
     for (int o = beg; o < end; ++o) rank += (__ldg(b.key_tmp + o) < k);
     b.key[beg + rank] = k;
-    b.pair_j[beg + rank] = (int)(k >> 24);
-    rout[beg + rank] = rin[e];
+    const int j = (int)(k >> 24);
+    b.pair_j[beg + rank] = j;
+    const int s1 = (int)((k >> 16) & 255) - 128, s2 = (int)((k >> 8) & 255) - 128,
+              s3 = (int)(k & 255) - 128;
+    rout[beg + rank] = pair_vector<T>(pos, b, i, j, s1, s2, s3);
   }
 }
 
@@ -479,13 +487,11 @@ cudaError_t sg_nbr_fill(const double* pos, const int* species, int n_atoms, int 
   if (n_atoms == 0) return cudaSuccess;
   const int threads = 128;
   const long long blocks = ((long long)n_atoms * 32 + threads - 1) / threads;
-  Vec4<T>* unsorted = reinterpret_cast<Vec4<T>*>(b.r_tmp);
-  fill_kernel<T><<<(unsigned)blocks, threads, 0, st>>>(pos, species, n_atoms, nsp, rc, cap, b,
-                                                       b.binpos, unsorted);
+  fill_kernel<<<(unsigned)blocks, threads, 0, st>>>(pos, species, n_atoms, nsp, rc, cap, b, b.binpos);
   const long long nseg = (long long)n_atoms * nsp;
   const long long sblocks = (nseg * 32 + threads - 1) / threads;
   Vec4<T>* sorted = reinterpret_cast<Vec4<T>*>(b.pair_r);
-  sort_kernel<T><<<(unsigned)sblocks, threads, 0, st>>>((int)nseg, b, unsorted, sorted);
+  sort_kernel<T><<<(unsigned)sblocks, threads, 0, st>>>((int)nseg, nsp, pos, b, sorted);
   rev_kernel<<<(unsigned)blocks, threads, 0, st>>>(n_atoms, nsp, species, b);
   sg_kernel_launches += 3;
   return cudaGetLastError();
