@@ -141,12 +141,15 @@ template <int NC, int LC> struct Dims {
   static constexpr int NP = (NC + 3) / 4 * 4;
 };
 
-// prologue scratch (floats): h [D] | c [nch][L] | pad to 4 | M [nsp][l_max+1][nch][NP] |
-// G [nsp][t16][NC]
+// prologue scratch (floats, each part 16-byte aligned):
+//   h [D] | q [D] | g [D] | c [nch][L] | M [nsp][l_max+1][nch][NP] | G [nsp][t16][NP]
+__host__ __device__ inline int align4(int x) { return (x + 3) & ~3; }
+
 template <int NC, int LC>
 int prologue_floats(int nsp, int nmax, int lmax, int dim, int t16) {
   const int nch = nsp * nmax, L = (lmax + 1) * (lmax + 1);
-  return ((dim + nch * L + 3) & ~3) + nsp * (lmax + 1) * nch * Dims<NC, LC>::NP + nsp * t16 * NC;
+  constexpr int NP = Dims<NC, LC>::NP;
+  return 3 * align4(dim) + align4(nch * L) + nsp * (lmax + 1) * nch * NP + nsp * t16 * NP;
 }
 
 template <int NC, int LC, int W>
@@ -154,7 +157,8 @@ MmaLayout make_layout(int nsp, int nmax, int lmax, int dim) {
   using Dm = Dims<NC, LC>;
   MmaLayout m{};
   m.t16 = tau_rows16(lmax);
-  const int coef = (int)sizeof(CoefShared<LC>);
+  const int nch = nsp * nmax;
+  const int coef = (int)sizeof(CoefShared<LC>) + 4 * align4(nch * (nch + 1) / 2);
   const int g16 = nsp * m.t16 * Dm::RB;
   const int prologue = 4 * prologue_floats<NC, LC>(nsp, nmax, lmax, dim, m.t16);
   m.loop_warp = 2 * 32 * Dm::RB + 8 * 32 * 16 + 2 * Dm::LP * 32 * 4;
@@ -212,11 +216,16 @@ pair_adj_mma_kernel(const AdjArgs<float> a, const MmaLayout lay) {
   const int t16 = lay.t16;
   const int tE = tau_even(lmax), tN = tau_count(lmax);
 
+  const int npair = nch * (nch + 1) / 2;
+  // channel-pair decode table (c1 | c2 << 16 for packed index pc), after the coefficients
+  int* pcdec = reinterpret_cast<int*>(smem + sizeof(CoefShared<LC>));
   // prologue scratch (aliases the pair-loop scratch)
-  float* hs = reinterpret_cast<float*>(uni);     // [D]
-  float* cs = hs + D;                            // [nch][L]
-  float* ms = hs + ((D + nch * L + 3) & ~3);     // [nsp][lp1][nch][NP], 16-byte aligned
-  float* g32 = ms + a.nsp * lp1 * nch * NP;      // [nsp][t16][NC]
+  float* hs = reinterpret_cast<float*>(uni);     // [D] dE/dp
+  float* qs = hs + align4(D);                    // [D]
+  float* gs = qs + align4(D);                    // [D]
+  float* cs = gs + align4(D);                    // [nch][L]
+  float* ms = cs + align4(nch * L);              // [nsp][lp1][nch][NP]
+  float* g32 = ms + a.nsp * lp1 * nch * NP;      // [nsp][t16][NP]
   // pair-loop scratch of this warp
   unsigned char* wbase = uni + (size_t)warp * lay.loop_warp;
   unsigned char* bv = wbase;                                                   // [2][32] rows
@@ -229,45 +238,61 @@ pair_adj_mma_kernel(const AdjArgs<float> a, const MmaLayout lay) {
                              coef_b(a.yc, l, m + 1));
     cf.q[l][m] = make_float4(coef_c(a.yc, l, m), coef_c(a.yc, l, m + 1), a.yc.d[l][m], 0.f);
   }
+  for (int pc = tid; pc < npair; pc += NT) {
+    int c1 = 0, rem = pc;
+    while (rem >= nch - c1) {
+      rem -= nch - c1;
+      ++c1;
+    }
+    pcdec[pc] = c1 | ((c1 + rem) << 16);
+  }
 
   for (int atom = blockIdx.x; atom < a.n_atoms; atom += gridDim.x) {
-    __syncthreads();  // previous atom done with G16 and the scratch; coefficients visible
-    // ---- h = dE/dp = w (g - q (q.g)) / |p|;  c staged in shared memory
+    __syncthreads();  // previous atom done with G16 and the scratch; tables visible
+    // ---- c, q, g -> shared memory (one pass of independent loads)
     const float w = (float)a.struct_w[a.atom_struct[atom]];
-    const float* qi = a.q + (size_t)atom * D;
-    const float* gi = a.g + (size_t)atom * D;
-    const float* ci = a.c + (size_t)atom * nch * L;
+    const float pn = a.pnorm[atom];
+    {
+      const float* qi = a.q + (size_t)atom * D;
+      const float* gi = a.g + (size_t)atom * D;
+      const float* ci = a.c + (size_t)atom * nch * L;
 #pragma unroll 4
-    for (int k = tid; k < nch * L; k += NT) cs[k] = __ldg(ci + k);
+      for (int k = tid; k < nch * L; k += NT) cs[k] = __ldg(ci + k);
+#pragma unroll 4
+      for (int k = tid; k < D; k += NT) {
+        qs[k] = __ldg(qi + k);
+        gs[k] = __ldg(gi + k);
+      }
+    }
+    __syncthreads();
+    // ---- h = dE/dp = w (g - q (q.g)) / |p|
     float dot = 0.f;
-    for (int k = tid; k < D; k += NT) dot += __ldg(qi + k) * __ldg(gi + k);
+    for (int k = tid; k < D; k += NT) dot += qs[k] * gs[k];
     dot = block_sum<W>(dot, red2);
-    const float sc = w / a.pnorm[atom];
-    for (int k = tid; k < D; k += NT) hs[k] = sc * (__ldg(gi + k) - __ldg(qi + k) * dot);
+    const float sc = w / pn;
+    for (int k = tid; k < D; k += NT) hs[k] = sc * (gs[k] - qs[k] * dot);
     __syncthreads();
 
     // ---- M[s][l][c2][n] = d p_(c1 c2 l) / d(c1, c2 product) with c1 = (s, n): 2 h on the
-    //      diagonal, sqrt(2) h off it (packed index of c1 <= c2: c1 nch - c1 (c1 + 1) / 2 + c2)
-    for (int row = tid; row < a.nsp * lp1 * nch; row += NT) {
-      const int s = row / (lp1 * nch);
-      const int rem = row - s * lp1 * nch;
-      const int l = rem / nch, c2 = rem - l * nch;
-      float* mrow = ms + (size_t)row * NP;
-#pragma unroll
-      for (int n = 0; n < NP; ++n) {
-        float v = 0.f;
-        if (n < NC && (EXACT || n < nmax)) {
-          const int c1 = s * nmax + n;
-          const int lo = min(c1, c2), hi = max(c1, c2);
-          const float hv = hs[(lo * nch - lo * (lo + 1) / 2 + hi) * lp1 + l];
-          v = (c1 == c2 ? 2.f : 1.41421356237f) * hv;
-        }
-        mrow[n] = v;
+    //      diagonal, sqrt(2) h off it; one thread per packed channel pair writes both halves
+    for (int pc = tid; pc < npair; pc += NT) {
+      const int dec = pcdec[pc];
+      const int c1 = dec & 0xffff, c2 = dec >> 16;
+      const int s1 = c1 / nmax, n1 = c1 - s1 * nmax;
+      const int s2 = c2 / nmax, n2 = c2 - s2 * nmax;
+      const float f = c1 == c2 ? 2.f : 1.41421356237f;
+      const float* hrow = hs + pc * lp1;
+      float* m1 = ms + ((size_t)s1 * lp1 * nch + c2) * NP + n1;  // + l nch NP
+      float* m2 = ms + ((size_t)s2 * lp1 * nch + c1) * NP + n2;
+      for (int l = 0; l <= lmax; ++l) {
+        const float hv = f * hrow[l];
+        m1[(size_t)l * nch * NP] = hv;
+        if (c1 != c2) m2[(size_t)l * nch * NP] = hv;
       }
     }
     __syncthreads();
 
-    // ---- G[s][lm][n] = sum_c2 M[s][l][c2][n] c[c2][lm]
+    // ---- G[s][lm][n] = sum_c2 M[s][l][c2][n] c[c2][lm]  (n < NC; n >= n_max zeroed below)
     float gmax = 0.f;
     for (int lm = tid; lm < L; lm += NT) {
       const int l = (int)sqrtf((float)lm + 0.5f);
@@ -284,18 +309,21 @@ pair_adj_mma_kernel(const AdjArgs<float> a, const MmaLayout lay) {
 #pragma unroll
           for (int q4 = 0; q4 < NP / 4; ++q4) {
             const float4 mv = m4[c2 * (NP / 4) + q4];
-            acc[4 * q4 + 0] = fmaf(mv.x, cv, acc[4 * q4 + 0]);
-            acc[4 * q4 + 1] = fmaf(mv.y, cv, acc[4 * q4 + 1]);
-            acc[4 * q4 + 2] = fmaf(mv.z, cv, acc[4 * q4 + 2]);
-            acc[4 * q4 + 3] = fmaf(mv.w, cv, acc[4 * q4 + 3]);
+            if (4 * q4 + 0 < NC) acc[4 * q4 + 0] = fmaf(mv.x, cv, acc[4 * q4 + 0]);
+            if (4 * q4 + 1 < NC) acc[4 * q4 + 1] = fmaf(mv.y, cv, acc[4 * q4 + 1]);
+            if (4 * q4 + 2 < NC) acc[4 * q4 + 2] = fmaf(mv.z, cv, acc[4 * q4 + 2]);
+            if (4 * q4 + 3 < NC) acc[4 * q4 + 3] = fmaf(mv.w, cv, acc[4 * q4 + 3]);
           }
         }
-        float* row = g32 + ((size_t)s * t16 + tau) * NC;
 #pragma unroll
-        for (int n = 0; n < NC; ++n) {
-          row[n] = acc[n];
+        for (int n = 0; n < NP; ++n) {
+          if (!(n < NC && (EXACT || n < nmax))) acc[n] = 0.f;
           gmax = fmaxf(gmax, fabsf(acc[n]));
         }
+        float4* row = reinterpret_cast<float4*>(g32 + ((size_t)s * t16 + tau) * NP);
+#pragma unroll
+        for (int q4 = 0; q4 < NP / 4; ++q4)
+          row[q4] = make_float4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3]);
       }
     }
     gmax = block_max<W>(gmax, red2 + W);
@@ -307,11 +335,33 @@ pair_adj_mma_kernel(const AdjArgs<float> a, const MmaLayout lay) {
       const int s = row / t16, tau = row - s * t16;
       const bool real = tau < tE ? tau <= lmax : tau < tN;
       float v[NC];
+      const float4* r4 = reinterpret_cast<const float4*>(g32 + (size_t)row * NP);
 #pragma unroll
-      for (int n = 0; n < NC; ++n) v[n] = real ? g32[(size_t)row * NC + n] * sg : 0.f;
+      for (int q4 = 0; q4 < NP / 4; ++q4) {
+        const float4 x = real ? r4[q4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (4 * q4 + 0 < NC) v[4 * q4 + 0] = x.x * sg;
+        if (4 * q4 + 1 < NC) v[4 * q4 + 1] = x.y * sg;
+        if (4 * q4 + 2 < NC) v[4 * q4 + 2] = x.z * sg;
+        if (4 * q4 + 3 < NC) v[4 * q4 + 3] = x.w * sg;
+      }
       write_split_row<NC, KP, false>(g16 + (size_t)s * t16 * RB, tau, v);
     }
     __syncthreads();
+
+    // next atom's inputs towards L2 while this one's pairs run
+    {
+      const int nxt = atom + gridDim.x;
+      if (nxt < a.n_atoms) {
+        const int lc = (nch * L * 4 + 127) >> 7, lq = (D * 4 + 127) >> 7;
+        for (int k = tid; k < lc + 2 * lq; k += NT) {
+          const char* p;
+          if (k < lc) p = reinterpret_cast<const char*>(a.c + (size_t)nxt * nch * L) + ((size_t)k << 7);
+          else if (k < lc + lq) p = reinterpret_cast<const char*>(a.q + (size_t)nxt * D) + ((size_t)(k - lc) << 7);
+          else p = reinterpret_cast<const char*>(a.g + (size_t)nxt * D) + ((size_t)(k - lc - lq) << 7);
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+        }
+      }
+    }
 
     // ---- pair batches: warp w takes batches w, w + W, ... of this atom
     float vir[9];
