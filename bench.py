@@ -137,6 +137,26 @@ def algorithmic_flops(stage, n_pairs, n_atoms, w):
 
 
 # --------------------------------------------------------------------------- arms
+def profiled_traffic(w, stage, n_atoms):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary
+    (profiles/traffic_<workload>.json), or None when there is none for this stage and size or
+    the kernel's source files have changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"traffic_{w.name.split('@')[0]}.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        if rec.get("stage") != stage or rec["scaled_to"]["atoms"] != n_atoms:
+            return None
+        h = hashlib.sha256()
+        for fn in rec["source_files"]:
+            with open(os.path.join(ROOT, fn), "rb") as f:
+                h.update(f.read())
+        return rec["bytes_per_launch"] if h.hexdigest() == rec["source_sha256"] else None
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def oracle_sample_rate(w, n_sample_atoms: int, seed: int = 11):
     """FP64 oracle on a bounded sample: a box of n_sample_atoms with the workload's recipe
     (density, minimum distance, hyperparameters, sparse-set size, zeta); energies, forces
@@ -288,14 +308,16 @@ def run_ours(args, rank, world, local_rank):
     peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     achieved = flops / (stages[dom] / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": profiled_traffic(w, dom, n),
+                "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
                 "peak_source": FP32_PEAK_NOTE + f" ({sm_mhz:.0f} MHz)",
                 "flops_per_launch": flops}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        rate, dt, threads = oracle_sample_rate(w, 128)
+        n_cpu = 768
+        rate, dt, threads = oracle_sample_rate(w, n_cpu)
         cpu = {"value": rate, "unit": "atoms/s", "cores": threads, "kind": "oracle",
-               "sample": f"128-atom box of the workload recipe, energies+forces+virial, {dt:.1f} s"}
+               "sample": f"{n_cpu}-atom box of the workload recipe, energies+forces+virial, {dt:.1f} s"}
     line = {
         "metric": METRIC, "value": world * n / t_max * args.steps, "unit": "atoms/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

@@ -388,10 +388,17 @@ static int setup_geometry(soapgap_handle* h, const soapgap_batch* b) {
   return SOAPGAP_OK;
 }
 
-__global__ void atom_struct_kernel(const int64_t* offs, int S, int* out) {
-  int s = blockIdx.x;
-  if (s >= S) return;
-  for (int64_t i = offs[s] + threadIdx.x; i < offs[s + 1]; i += blockDim.x) out[i] = s;
+// structure index of every atom: the last s with offs[s] <= i (skips empty structures)
+__global__ void atom_struct_kernel(const int64_t* __restrict__ offs, int S, int n, int* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int lo = 0, hi = S - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (offs[mid] <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  out[i] = lo;
 }
 
 __global__ void fill_ones(double* w, int n) {
@@ -444,7 +451,9 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
                           cudaMemcpyHostToDevice, st));
     CK(h, cudaMemsetAsync(h->err.p, 0, sizeof(int), st));
     mark(h, EV_NB0, st);
-    atom_struct_kernel<<<S, 128, 0, st>>>((const int64_t*)h->atom_offs.p, S, (int*)h->atom_struct.p);
+    if (N > 0)
+      atom_struct_kernel<<<(N + 255) / 256, 256, 0, st>>>((const int64_t*)h->atom_offs.p, S, N,
+                                                           (int*)h->atom_struct.p);
     ++sg_kernel_launches;
   }
   nb.geom = (const StructGeom*)h->geom.p;

@@ -106,17 +106,26 @@ __global__ void struct_partial_kernel(const int64_t* __restrict__ offs, const T*
   }
 }
 
+// one warp per structure: lanes take chunks c = lane, lane + 32, ..., then a fixed-order
+// shuffle tree (deterministic)
 __global__ void struct_total_kernel(int n_struct, int chunks, const double* __restrict__ part,
                                     double* e_struct, double* virial) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (s >= n_struct) return;
   double acc[10];
+#pragma unroll
   for (int t = 0; t < 10; ++t) acc[t] = 0;
-  for (int c = 0; c < chunks; ++c)
+  for (int c = lane; c < chunks; c += 32)
+#pragma unroll
     for (int t = 0; t < 10; ++t) acc[t] += part[((size_t)s * chunks + c) * 10 + t];
-  if (e_struct) e_struct[s] = acc[0];
-  if (virial)
-    for (int t = 0; t < 9; ++t) virial[(size_t)s * 9 + t] = acc[1 + t];
+#pragma unroll
+  for (int t = 0; t < 10; ++t) acc[t] = warp_sum(acc[t]);
+  if (lane == 0) {
+    if (e_struct) e_struct[s] = acc[0];
+    if (virial)
+      for (int t = 0; t < 9; ++t) virial[(size_t)s * 9 + t] = acc[1 + t];
+  }
 }
 
 int sg_finish_chunks(int max_struct_atoms) {
@@ -138,7 +147,7 @@ cudaError_t sg_finish(int n_atoms, int n_struct, int nsp, const int64_t* atom_of
   if (n_struct > 0 && (e_struct || virial)) {
     struct_partial_kernel<T><<<dim3(n_struct, chunks), 256, 0, st>>>(
         atom_offs_dev, e_struct ? e_atom : nullptr, virial ? vir_atom : nullptr, part, chunks);
-    struct_total_kernel<<<(n_struct + 127) / 128, 128, 0, st>>>(n_struct, chunks, part, e_struct, virial);
+    struct_total_kernel<<<(n_struct * 32 + 127) / 128, 128, 0, st>>>(n_struct, chunks, part, e_struct, virial);
     sg_kernel_launches += 2;
   }
   return cudaGetLastError();
