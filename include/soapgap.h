@@ -67,6 +67,8 @@ extern "C" {
 #define SOAPGAP_FORCES 4u /* write forces (needs a model)               */
 #define SOAPGAP_VIRIAL 8u /* write virial (needs a model)               */
 #define SOAPGAP_TIMING 16u /* record per-stage device times (soapgap_stage_times) */
+#define SOAPGAP_ASYNC 32u  /* no allocation and no host synchronisation: capturable in a
+                              CUDA graph (see soapgap_compute)                         */
 
 /* Stages reported by soapgap_stage_times, in this order. */
 #define SOAPGAP_N_STAGES 7 /* neighbours, pair_forward, power_spectrum, gap_forward,
@@ -145,6 +147,35 @@ int soapgap_set_model(soapgap_handle* h, const double* q_sparse, const double* a
 int soapgap_compute(soapgap_handle* h, const soapgap_batch* batch, uint32_t flags,
                     void* q, void* pnorm, void* e_atom, double* e_struct, double* forces,
                     double* virial, void* stream);
+
+/* Asynchronous evaluation (flags | SOAPGAP_ASYNC, not with SOAPGAP_TIMING).  The call enqueues
+ * its work on `stream` and returns without waiting: it allocates nothing and never
+ * synchronises, so it may be captured in a CUDA graph (stream capture) and replayed.
+ * Requirements and behaviour:
+ *   - an earlier synchronous call on this handle with the same batch shape (n_atoms,
+ *     n_struct) and flags must have sized the workspace; otherwise SOAPGAP_E_STATE;
+ *   - the neighbour-pair count is not read back.  The pair buffers of the earlier calls
+ *     (their size plus 25 %) bound it; if a configuration needs more pairs, every output of
+ *     the call is invalid and soapgap_sync_status reports SOAPGAP_E_CAPACITY;
+ *   - pos and species are read from their device pointers when the work runs (at every
+ *     replay); the cell and atom_offs are taken at call (capture) time through the
+ *     handle's pinned staging, so the handle must not be used for another batch shape
+ *     between replays of a captured graph;
+ *   - device-detected errors (atom outside its cell, coincident atoms, pair capacity) are
+ *     reported by soapgap_sync_status, not by the return value. */
+
+/* Wait for `stream` and report the device error word of the last asynchronous call:
+ * SOAPGAP_OK, SOAPGAP_E_CAPACITY (pair buffers too small), SOAPGAP_E_INVALID_ARG (atom
+ * outside its cell, coincident atoms) or SOAPGAP_E_CUDA; soapgap_last_error has the text. */
+int soapgap_sync_status(soapgap_handle* h, void* stream);
+
+/* Autotuner: runs one synchronous ENERGY|FORCES|VIRIAL evaluation of `batch` (device
+ * pos/species, as for soapgap_compute; it also sizes the workspace for asynchronous calls),
+ * then times the tensor-core adjoint kernel with 2, 3 and 4 warps (pair batches) per block
+ * on it and keeps the fastest for this basis class, species count and pairs per atom.
+ * Later calls on the handle with matching problems use it.  *choice (may be NULL) receives
+ * the warps chosen (0 on the FP64 path, which has nothing to tune).  Synchronises. */
+int soapgap_autotune(soapgap_handle* h, const soapgap_batch* batch, int32_t* choice, void* stream);
 
 /* Adjoint of the last ENERGY evaluation on this handle, for the same batch:
  * dE_dEstruct [n_struct] DEVICE double (weights of each structure's energy);

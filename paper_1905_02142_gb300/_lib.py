@@ -22,6 +22,7 @@ ENERGY = 2
 FORCES = 4
 VIRIAL = 8
 TIMING = 16
+ASYNC = 32
 N_STAGES = 7
 STAGES = ("neighbours", "pair_forward", "power_spectrum", "gap_forward", "gap_backward",
           "pair_adjoint", "finish")
@@ -64,6 +65,9 @@ SIGNATURES = {
     "soapgap_export_pairs": (ctypes.c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
     "soapgap_gap_energy_noalloc": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int32,
                                                   c_int32, c_double, c_void_p, c_void_p]),
+    "soapgap_sync_status": (ctypes.c_int, [c_void_p, c_void_p]),
+    "soapgap_autotune": (ctypes.c_int, [c_void_p, ctypes.POINTER(Batch), ctypes.POINTER(c_int32),
+                                        c_void_p]),
     "soapgap_last_error": (ctypes.c_char_p, [c_void_p]),
     "soapgap_destroy": (None, [c_void_p]),
 }

@@ -116,12 +116,17 @@ class SoapGap:
         self.m = qs.shape[0]
 
     def compute(self, s: Structures, *, desc=False, energy=False, forces=False, virial=False,
-                timing=False, stream=None):
-        """Run one evaluation; returns a dict of CUDA tensors for the requested outputs."""
+                timing=False, asynchronous=False, stream=None):
+        """Run one evaluation; returns a dict of CUDA tensors for the requested outputs.
+
+        asynchronous=True: no allocation inside the library and no host synchronisation
+        (capturable in a CUDA graph); needs an earlier synchronous call with the same batch
+        shape, and device-side errors are reported by sync_status()."""
         dev = s.pos.device
         n, ns = s.n_atoms, s.n_struct
         flags = (L.DESC if desc else 0) | (L.ENERGY if energy else 0) | \
-            (L.FORCES if forces else 0) | (L.VIRIAL if virial else 0) | (L.TIMING if timing else 0)
+            (L.FORCES if forces else 0) | (L.VIRIAL if virial else 0) | \
+            (L.TIMING if timing else 0) | (L.ASYNC if asynchronous else 0)
         out = {}
         if desc:
             out["q"] = torch.empty((n, self.dim), dtype=self.dtype, device=dev)
@@ -140,6 +145,21 @@ class SoapGap:
             _ptr(out.get("e_atom")), _ptr(out.get("e_struct")), _ptr(out.get("forces")),
             _ptr(out.get("virial")), st))
         return out
+
+    def sync_status(self, stream=None):
+        """Wait for the stream; raise SoapGapError if the last asynchronous call flagged a
+        device-side error (pair capacity, atom outside its cell, coincident atoms)."""
+        st = (stream or torch.cuda.current_stream()).cuda_stream
+        self._check(self.lib.soapgap_sync_status(self.h, st))
+
+    def autotune(self, s: Structures, stream=None) -> int:
+        """Time the adjoint's block shapes on this batch and keep the fastest (see
+        soapgap_autotune); returns the warps per block chosen (0 on the FP64 path)."""
+        st = (stream or torch.cuda.current_stream(s.pos.device)).cuda_stream
+        b = s.c_batch()
+        w = ctypes.c_int32()
+        self._check(self.lib.soapgap_autotune(self.h, ctypes.byref(b), ctypes.byref(w), st))
+        return int(w.value)
 
     def backward(self, s: Structures, dE_dEstruct: torch.Tensor, virial=False, stream=None):
         """Gradient of sum_s w_s E_s with respect to positions (after an energy evaluation)."""
@@ -231,3 +251,24 @@ class SoapGapEnergy(torch.autograd.Function):
     def backward(ctx, grad_e):
         grad = ctx.model.backward(ctx.s, grad_e.detach())
         return grad, None, None
+
+
+class CapturedEvaluation:
+    """One evaluation of a fixed batch shape captured in a CUDA graph.
+
+    The constructor makes one synchronous call (sizing the workspace), then captures an
+    asynchronous call; replay() re-runs the whole evaluation (neighbour list included) on
+    the current contents of s.pos / s.species and returns the same output tensors, updated
+    in place.  Call model.sync_status() after replays to surface device-side errors."""
+
+    def __init__(self, model: SoapGap, s: Structures, **outputs):
+        self.model, self.s = model, s
+        model.compute(s, **outputs)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.out = model.compute(s, asynchronous=True, **outputs)
+
+    def replay(self):
+        self.graph.replay()
+        return self.out

@@ -5,6 +5,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -101,6 +103,11 @@ struct soapgap_handle {
       host_virial;
   int* h_err = nullptr;           // pinned
   int* h_count = nullptr;         // pinned
+  int* h_err_async = nullptr;     // pinned: device error word of the last asynchronous call
+  int64_t* h_offs = nullptr;      // pinned staging of atom_offs (read by captured copies)
+  size_t h_offs_cap = 0;
+  bool async_call = false;        // current call must not allocate or synchronise
+  std::map<long long, int> adj_warps;  // autotuned adjoint block shape per problem class
   StructGeom* h_geom = nullptr;   // pinned staging
   size_t h_geom_cap = 0;
   double* h_w = nullptr;
@@ -135,6 +142,21 @@ static int fail(soapgap_handle* h, int code, const std::string& m) {
     cudaError_t e_ = (x);                                                               \
     if (e_ != cudaSuccess)                                                              \
       return fail((h), SOAPGAP_E_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// workspace growth; an asynchronous call (SOAPGAP_ASYNC) may only use what earlier calls
+// allocated
+#define ENS(h, buf, bytes)                                                                  \
+  do {                                                                                      \
+    const size_t b_ = (bytes);                                                              \
+    if ((h)->async_call) {                                                                  \
+      if (!(buf).p || (buf).cap < b_)                                                       \
+        return fail((h), SOAPGAP_E_STATE,                                                   \
+                    "workspace too small for an asynchronous call (" #buf                   \
+                    "): make one synchronous call with the same batch first");             \
+    } else {                                                                                \
+      CK((h), ensure((buf), b_));                                                           \
+    }                                                                                       \
   } while (0)
 
 static int check_params(const soapgap_params* p, std::string& why) {
@@ -215,6 +237,8 @@ extern "C" int soapgap_create(const soapgap_params* params, soapgap_handle** out
   }
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_count, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&h->h_err_async, sizeof(int));
+  if (e == cudaSuccess) *h->h_err_async = 0;
   if (e == cudaSuccess) e = ensure(h->err, sizeof(int));
   if (e != cudaSuccess) {
     std::fprintf(stderr, "soapgap_create: CUDA error: %s\n", cudaGetErrorString(e));
@@ -328,6 +352,8 @@ extern "C" int soapgap_set_model(soapgap_handle* h, const double* q_sparse, cons
 static int setup_geometry(soapgap_handle* h, const soapgap_batch* b) {
   const int S = b->n_struct;
   if ((size_t)S > h->h_geom_cap) {
+    if (h->async_call)
+      return fail(h, SOAPGAP_E_STATE, "host staging too small for an asynchronous call: make one synchronous call with the same batch first");
     if (h->h_geom) cudaFreeHost(h->h_geom);
     h->h_geom = nullptr;
     h->h_geom_cap = 0;
@@ -416,6 +442,33 @@ static std::string device_error_text(int code) {
   return m;
 }
 
+// tuning-table key of the adjoint: basis class, species, 32-pair batches per atom
+static long long adj_key(const soapgap_handle* h, int n_atoms, long long n_pairs) {
+  const int nsp = h->prm.n_species;
+  const int batches = std::min(63, sg_adj_batches_per_atom(n_pairs, n_atoms, nsp));
+  return ((long long)h->cls * 16 + nsp) * 64 + batches;
+}
+
+// arguments of the adjoint pair kernel from the handle's workspace (after a forward pass)
+template <typename T>
+static AdjArgs<T> adj_args(soapgap_handle* h, int N, const int* species) {
+  AdjArgs<T> aa{};
+  aa.n_atoms = N; aa.nsp = h->prm.n_species; aa.nmax = h->prm.n_max; aa.lmax = h->prm.l_max;
+  aa.dim = h->D;
+  aa.n_pairs = h->last_pairs;
+  auto it = h->adj_warps.find(adj_key(h, N, h->last_pairs));
+  aa.warps = it == h->adj_warps.end() ? 0 : it->second;
+  aa.species = species; aa.atom_struct = (const int*)h->atom_struct.p;
+  aa.struct_w = (const double*)h->struct_w.p; aa.seg_offs = (const int*)h->seg_offs.p;
+  aa.pair_r = (const Vec4<T>*)h->pair_r.p; aa.table = (const float*)h->table.p; aa.ti = h->ti;
+  aa.p = h->dp;
+  if constexpr (sizeof(T) == 4) { aa.yc = h->yc32; aa.bc = h->bc32; }
+  else { aa.yc = h->yc64; aa.bc = h->bc64; }
+  aa.c = (const T*)h->c.p; aa.q = (const T*)h->q.p; aa.pnorm = (const T*)h->pnorm.p;
+  aa.g = (const T*)h->g.p; aa.dedr = (Vec4<T>*)h->dedr.p; aa.vir_atom = (T*)h->vir_atom.p;
+  return aa;
+}
+
 template <typename T>
 static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* q_out,
                void* pnorm_out, void* e_atom_out, double* e_struct, double* forces,
@@ -431,23 +484,34 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     int rc = setup_geometry(h, b);
     if (rc != SOAPGAP_OK) return rc;
     const int nseg = N * nsp;
-    CK(h, ensure(h->geom, sizeof(StructGeom) * (size_t)S));
-    CK(h, ensure(h->atom_offs, sizeof(int64_t) * (size_t)(S + 1)));
-    CK(h, ensure(h->atom_struct, sizeof(int) * (size_t)std::max(N, 1)));
-    CK(h, ensure(h->atom_bin, sizeof(int) * (size_t)std::max(N, 1)));
-    CK(h, ensure(h->atom_bin4, sizeof(int4) * (size_t)std::max(N, 1)));
-    CK(h, ensure(h->atom_slot, sizeof(int) * (size_t)std::max(N, 1)));
-    CK(h, ensure(h->bin_atoms, sizeof(int) * (size_t)std::max(N, 1)));
-    CK(h, ensure(h->binpos, sizeof(float4) * (size_t)std::max(N, 1)));
-    CK(h, ensure(h->atom_hi, sizeof(float4) * (size_t)std::max(N, 1)));
-    CK(h, ensure(h->atom_lo, sizeof(float4) * (size_t)std::max(N, 1)));
-    CK(h, ensure(h->bin_count, sizeof(int) * (size_t)(h->n_bins + 1)));
-    CK(h, ensure(h->bin_start, sizeof(int) * (size_t)(h->n_bins + 1)));
-    CK(h, ensure(h->seg_count, sizeof(int) * (size_t)std::max(nseg, 1)));
-    CK(h, ensure(h->seg_offs, sizeof(int) * (size_t)(nseg + 1)));
-    CK(h, ensure(h->scan_tmp, sizeof(int) * sg_scan_tmp_ints(std::max(std::max(nseg, h->n_bins), 1))));
+    ENS(h, h->geom, sizeof(StructGeom) * (size_t)S);
+    ENS(h, h->atom_offs, sizeof(int64_t) * (size_t)(S + 1));
+    ENS(h, h->atom_struct, sizeof(int) * (size_t)std::max(N, 1));
+    ENS(h, h->atom_bin, sizeof(int) * (size_t)std::max(N, 1));
+    ENS(h, h->atom_bin4, sizeof(int4) * (size_t)std::max(N, 1));
+    ENS(h, h->atom_slot, sizeof(int) * (size_t)std::max(N, 1));
+    ENS(h, h->bin_atoms, sizeof(int) * (size_t)std::max(N, 1));
+    ENS(h, h->binpos, sizeof(float4) * (size_t)std::max(N, 1));
+    ENS(h, h->atom_hi, sizeof(float4) * (size_t)std::max(N, 1));
+    ENS(h, h->atom_lo, sizeof(float4) * (size_t)std::max(N, 1));
+    ENS(h, h->bin_count, sizeof(int) * (size_t)(h->n_bins + 1));
+    ENS(h, h->bin_start, sizeof(int) * (size_t)(h->n_bins + 1));
+    ENS(h, h->seg_count, sizeof(int) * (size_t)std::max(nseg, 1));
+    ENS(h, h->seg_offs, sizeof(int) * (size_t)(nseg + 1));
+    ENS(h, h->scan_tmp, sizeof(int) * sg_scan_tmp_ints(std::max(std::max(nseg, h->n_bins), 1)));
     CK(h, cudaMemcpyAsync(h->geom.p, h->h_geom, sizeof(StructGeom) * (size_t)S, cudaMemcpyHostToDevice, st));
-    CK(h, cudaMemcpyAsync(h->atom_offs.p, b->atom_offs_host, sizeof(int64_t) * (size_t)(S + 1),
+    // atom offsets through pinned staging: a copy captured in a CUDA graph reads it at replay
+    if ((size_t)(S + 1) > h->h_offs_cap) {
+      if (h->async_call)
+        return fail(h, SOAPGAP_E_STATE, "host staging too small for an asynchronous call: make one synchronous call with the same batch first");
+      if (h->h_offs) cudaFreeHost(h->h_offs);
+      h->h_offs = nullptr;
+      h->h_offs_cap = 0;
+      CK(h, cudaMallocHost(&h->h_offs, sizeof(int64_t) * (size_t)(S + 1)));
+      h->h_offs_cap = (size_t)(S + 1);
+    }
+    std::memcpy(h->h_offs, b->atom_offs_host, sizeof(int64_t) * (size_t)(S + 1));
+    CK(h, cudaMemcpyAsync(h->atom_offs.p, h->h_offs, sizeof(int64_t) * (size_t)(S + 1),
                           cudaMemcpyHostToDevice, st));
     CK(h, cudaMemsetAsync(h->err.p, 0, sizeof(int), st));
     mark(h, EV_NB0, st);
@@ -475,19 +539,39 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     CK(h, sg_nbr_bin(b->pos, N, h->n_bins, nb, st));
     CK(h, sg_nbr_count(b->pos, b->species, N, nsp, h->prm.r_cut, nb, st));
     mark(h, EV_NB1, st);
-    CK(h, cudaMemcpyAsync(h->h_count, (int*)h->seg_offs.p + N * nsp, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(h, cudaMemcpyAsync(h->h_err, h->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(h, cudaStreamSynchronize(st));
-    if (*h->h_err) return fail(h, SOAPGAP_E_INVALID_ARG, device_error_text(*h->h_err));
-    h->last_pairs = *h->h_count;
+    if (!h->async_call) {
+      CK(h, cudaMemcpyAsync(h->h_count, (int*)h->seg_offs.p + N * nsp, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(h, cudaMemcpyAsync(h->h_err, h->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(h, cudaStreamSynchronize(st));
+      if (*h->h_err) return fail(h, SOAPGAP_E_INVALID_ARG, device_error_text(*h->h_err));
+      h->last_pairs = *h->h_count;
+    }
   }
-  const long long P = h->last_pairs;
+  long long P = h->last_pairs;
+  if (h->async_call && !backward) {
+    // the pair count is not read back: the pair buffers' capacity bounds it, and a
+    // device-side guard empties every segment (and flags SG_ERR_PAIR_CAPACITY) if the
+    // count exceeds it
+    const Buf* pb[5] = {&h->key_tmp, &h->key, &h->pair_j, &h->pair_r, &h->rev};
+    const size_t el[5] = {8, 8, 4, sizeof(Vec4<T>), 4};
+    long long cap = std::numeric_limits<long long>::max();
+    for (int k = 0; k < 5; ++k) {
+      if (!pb[k]->p) return fail(h, SOAPGAP_E_STATE, "no pair buffers for an asynchronous call: make one synchronous call with the same batch first");
+      cap = std::min(cap, (long long)(pb[k]->cap / el[k]));
+    }
+    if (want_grad) {
+      if (!h->dedr.p) return fail(h, SOAPGAP_E_STATE, "no pair buffers for an asynchronous call: make one synchronous call with the same batch first");
+      cap = std::min(cap, (long long)(h->dedr.cap / sizeof(Vec4<T>)));
+    }
+    P = cap;
+    CK(h, sg_nbr_cap_guard((int*)h->seg_offs.p, N * nsp, P, (int*)h->err.p, st));
+  }
   const size_t Pc = (size_t)std::max(P, 1LL);
-  CK(h, ensure(h->key_tmp, 8 * Pc));
-  CK(h, ensure(h->key, 8 * Pc));
-  CK(h, ensure(h->pair_j, 4 * Pc));
-  CK(h, ensure(h->pair_r, sizeof(Vec4<T>) * Pc));
-  CK(h, ensure(h->rev, 4 * Pc));
+  ENS(h, h->key_tmp, 8 * Pc);
+  ENS(h, h->key, 8 * Pc);
+  ENS(h, h->pair_j, 4 * Pc);
+  ENS(h, h->pair_r, sizeof(Vec4<T>) * Pc);
+  ENS(h, h->rev, 4 * Pc);
   nb.key_tmp = (unsigned long long*)h->key_tmp.p;
   nb.key = (unsigned long long*)h->key.p;
   nb.pair_j = (int*)h->pair_j.p;
@@ -495,9 +579,9 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
   nb.rev = (int*)h->rev.p;
   const int L = h->L, nch = h->nch, D = h->D;
   const size_t N1 = (size_t)std::max(N, 1);
-  CK(h, ensure(h->c, es * N1 * nch * L));
-  CK(h, ensure(h->q, es * N1 * D));
-  CK(h, ensure(h->pnorm, es * N1));
+  ENS(h, h->c, es * N1 * nch * L);
+  ENS(h, h->q, es * N1 * D);
+  ENS(h, h->pnorm, es * N1);
   if (!backward) {
     mark(h, EV_FILL0, st);
     CK(h, sg_nbr_fill<T>(b->pos, b->species, N, nsp, h->prm.r_cut, P, nb, st));
@@ -521,25 +605,25 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
   if (want_energy || backward) {
     const int M = h->M;
     const int tiles = h->mixed ? sg_gap_tc_tiles(h->tcm.mp) : sg_gap_tiles(M);
-    CK(h, ensure(h->eps_part, es * N1 * tiles));
-    CK(h, ensure(h->e_atom, es * N1));
+    ENS(h, h->eps_part, es * N1 * tiles);
+    ENS(h, h->e_atom, es * N1);
     if (want_grad) {
-      if (!h->mixed) CK(h, ensure(h->kp, es * N1 * M));
-      CK(h, ensure(h->g, es * N1 * D));
-      CK(h, ensure(h->vir_atom, es * N1 * 9));
-      CK(h, ensure(h->dedr, sizeof(Vec4<T>) * Pc));
-      CK(h, ensure(h->struct_w, sizeof(double) * (size_t)S));
+      if (!h->mixed) ENS(h, h->kp, es * N1 * M);
+      ENS(h, h->g, es * N1 * D);
+      ENS(h, h->vir_atom, es * N1 * 9);
+      ENS(h, h->dedr, sizeof(Vec4<T>) * Pc);
+      ENS(h, h->struct_w, sizeof(double) * (size_t)S);
     }
     mark(h, EV_GF0, st);
     h->stage_ran[3] = true;
     if constexpr (sizeof(T) == 4) {
       // tensor cores: centred, norm-scaled FP16 split operands (see gap_tc.cu)
       const GapTcModel& tm = h->tcm;
-      CK(h, ensure(h->A16, sizeof(__half) * N1 * 3 * tm.dp));
-      CK(h, ensure(h->nrm, sizeof(float) * N1));
-      CK(h, ensure(h->uq, sizeof(float) * N1));
-      CK(h, ensure(h->r_part, sizeof(float) * N1 * tiles));
-      if (want_grad) CK(h, ensure(h->kp16, sizeof(__half) * N1 * tm.mp));
+      ENS(h, h->A16, sizeof(__half) * N1 * 3 * tm.dp);
+      ENS(h, h->nrm, sizeof(float) * N1);
+      ENS(h, h->uq, sizeof(float) * N1);
+      ENS(h, h->r_part, sizeof(float) * N1 * tiles);
+      if (want_grad) ENS(h, h->kp16, sizeof(__half) * N1 * tm.mp);
       CK(h, sg_gap_tc_prepare((const float*)h->q.p, N, D, tm.dp, tm.qbar, (__half*)h->A16.p,
                               (float*)h->nrm.p, (float*)h->uq.p, st));
       CK(h, sg_gap_tc_forward(tm, (const __half*)h->A16.p, (const float*)h->nrm.p, (const float*)h->uq.p, N,
@@ -563,17 +647,7 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
         fill_ones<<<(S + 255) / 256, 256, 0, st>>>((double*)h->struct_w.p, S);
         ++sg_kernel_launches;
       }
-      AdjArgs<T> aa{};
-      aa.n_atoms = N; aa.nsp = nsp; aa.nmax = h->prm.n_max; aa.lmax = h->prm.l_max; aa.dim = D;
-      aa.n_pairs = h->last_pairs;
-      aa.species = b->species; aa.atom_struct = (const int*)h->atom_struct.p;
-      aa.struct_w = (const double*)h->struct_w.p; aa.seg_offs = nb.seg_offs;
-      aa.pair_r = (const Vec4<T>*)h->pair_r.p; aa.table = (const float*)h->table.p; aa.ti = h->ti;
-      aa.p = h->dp;
-      if constexpr (sizeof(T) == 4) { aa.yc = h->yc32; aa.bc = h->bc32; }
-      else { aa.yc = h->yc64; aa.bc = h->bc64; }
-      aa.c = (const T*)h->c.p; aa.q = (const T*)h->q.p; aa.pnorm = (const T*)h->pnorm.p;
-      aa.g = (const T*)h->g.p; aa.dedr = (Vec4<T>*)h->dedr.p; aa.vir_atom = (T*)h->vir_atom.p;
+      AdjArgs<T> aa = adj_args<T>(h, N, b->species);
       mark(h, EV_ADJ0, st);
       cudaError_t e = sg_pair_adjoint<T>(aa, h->cls, h->mixed, st);
       if (e == cudaErrorInvalidConfiguration)
@@ -585,7 +659,7 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     double* f_out = backward ? grad_pos : ((flags & SOAPGAP_FORCES) ? forces : nullptr);
     double* v_out = (backward || (flags & SOAPGAP_VIRIAL)) ? virial : nullptr;
     double* es_out = backward ? nullptr : e_struct;
-    CK(h, ensure(h->finish_part, sizeof(double) * 10 * (size_t)S * h->finish_chunks));
+    ENS(h, h->finish_part, sizeof(double) * 10 * (size_t)S * h->finish_chunks);
     CK(h, sg_finish<T>(N, S, nsp, (const int64_t*)h->atom_offs.p, nb.seg_offs, (const int*)h->rev.p,
                        (const Vec4<T>*)h->dedr.p, (const T*)h->eps_part.p, tiles,
                        v_out ? (const T*)h->vir_atom.p : nullptr, (T*)h->e_atom.p, es_out, f_out,
@@ -594,6 +668,18 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
       CK(h, cudaMemcpyAsync(e_atom_out, h->e_atom.p, es * (size_t)N, cudaMemcpyDeviceToDevice, st));
   }
   mark(h, EV_END, st);
+  if (h->async_call) {
+    // no synchronisation: the error word lands in pinned memory for soapgap_sync_status
+    CK(h, cudaMemcpyAsync(h->h_err_async, h->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    h->launches = sg_kernel_launches - launches0;
+    if (!backward) {
+      h->have_forward = want_energy;
+      h->fw_atoms = N;
+      h->fw_struct = S;
+    }
+    h->msg.clear();
+    return SOAPGAP_OK;
+  }
   CK(h, cudaMemcpyAsync(h->h_err, h->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(h, cudaStreamSynchronize(st));
   h->launches = sg_kernel_launches - launches0;
@@ -626,8 +712,12 @@ extern "C" int soapgap_compute(soapgap_handle* h, const soapgap_batch* batch, ui
   if (!h) return SOAPGAP_E_INVALID_ARG;
   int rc = check_batch(h, batch);
   if (rc != SOAPGAP_OK) return rc;
-  if (flags & ~(SOAPGAP_DESC | SOAPGAP_ENERGY | SOAPGAP_FORCES | SOAPGAP_VIRIAL | SOAPGAP_TIMING))
+  if (flags & ~(SOAPGAP_DESC | SOAPGAP_ENERGY | SOAPGAP_FORCES | SOAPGAP_VIRIAL | SOAPGAP_TIMING |
+                SOAPGAP_ASYNC))
     return fail(h, SOAPGAP_E_INVALID_ARG, "unknown flag bits");
+  if ((flags & SOAPGAP_ASYNC) && (flags & SOAPGAP_TIMING))
+    return fail(h, SOAPGAP_E_INVALID_ARG, "SOAPGAP_TIMING cannot be combined with SOAPGAP_ASYNC");
+  h->async_call = (flags & SOAPGAP_ASYNC) != 0;
   h->timed = (flags & SOAPGAP_TIMING) != 0;
   for (int k = 0; k < SOAPGAP_N_STAGES; ++k) h->stage_ran[k] = false;
   if (h->timed && !h->ev_made) {
@@ -657,6 +747,7 @@ extern "C" int soapgap_backward(soapgap_handle* h, const soapgap_batch* batch, c
   if (!dE_dEstruct || !grad_pos) return fail(h, SOAPGAP_E_INVALID_ARG, "backward needs dE_dEstruct and grad_pos");
   cudaStream_t st = (cudaStream_t)stream;
   h->timed = false;
+  h->async_call = false;
   if (h->mixed)
     return run<float>(h, batch, 0, nullptr, nullptr, nullptr, nullptr, nullptr, virial, dE_dEstruct, grad_pos, true, st);
   return run<double>(h, batch, 0, nullptr, nullptr, nullptr, nullptr, nullptr, virial, dE_dEstruct, grad_pos, true, st);
@@ -687,7 +778,7 @@ extern "C" int soapgap_compute_host(soapgap_handle* h, const soapgap_batch* batc
   if (e_struct) { CK(h, ensure(h->host_e_struct, sizeof(double) * S)); des = (double*)h->host_e_struct.p; }
   if (forces) { CK(h, ensure(h->host_forces, sizeof(double) * 3 * N1)); df = (double*)h->host_forces.p; }
   if (virial) { CK(h, ensure(h->host_virial, sizeof(double) * 9 * S)); dv = (double*)h->host_virial.p; }
-  rc = soapgap_compute(h, &db, flags, dq, dpn, dea, des, df, dv, stream);
+  rc = soapgap_compute(h, &db, flags & ~SOAPGAP_ASYNC, dq, dpn, dea, des, df, dv, stream);
   if (rc != SOAPGAP_OK) return rc;
   if (q && (flags & SOAPGAP_DESC)) CK(h, cudaMemcpyAsync(q, dq, es * (size_t)N * D, cudaMemcpyDeviceToHost, st));
   if (pnorm && (flags & SOAPGAP_DESC)) CK(h, cudaMemcpyAsync(pnorm, dpn, es * (size_t)N, cudaMemcpyDeviceToHost, st));
@@ -784,7 +875,77 @@ extern "C" void soapgap_destroy(soapgap_handle* h) {
   if (h->h_err) cudaFreeHost(h->h_err);
   if (h->h_count) cudaFreeHost(h->h_count);
   if (h->h_geom) cudaFreeHost(h->h_geom);
+  if (h->h_offs) cudaFreeHost(h->h_offs);
+  if (h->h_err_async) cudaFreeHost(h->h_err_async);
   if (h->ev_made)
     for (int k = 0; k < 10; ++k) cudaEventDestroy(h->ev[k]);
   delete h;
+}
+
+extern "C" int soapgap_sync_status(soapgap_handle* h, void* stream) {
+  if (!h) return SOAPGAP_E_INVALID_ARG;
+  CK(h, cudaStreamSynchronize((cudaStream_t)stream));
+  const int code = *h->h_err_async;
+  if (!code) {
+    h->msg.clear();
+    return SOAPGAP_OK;
+  }
+  const int rc = (code & SG_ERR_PAIR_CAPACITY) ? SOAPGAP_E_CAPACITY
+                 : (code & SG_ERR_TIMEOUT)     ? SOAPGAP_E_CUDA
+                                               : SOAPGAP_E_INVALID_ARG;
+  return fail(h, rc, device_error_text(code));
+}
+
+extern "C" int soapgap_autotune(soapgap_handle* h, const soapgap_batch* batch, int32_t* choice,
+                                void* stream) {
+  if (!h) return SOAPGAP_E_INVALID_ARG;
+  int rc = check_batch(h, batch);
+  if (rc != SOAPGAP_OK) return rc;
+  if (!h->has_model) return fail(h, SOAPGAP_E_STATE, "no GAP model: call soapgap_set_model first");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = batch->n_atoms, S = batch->n_struct;
+  const size_t N1 = (size_t)std::max(N, 1);
+  // one synchronous evaluation sizes the workspace and leaves the adjoint's inputs
+  CK(h, ensure(h->host_e_struct, sizeof(double) * S));
+  CK(h, ensure(h->host_forces, sizeof(double) * 3 * N1));
+  CK(h, ensure(h->host_virial, sizeof(double) * 9 * S));
+  rc = soapgap_compute(h, batch, SOAPGAP_ENERGY | SOAPGAP_FORCES | SOAPGAP_VIRIAL, nullptr, nullptr,
+                       nullptr, (double*)h->host_e_struct.p, (double*)h->host_forces.p,
+                       (double*)h->host_virial.p, stream);
+  if (rc != SOAPGAP_OK) return rc;
+  int best = 0;
+  if (h->mixed && N > 0) {
+    // the adjoint kernel is idempotent on the handle's state: time each block shape
+    cudaEvent_t e0, e1;
+    CK(h, cudaEventCreate(&e0));
+    CK(h, cudaEventCreate(&e1));
+    float best_ms = 0.f;
+    for (int w = 2; w <= 4; ++w) {
+      AdjArgs<float> aa = adj_args<float>(h, N, batch->species);
+      aa.warps = w;
+      float ms = 0.f;
+      bool ok = true;
+      for (int rep = 0; rep < 3 && ok; ++rep) {
+        CK(h, cudaEventRecord(e0, st));
+        cudaError_t e = sg_pair_adjoint<float>(aa, h->cls, true, st);
+        if (e == cudaErrorInvalidConfiguration) { cudaGetLastError(); ok = false; break; }
+        CK(h, e);
+        CK(h, cudaEventRecord(e1, st));
+        CK(h, cudaEventSynchronize(e1));
+        float t = 0.f;
+        CK(h, cudaEventElapsedTime(&t, e0, e1));
+        if (rep > 0) ms += t;  // first launch warms caches and sets kernel attributes
+      }
+      if (ok && (best == 0 || ms < best_ms)) {
+        best = w;
+        best_ms = ms;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best) h->adj_warps[adj_key(h, N, h->last_pairs)] = best;
+  }
+  if (choice) *choice = best;
+  h->msg.clear();
+  return SOAPGAP_OK;
 }

@@ -392,7 +392,7 @@ cudaError_t launch_gemm(const void* A, int a_rows, const void* B, int b_rows, in
   if (!make_map(&ma, A, a_rows, k, BM) || !make_map(&mb, B, b_rows, k, BN)) return cudaErrorInvalidValue;
   auto kern = tc_gemm_kernel<BN, STAGES, EPI_WARPS, Epi>;
   constexpr size_t smem = smem_bytes<BN, STAGES>();
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = sg_set_smem<tc_gemm_kernel<BN, STAGES, EPI_WARPS, Epi>>(smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);

@@ -6,6 +6,21 @@
 #include <stdint.h>
 #include "common.cuh"
 
+// Raise kernel Kern's dynamic shared-memory limit, once per device and size: the attribute
+// persists, and skipping repeated calls keeps a launch free of non-stream API calls (so
+// that launches can be captured in a CUDA graph).
+template <auto Kern>
+inline cudaError_t sg_set_smem(size_t bytes) {
+  static int done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+    return cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if ((int)bytes <= done[dev]) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done[dev] = (int)bytes;
+  return e;
+}
+
 // Kernels launched by this library since load (read around a call to count its launches).
 extern long long sg_kernel_launches;
 
@@ -62,6 +77,8 @@ cudaError_t sg_nbr_bin(const double* pos, int n_atoms, int n_bins, const NbrBuff
                        cudaStream_t st);
 cudaError_t sg_nbr_count(const double* pos, const int* species, int n_atoms, int nsp, double rc,
                          const NbrBuffers& b, cudaStream_t st);
+// asynchronous calls: empty all segments and flag SG_ERR_PAIR_CAPACITY if seg_offs[nseg] > cap
+cudaError_t sg_nbr_cap_guard(int* seg_offs, int nseg, long long cap, int* err, cudaStream_t st);
 template <typename T>
 cudaError_t sg_nbr_fill(const double* pos, const int* species, int n_atoms, int nsp, double rc,
                         long long cap, const NbrBuffers& b, cudaStream_t st);
@@ -124,6 +141,7 @@ cudaError_t sg_tc_gemm_store(const __half* A, int m, const __half* B, int n, int
 template <typename T> struct AdjArgs {
   int n_atoms, nsp, nmax, lmax, dim;
   long long n_pairs;
+  int warps;                // warps per block of the tensor-core adjoint (0: from n_pairs)
   const int* species;
   const int* atom_struct;
   const double* struct_w;   // [S] dE/dE_struct
@@ -145,6 +163,8 @@ template <typename T> cudaError_t sg_pair_adjoint(const AdjArgs<T>& a, int cls, 
                                                   cudaStream_t st);
 // mixed-precision (table) adjoint with the per-atom contraction on tensor cores
 cudaError_t sg_pair_adjoint_mma(const AdjArgs<float>& a, int cls, cudaStream_t st);
+// 32-pair batches of a typical atom (sum over its neighbour-species segments)
+int sg_adj_batches_per_atom(long long n_pairs, int n_atoms, int nsp);
 
 // ---------------------------------------------------------------- forces.cu
 // chunks per structure of the two-level per-structure sums (part: [S][chunks][10] doubles)

@@ -501,3 +501,23 @@ template cudaError_t sg_nbr_fill<float>(const double*, const int*, int, int, dou
                                         const NbrBuffers&, cudaStream_t);
 template cudaError_t sg_nbr_fill<double>(const double*, const int*, int, int, double, long long,
                                          const NbrBuffers&, cudaStream_t);
+
+// Pair-capacity guard of asynchronous calls: if the pair count (the last offset) exceeds
+// the capacity, every segment is emptied and SG_ERR_PAIR_CAPACITY is raised, so that no
+// later kernel indexes past the pair buffers.  One block: the decision is taken once.
+__global__ void cap_guard_kernel(int* seg_offs, int nseg, long long cap, int* err) {
+  __shared__ int over;
+  if (threadIdx.x == 0) {
+    over = (long long)seg_offs[nseg] > cap;
+    if (over) atomicOr(err, SG_ERR_PAIR_CAPACITY);
+  }
+  __syncthreads();
+  if (!over) return;
+  for (int k = threadIdx.x; k <= nseg; k += blockDim.x) seg_offs[k] = 0;
+}
+
+cudaError_t sg_nbr_cap_guard(int* seg_offs, int nseg, long long cap, int* err, cudaStream_t st) {
+  cap_guard_kernel<<<1, 1024, 0, st>>>(seg_offs, nseg, cap, err);
+  ++sg_kernel_launches;
+  return cudaGetLastError();
+}

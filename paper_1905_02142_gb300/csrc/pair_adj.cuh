@@ -272,7 +272,7 @@ static cudaError_t launch_adj_v(const AdjArgs<T>& a, cudaStream_t st) {
   const size_t smem = (sizeof(YlmShared<T>) + 15) / 16 * 16 + (size_t)SG_WARPS * per_warp * sizeof(T);
   if (smem > 220 * 1024) return cudaErrorInvalidConfiguration;
   auto kern = pair_adj_kernel<T, NC, LC, EXACT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = sg_set_smem<pair_adj_kernel<T, NC, LC, EXACT>>(smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);

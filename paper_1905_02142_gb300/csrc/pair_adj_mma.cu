@@ -566,7 +566,7 @@ cudaError_t launch_mma(const AdjArgs<float>& a, cudaStream_t st) {
   const MmaLayout lay = make_layout<NC, LC, W>(a.nsp, EXACT ? NC : a.nmax, EXACT ? LC : a.lmax, a.dim);
   if (lay.total > 220 * 1024) return cudaErrorInvalidConfiguration;
   auto kern = pair_adj_mma_kernel<NC, LC, W, EXACT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total);
+  cudaError_t e = sg_set_smem<pair_adj_mma_kernel<NC, LC, W, EXACT>>(lay.total);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
@@ -583,8 +583,10 @@ cudaError_t launch_mma(const AdjArgs<float>& a, cudaStream_t st) {
 // Warps per block = 32-pair batches of a typical atom (the warps of a block share one atom).
 template <int NC, int LC, bool EXACT>
 cudaError_t launch_mma_w(const AdjArgs<float>& a, cudaStream_t st) {
-  const double per_seg = (double)a.n_pairs / ((double)a.n_atoms * a.nsp);
-  const int batches = a.nsp * (int)std::ceil(per_seg / 32.0);
+  if (a.warps == 2) return launch_mma<NC, LC, 2, EXACT>(a, st);
+  if (a.warps == 3) return launch_mma<NC, LC, 3, EXACT>(a, st);
+  if (a.warps == 4) return launch_mma<NC, LC, 4, EXACT>(a, st);
+  const int batches = sg_adj_batches_per_atom(a.n_pairs, a.n_atoms, a.nsp);
   if (batches <= 2) return launch_mma<NC, LC, 2, EXACT>(a, st);
   if (batches == 3) return launch_mma<NC, LC, 3, EXACT>(a, st);
   return launch_mma<NC, LC, 4, EXACT>(a, st);
@@ -597,6 +599,12 @@ cudaError_t launch_mma_v(const AdjArgs<float>& a, cudaStream_t st) {
 }
 
 }  // namespace
+
+int sg_adj_batches_per_atom(long long n_pairs, int n_atoms, int nsp) {
+  if (n_atoms <= 0 || nsp <= 0) return 1;
+  const double per_seg = (double)n_pairs / ((double)n_atoms * nsp);
+  return nsp * (int)std::ceil(per_seg / 32.0);
+}
 
 cudaError_t sg_pair_adjoint_mma(const AdjArgs<float>& a, int cls, cudaStream_t st) {
   if (a.n_atoms == 0) return cudaSuccess;

@@ -140,7 +140,7 @@ static cudaError_t launch_fwd(const FwdArgs<T>& a, cudaStream_t st) {
   constexpr int NP = (NC + 3) / 4 * 4;
   const size_t smem = (size_t)SG_WARPS * (32 * AS + 32 * NP) * sizeof(T);
   auto kern = pair_fwd_kernel<T, NC, LC, TABLE>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = sg_set_smem<pair_fwd_kernel<T, NC, LC, TABLE>>(smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);

@@ -67,7 +67,7 @@ cudaError_t sg_power_spectrum(const T* c, int n_atoms, int nch, int lmax, T* q, 
   if (wpb < 1) return cudaErrorInvalidConfiguration;
   const size_t smem = warp_bytes * wpb;
   auto kern = powspec_kernel<T>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = sg_set_smem<powspec_kernel<T>>(smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
