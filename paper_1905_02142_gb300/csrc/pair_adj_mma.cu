@@ -193,6 +193,84 @@ template <int W> __device__ __forceinline__ float block_max(float v, float* red)
   return t;
 }
 
+// The (l, m) sweep of one pair with l_max = LC known at compile time: fully unrolled, so the
+// recursion coefficients are constant-bank operands of the kernel's parameters, every
+// shared-memory offset is an immediate, and the 16-row refills of u / u' sit at fixed
+// points.  Same arithmetic as the rolled sweep in the kernel (real-harmonic recursion in
+// l for columns m and m + 1, cos/sin(m phi) rho^m by rotation).
+//   ubx[k]: this lane's entry of ubuf row 0 under column swizzle XOR 2k (see refill)
+//   il_l:   this lane's 4 pi ilexp_l at il_l[32 l], its r-derivative at il_l[32 (LP + l)]
+template <int LC, typename Refill>
+__device__ __forceinline__ void adj_sweep_unrolled(const YlmCoef<float>& yc, float ux, float uy, float uz,
+                                                   const float* il_l, const float4* const (&ubx)[4],
+                                                   Refill&& refill, float& srad, float& hx, float& hy,
+                                                   float& hz) {
+  constexpr int LP = LC + 1;
+  constexpr int TE = (LC + 2) & ~1;
+  float cm = 1.f, sm = 0.f, cmm1 = 0.f, smm1 = 0.f;
+#pragma unroll
+  for (int m = 0; m <= LC; ++m) {
+    if (m > 0) {
+      cmm1 = cm;
+      smm1 = sm;
+      cm = ux * cmm1 - uy * smm1;
+      sm = ux * smm1 + uy * cmm1;
+    }
+    float a1 = yc.seed[m], a2 = 0.f;
+    float b1 = (m + 1 <= LC) ? yc.seed[m + 1] : 0.f, b2 = 0.f;
+    float Rc = 0.f, Rs = 0.f, Xc = 0.f, Xs = 0.f, Zc = 0.f, Zs = 0.f;
+#pragma unroll
+    for (int l = m; l <= LC; ++l) {
+      float pl, ql = 0.f;
+      if (l == m) {
+        pl = a1;
+      } else {
+        pl = (l == m + 1) ? (yc.s1[m] * uz) * a1 : fmaf(yc.a[l][m] * uz, a1, -yc.b[l][m] * a2);
+        a2 = a1;
+        a1 = pl;
+      }
+      if (m + 1 <= LC && l >= m + 1) {
+        if (l == m + 1) {
+          ql = b1;
+        } else {
+          ql = (l == m + 2) ? (yc.s1[m + 1] * uz) * b1 : fmaf(yc.a[l][m + 1] * uz, b1, -yc.b[l][m + 1] * b2);
+          b2 = b1;
+          b1 = ql;
+        }
+      }
+      const float dz = yc.d[l][m] * ql;
+      const float il = il_l[32 * l], dil = il_l[32 * (LP + l)];
+      // tau of (l, m): l for m = 0, else the cos-type entry of the (cos, sin) pair
+      const int tau = m == 0 ? l : TE + 2 * ((m - 1) * (LC + 1) - m * (m - 1) / 2) + 2 * (l - m);
+      if ((tau & 15) == 0) refill(tau >> 4);
+      const float4 u = ubx[(tau & 6) >> 1][((tau >> 1) & 7) * 32];
+      if (m == 0) {
+        const float uu = (tau & 1) ? u.z : u.x, up = (tau & 1) ? u.w : u.y;
+        Rc = fmaf(fmaf(up, il, uu * dil), pl, Rc);
+        Zc = fmaf(uu * il, dz, Zc);
+      } else {
+        const float wc = u.x * il, ws = u.z * il;
+        Rc = fmaf(fmaf(u.y, il, u.x * dil), pl, Rc);
+        Rs = fmaf(fmaf(u.w, il, u.z * dil), pl, Rs);
+        Xc = fmaf(wc, pl, Xc);
+        Xs = fmaf(ws, pl, Xs);
+        Zc = fmaf(wc, dz, Zc);
+        Zs = fmaf(ws, dz, Zs);
+      }
+    }
+    if (m == 0) {
+      srad += Rc;
+      hz += Zc;
+    } else {
+      const float fm = (float)m;
+      srad = fmaf(Rc, cm, fmaf(Rs, sm, srad));
+      hx = fmaf(fm, fmaf(Xc, cmm1, Xs * smm1), hx);
+      hy = fmaf(fm, fmaf(Xs, cmm1, -Xc * smm1), hy);
+      hz = fmaf(Zc, cm, fmaf(Zs, sm, hz));
+    }
+  }
+}
+
 template <int NC, int LC, int W, bool EXACT>
 __global__ void __launch_bounds__(W * 32, (W == 4 ? 4 : (W == 3 ? 5 : 8)))
 pair_adj_mma_kernel(const AdjArgs<float> a, const MmaLayout lay) {
@@ -461,6 +539,10 @@ pair_adj_mma_kernel(const AdjArgs<float> a, const MmaLayout lay) {
 
         const float* il_l = ild + lane;
         float srad = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
+        if constexpr (EXACT) {
+          const float4* const ubx[4] = {ubuf + lane, ubuf + (lane ^ 2), ubuf + (lane ^ 4), ubuf + (lane ^ 6)};
+          adj_sweep_unrolled<LC>(a.yc, ux, uy, uz, il_l, ubx, refill, srad, hx, hy, hz);
+        } else {
         int tau = 0;
         // m = 0 column: N~_l^0 and its z-derivative d[l][0] N~_l^1
         {
@@ -525,6 +607,7 @@ pair_adj_mma_kernel(const AdjArgs<float> a, const MmaLayout lay) {
             hz = fmaf(Zc, cm, fmaf(Zs, sm, hz));
           }
         }
+        }  // rolled sweep
         if (valid) {
           const float inv_s = ldexpf(1.f, eg + eb - 28);
           srad *= inv_s;
