@@ -96,7 +96,10 @@ struct soapgap_handle {
   // workspace
   Buf geom, atom_offs, atom_struct, atom_bin, atom_bin4, atom_slot, bin_count, bin_start, bin_atoms, binpos,
       atom_hi, atom_lo;
-  Buf seg_count, seg_offs, scan_tmp, key_tmp, key, pair_j, pair_r, rev, dedr;
+  Buf seg_count, seg_offs, scan_tmp, key_tmp, key, pair_j, pair_r, rev, dedr, slot_count, max_count;
+  int slot_maxn = 0;        // slot capacity per atom of the last synchronous neighbour search
+  int cur_maxn = 0;         // slot capacity used by the current call
+  int slot_maxn_est = 0;    // estimate for the current batch (from its densities)
   Buf c, q, pnorm, e_atom, eps_part, kp, g, vir_atom, struct_w, err, cen_tmp, finish_part;
   int finish_chunks = 1;
   Buf host_in_pos, host_in_species, host_q, host_pnorm, host_e_atom, host_e_struct, host_forces,
@@ -362,6 +365,7 @@ static int setup_geometry(soapgap_handle* h, const soapgap_batch* b) {
   }
   const double rc = h->prm.r_cut;
   int bins = 0, max_atoms = 0;
+  double slot_est = 0.0;
   for (int s = 0; s < S; ++s) {
     StructGeom& g = h->h_geom[s];
     const double* c = b->cell_host + 9 * s;
@@ -404,6 +408,9 @@ static int setup_geometry(soapgap_handle* h, const soapgap_batch* b) {
     // rounded lattice vectors, two additions); the margin bounds the error of d2 twice over
     g.margin = (float)(2.0 * (2.0 * std::sqrt(3.0) * 10.0 * rc * X * u + 4.0 * rc * rc * u) + 1e-30);
     max_atoms = std::max(max_atoms, na);
+    // kept pairs per atom ~ density x sphere volume (periodic images included)
+    const double est = (double)na / std::fabs(det) * 4.18879020478639 * rc * rc * rc;
+    slot_est = std::max(slot_est, est);
     g.bin_off = bins;
     g.atom_off = (int)b->atom_offs_host[s];
     g.n_atoms = na;
@@ -411,6 +418,7 @@ static int setup_geometry(soapgap_handle* h, const soapgap_batch* b) {
   }
   h->n_bins = bins;
   h->finish_chunks = sg_finish_chunks(max_atoms);
+  h->slot_maxn_est = ((int)std::ceil(1.3 * slot_est) + 32 + 7) & ~7;
   return SOAPGAP_OK;
 }
 
@@ -480,6 +488,7 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
   const size_t es = sizeof(T);
   NbrBuffers nb{};
   const long long launches0 = sg_kernel_launches;
+  const size_t N1n = (size_t)std::max(N, 1);
   if (!backward) {
     int rc = setup_geometry(h, b);
     if (rc != SOAPGAP_OK) return rc;
@@ -536,26 +545,49 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
   nb.scan_tmp = (int*)h->scan_tmp.p;
   nb.err = (int*)h->err.p;
   if (!backward) {
+    // one sweep over the candidates into per-atom slot arrays; a synchronous call retries
+    // once with the measured largest count if the density estimate was too small
+    int maxn = h->async_call ? h->slot_maxn : h->slot_maxn_est;
+    if (h->async_call && maxn <= 0)
+      return fail(h, SOAPGAP_E_STATE, "no neighbour slots for an asynchronous call: make one synchronous call with the same batch first");
+    ENS(h, h->slot_count, sizeof(int) * N1n);
+    ENS(h, h->max_count, sizeof(int));
+    nb.slot_count = (int*)h->slot_count.p;
+    nb.max_count = (int*)h->max_count.p;
     CK(h, sg_nbr_bin(b->pos, N, h->n_bins, nb, st));
-    CK(h, sg_nbr_count(b->pos, b->species, N, nsp, h->prm.r_cut, nb, st));
-    mark(h, EV_NB1, st);
-    if (!h->async_call) {
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      ENS(h, h->key_tmp, 8 * N1n * (size_t)maxn);
+      nb.key_tmp = (unsigned long long*)h->key_tmp.p;
+      CK(h, sg_nbr_slots(b->pos, b->species, N, nsp, h->prm.r_cut, maxn, nb, st));
+      if (h->async_call) break;
       CK(h, cudaMemcpyAsync(h->h_count, (int*)h->seg_offs.p + N * nsp, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(h, cudaMemcpyAsync(h->h_count + 1, h->max_count.p, sizeof(int), cudaMemcpyDeviceToHost, st));
       CK(h, cudaMemcpyAsync(h->h_err, h->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
       CK(h, cudaStreamSynchronize(st));
-      if (*h->h_err) return fail(h, SOAPGAP_E_INVALID_ARG, device_error_text(*h->h_err));
+      const int derr = *h->h_err;
+      if (derr & ~SG_ERR_PAIR_CAPACITY) return fail(h, SOAPGAP_E_INVALID_ARG, device_error_text(derr));
+      if (h->h_count[1] > maxn && attempt == 0) {
+        maxn = (h->h_count[1] + 8 + 7) & ~7;
+        CK(h, cudaMemsetAsync(h->err.p, 0, sizeof(int), st));
+        continue;
+      }
+      if (derr) return fail(h, SOAPGAP_E_INVALID_ARG, device_error_text(derr));
       h->last_pairs = *h->h_count;
+      h->slot_maxn = maxn;
+      break;
     }
+    h->cur_maxn = maxn;
+    mark(h, EV_NB1, st);
   }
   long long P = h->last_pairs;
   if (h->async_call && !backward) {
     // the pair count is not read back: the pair buffers' capacity bounds it, and a
     // device-side guard empties every segment (and flags SG_ERR_PAIR_CAPACITY) if the
-    // count exceeds it
-    const Buf* pb[5] = {&h->key_tmp, &h->key, &h->pair_j, &h->pair_r, &h->rev};
-    const size_t el[5] = {8, 8, 4, sizeof(Vec4<T>), 4};
+    // count exceeds it or a slot array overflowed
+    const Buf* pb[4] = {&h->key, &h->pair_j, &h->pair_r, &h->rev};
+    const size_t el[4] = {8, 4, sizeof(Vec4<T>), 4};
     long long cap = std::numeric_limits<long long>::max();
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < 4; ++k) {
       if (!pb[k]->p) return fail(h, SOAPGAP_E_STATE, "no pair buffers for an asynchronous call: make one synchronous call with the same batch first");
       cap = std::min(cap, (long long)(pb[k]->cap / el[k]));
     }
@@ -567,12 +599,13 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     CK(h, sg_nbr_cap_guard((int*)h->seg_offs.p, N * nsp, P, (int*)h->err.p, st));
   }
   const size_t Pc = (size_t)std::max(P, 1LL);
-  ENS(h, h->key_tmp, 8 * Pc);
   ENS(h, h->key, 8 * Pc);
   ENS(h, h->pair_j, 4 * Pc);
   ENS(h, h->pair_r, sizeof(Vec4<T>) * Pc);
   ENS(h, h->rev, 4 * Pc);
   nb.key_tmp = (unsigned long long*)h->key_tmp.p;
+  nb.slot_count = (int*)h->slot_count.p;
+  nb.max_count = (int*)h->max_count.p;
   nb.key = (unsigned long long*)h->key.p;
   nb.pair_j = (int*)h->pair_j.p;
   nb.pair_r = h->pair_r.p;
@@ -584,7 +617,12 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
   ENS(h, h->pnorm, es * N1);
   if (!backward) {
     mark(h, EV_FILL0, st);
-    CK(h, sg_nbr_fill<T>(b->pos, b->species, N, nsp, h->prm.r_cut, P, nb, st));
+    {
+      cudaError_t e = sg_nbr_place<T>(b->pos, b->species, N, nsp, h->cur_maxn, nb, st);
+      if (e == cudaErrorInvalidConfiguration)
+        return fail(h, SOAPGAP_E_UNSUPPORTED, "too many neighbours per atom for the pair sort");
+      CK(h, e);
+    }
     mark(h, EV_FWD0, st);
     h->stage_ran[0] = h->stage_ran[1] = h->stage_ran[2] = true;
     FwdArgs<T> fa{};
@@ -867,7 +905,7 @@ extern "C" void soapgap_destroy(soapgap_handle* h) {
                  &h->binpos, &h->atom_hi, &h->atom_lo, &h->seg_count, &h->seg_offs, &h->scan_tmp, &h->key_tmp,
                  &h->key, &h->pair_j, &h->pair_r, &h->rev, &h->dedr, &h->c, &h->q, &h->pnorm,
                  &h->e_atom, &h->eps_part, &h->kp, &h->g, &h->vir_atom, &h->struct_w, &h->err,
-                 &h->finish_part,
+                 &h->finish_part, &h->slot_count, &h->max_count,
                  &h->cen_tmp, &h->host_in_pos, &h->host_in_species, &h->host_q, &h->host_pnorm,
                  &h->host_e_atom, &h->host_e_struct, &h->host_forces, &h->host_virial};
   for (Buf* b : bufs)

@@ -63,7 +63,9 @@ struct NbrBuffers {
   float4* binpos;            // [N] FP32 positions in bin order, .w = atom index
   float4* atom_hi;           // [N] FP32 positions, atom order
   float4* atom_lo;           // [N] their low words
-  unsigned long long* key_tmp;  // [cap]
+  unsigned long long* key_tmp;  // [N][maxn] per-atom slots of kept pair keys (visit order)
+  int* slot_count;           // [N] keys written per atom (may exceed maxn: overflow)
+  int* max_count;            // [1] largest slot count
   unsigned long long* key;   // [cap]
   int* pair_j;               // [cap]
   void* pair_r;              // [cap] Vec4<T>
@@ -75,13 +77,17 @@ size_t sg_scan_tmp_ints(int n);
 cudaError_t sg_exclusive_scan(const int* in, int* out, int n, int* tmp, cudaStream_t st);
 cudaError_t sg_nbr_bin(const double* pos, int n_atoms, int n_bins, const NbrBuffers& b,
                        cudaStream_t st);
-cudaError_t sg_nbr_count(const double* pos, const int* species, int n_atoms, int nsp, double rc,
-                         const NbrBuffers& b, cudaStream_t st);
+// one sweep over the candidates: per-atom slot arrays of keys (capacity maxn), counts per
+// (atom, species) segment, their exclusive scan into seg_offs, and the largest count
+cudaError_t sg_nbr_slots(const double* pos, const int* species, int n_atoms, int nsp, double rc,
+                         int maxn, const NbrBuffers& b, cudaStream_t st);
 // asynchronous calls: empty all segments and flag SG_ERR_PAIR_CAPACITY if seg_offs[nseg] > cap
+// or a slot array overflowed
 cudaError_t sg_nbr_cap_guard(int* seg_offs, int nseg, long long cap, int* err, cudaStream_t st);
+// keys ranked into their segments with j and the separation vectors, then the reverse index
 template <typename T>
-cudaError_t sg_nbr_fill(const double* pos, const int* species, int n_atoms, int nsp, double rc,
-                        long long cap, const NbrBuffers& b, cudaStream_t st);
+cudaError_t sg_nbr_place(const double* pos, const int* species, int n_atoms, int nsp, int maxn,
+                         const NbrBuffers& b, cudaStream_t st);
 
 // ---------------------------------------------------------------- pair_fwd.cu
 template <typename T> struct FwdArgs {

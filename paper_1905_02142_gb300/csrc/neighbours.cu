@@ -302,90 +302,72 @@ __device__ __forceinline__ void visit_pairs(const double* __restrict__ pos, cons
   }
 }
 
-// per-lane pair counts by neighbour species
-struct Count {
-  static constexpr bool kNeedsShift = false;
-  int* cnt;
-  const int* species;
-  __device__ void operator()(bool keep, int j, int, int, int, int, float, float, float, const double*,
-                             const double*, double) const {
-    if (keep) {
-      const int sj = species[j];
-#pragma unroll
-      for (int s = 0; s < SG_MAX_SPECIES; ++s) cnt[s] += (s == sj);
-    }
-  }
-};
-
-__global__ void count_kernel(const double* __restrict__ pos, const int* __restrict__ species,
-                             int n, int nsp, double rc, NbrBuffers b, const float4* binpos) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= n) return;
-  const int i = warp;
-  int cnt[SG_MAX_SPECIES];
-#pragma unroll
-  for (int s = 0; s < SG_MAX_SPECIES; ++s) cnt[s] = 0;
-  visit_pairs(pos, binpos, i, rc, b, Count{cnt, species});
-  for (int s = 0; s < nsp; ++s) {
-    int v = warp_sum(cnt[s]);
-    if (lane == 0) b.seg_count[i * nsp + s] = v;
-  }
-}
-
-cudaError_t sg_nbr_count(const double* pos, const int* species, int n_atoms, int nsp, double rc,
-                         const NbrBuffers& b, cudaStream_t st) {
-  if (n_atoms > 0) {
-    const int threads = 128;
-    const long long blocks = ((long long)n_atoms * 32 + threads - 1) / threads;
-    count_kernel<<<(unsigned)blocks, threads, 0, st>>>(pos, species, n_atoms, nsp, rc, b,
-                                                      b.binpos);
-    ++sg_kernel_launches;
-  }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return sg_exclusive_scan(b.seg_count, b.seg_offs, n_atoms * nsp, b.scan_tmp, st);
-}
-
 __device__ __forceinline__ unsigned long long pair_key(int j, int s1, int s2, int s3) {
   return ((unsigned long long)(unsigned)j << 24) | ((unsigned long long)(s1 + 128) << 16) |
          ((unsigned long long)(s2 + 128) << 8) | (unsigned long long)(s3 + 128);
 }
 
-// writes each kept pair's key at its place in the (centre, species) segment; the separation
-// vectors are computed after the per-segment sort, one pair per lane
-struct Fill {
+// One sweep over the candidates of atom i: each kept pair's key goes to the atom's slot
+// array (in visit order), and the kept pairs are counted per neighbour species.
+struct FillSlots {
   static constexpr bool kNeedsShift = false;
-  int nsp, lane;
-  long long cap;
-  int* next;
+  int lane, maxn;
+  int* cnt;                      // running slot count (warp-uniform)
+  int* percnt;                   // per-lane counts by species [SG_MAX_SPECIES]
   const int* species;
-  const NbrBuffers* b;
+  unsigned long long* slots;     // this atom's maxn slots
+  int* err;
   __device__ void operator()(bool keep, int j, int, int S1, int S2, int S3, float, float, float,
                              const double*, const double*, double) const {
-    const int sj = keep ? species[j] : -1;
-    for (int sp = 0; sp < nsp; ++sp) {
-      const unsigned mask = __ballot_sync(0xffffffffu, keep && sj == sp);
-      if (keep && sj == sp) {
-        const int at = next[sp] + __popc(mask & ((1u << lane) - 1u));
-        if (at < cap) b->key_tmp[at] = pair_key(j, S1, S2, S3);
-        else atomicOr(b->err, SG_ERR_PAIR_CAPACITY);
-      }
-      next[sp] += __popc(mask);
+    const unsigned mask = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+      const int sj = species[j];
+#pragma unroll
+      for (int s = 0; s < SG_MAX_SPECIES; ++s) percnt[s] += (s == sj);
+      const int at = *cnt + __popc(mask & ((1u << lane) - 1u));
+      if (at < maxn) slots[at] = pair_key(j, S1, S2, S3);
+      else atomicOr(err, SG_ERR_PAIR_CAPACITY);
     }
+    *cnt += __popc(mask);
   }
 };
 
-__global__ void fill_kernel(const double* __restrict__ pos, const int* __restrict__ species,
-                            int n, int nsp, double rc, long long cap, NbrBuffers b,
-                            const float4* binpos) {
+__global__ void fill_slots_kernel(const double* __restrict__ pos, const int* __restrict__ species,
+                                  int n, int nsp, double rc, int maxn, NbrBuffers b,
+                                  const float4* binpos) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n) return;
   const int i = warp;
-  int next[SG_MAX_SPECIES];
-  for (int s = 0; s < nsp; ++s) next[s] = b.seg_offs[i * nsp + s];
-  visit_pairs(pos, binpos, i, rc, b, Fill{nsp, lane, cap, next, species, &b});
+  int cnt = 0;
+  int percnt[SG_MAX_SPECIES];
+#pragma unroll
+  for (int s = 0; s < SG_MAX_SPECIES; ++s) percnt[s] = 0;
+  visit_pairs(pos, binpos, i, rc, b,
+              FillSlots{lane, maxn, &cnt, percnt, species, b.key_tmp + (size_t)i * maxn, b.err});
+  for (int s = 0; s < nsp; ++s) {
+    const int v = warp_sum(percnt[s]);
+    if (lane == 0) b.seg_count[i * nsp + s] = v;
+  }
+  if (lane == 0) {
+    b.slot_count[i] = cnt;
+    atomicMax(b.max_count, cnt);
+  }
+}
+
+cudaError_t sg_nbr_slots(const double* pos, const int* species, int n_atoms, int nsp, double rc,
+                         int maxn, const NbrBuffers& b, cudaStream_t st) {
+  cudaMemsetAsync(b.max_count, 0, sizeof(int), st);
+  if (n_atoms > 0) {
+    const int threads = 128;
+    const long long blocks = ((long long)n_atoms * 32 + threads - 1) / threads;
+    fill_slots_kernel<<<(unsigned)blocks, threads, 0, st>>>(pos, species, n_atoms, nsp, rc, maxn, b,
+                                                            b.binpos);
+    ++sg_kernel_launches;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return sg_exclusive_scan(b.seg_count, b.seg_offs, n_atoms * nsp, b.scan_tmp, st);
 }
 
 // Separation r = x_j + S.h - x_i of pair (i, j, S), exactly antisymmetric under
@@ -434,25 +416,42 @@ __device__ __forceinline__ Vec4<T> pair_vector(const double* __restrict__ pos, c
   return v;
 }
 
-// rank sort inside each (centre, species) segment, then keys -> j and separation vectors
+// Per atom (one warp): the slot keys, staged in shared memory with their neighbour
+// species, are ranked within their species; each pair goes to its (centre, species)
+// segment in key order with its j and separation vector.  Writes stay inside the segment
+// (a segment emptied by the capacity guard receives nothing).
 template <typename T>
-__global__ void sort_kernel(int nseg, int nsp, const double* __restrict__ pos, NbrBuffers b,
-                            Vec4<T>* rout) {
-  const int seg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (seg >= nseg) return;
-  const int i = seg / nsp;
-  const int beg = b.seg_offs[seg], end = b.seg_offs[seg + 1];
-  for (int e = beg + lane; e < end; e += 32) {
-    const unsigned long long k = b.key_tmp[e];
+__global__ void place_kernel(int n, int nsp, int maxn, const double* __restrict__ pos,
+                             const int* __restrict__ species, NbrBuffers b, Vec4<T>* rout) {
+  extern __shared__ unsigned long long sk[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + wib;
+  unsigned long long* keys = sk + (size_t)wib * maxn;
+  unsigned char* spc = reinterpret_cast<unsigned char*>(sk + (size_t)(blockDim.x >> 5) * maxn) +
+                       (size_t)wib * maxn;
+  if (i >= n) return;
+  const int cnt = min(b.slot_count[i], maxn);
+  const unsigned long long* src = b.key_tmp + (size_t)i * maxn;
+  for (int e = lane; e < cnt; e += 32) {
+    const unsigned long long k = src[e];
+    keys[e] = k;
+    spc[e] = (unsigned char)(nsp > 1 ? species[(int)(k >> 24)] : 0);
+  }
+  __syncwarp();
+  for (int e = lane; e < cnt; e += 32) {
+    const unsigned long long k = keys[e];
+    const int s = spc[e];
     int rank = 0;
-    for (int o = beg; o < end; ++o) rank += (__ldg(b.key_tmp + o) < k);
-    b.key[beg + rank] = k;
-    const int j = (int)(k >> 24);
-    b.pair_j[beg + rank] = j;
-    const int s1 = (int)((k >> 16) & 255) - 128, s2 = (int)((k >> 8) & 255) - 128,
-              s3 = (int)(k & 255) - 128;
-    rout[beg + rank] = pair_vector<T>(pos, b, i, j, s1, s2, s3);
+    for (int o = 0; o < cnt; ++o) rank += (keys[o] < k) & (spc[o] == s);
+    const int at = b.seg_offs[i * nsp + s] + rank;
+    if (at < b.seg_offs[i * nsp + s + 1]) {
+      b.key[at] = k;
+      const int j = (int)(k >> 24);
+      b.pair_j[at] = j;
+      const int s1 = (int)((k >> 16) & 255) - 128, s2 = (int)((k >> 8) & 255) - 128,
+                s3 = (int)(k & 255) - 128;
+      rout[at] = pair_vector<T>(pos, b, i, j, s1, s2, s3);
+    }
   }
 }
 
@@ -482,25 +481,27 @@ __global__ void rev_kernel(int n, int nsp, const int* __restrict__ species, NbrB
 }
 
 template <typename T>
-cudaError_t sg_nbr_fill(const double* pos, const int* species, int n_atoms, int nsp, double rc,
-                        long long cap, const NbrBuffers& b, cudaStream_t st) {
+cudaError_t sg_nbr_place(const double* pos, const int* species, int n_atoms, int nsp, int maxn,
+                         const NbrBuffers& b, cudaStream_t st) {
   if (n_atoms == 0) return cudaSuccess;
+  const int warps = 4;
+  const size_t smem = (size_t)warps * maxn * 9;
+  if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = sg_set_smem<place_kernel<T>>(smem);
+  if (e != cudaSuccess) return e;
+  place_kernel<T><<<(n_atoms + warps - 1) / warps, warps * 32, smem, st>>>(
+      n_atoms, nsp, maxn, pos, species, b, reinterpret_cast<Vec4<T>*>(b.pair_r));
   const int threads = 128;
   const long long blocks = ((long long)n_atoms * 32 + threads - 1) / threads;
-  fill_kernel<<<(unsigned)blocks, threads, 0, st>>>(pos, species, n_atoms, nsp, rc, cap, b, b.binpos);
-  const long long nseg = (long long)n_atoms * nsp;
-  const long long sblocks = (nseg * 32 + threads - 1) / threads;
-  Vec4<T>* sorted = reinterpret_cast<Vec4<T>*>(b.pair_r);
-  sort_kernel<T><<<(unsigned)sblocks, threads, 0, st>>>((int)nseg, nsp, pos, b, sorted);
   rev_kernel<<<(unsigned)blocks, threads, 0, st>>>(n_atoms, nsp, species, b);
-  sg_kernel_launches += 3;
+  sg_kernel_launches += 2;
   return cudaGetLastError();
 }
 
-template cudaError_t sg_nbr_fill<float>(const double*, const int*, int, int, double, long long,
-                                        const NbrBuffers&, cudaStream_t);
-template cudaError_t sg_nbr_fill<double>(const double*, const int*, int, int, double, long long,
-                                         const NbrBuffers&, cudaStream_t);
+template cudaError_t sg_nbr_place<float>(const double*, const int*, int, int, int, const NbrBuffers&,
+                                         cudaStream_t);
+template cudaError_t sg_nbr_place<double>(const double*, const int*, int, int, int, const NbrBuffers&,
+                                          cudaStream_t);
 
 // Pair-capacity guard of asynchronous calls: if the pair count (the last offset) exceeds
 // the capacity, every segment is emptied and SG_ERR_PAIR_CAPACITY is raised, so that no
@@ -508,7 +509,7 @@ template cudaError_t sg_nbr_fill<double>(const double*, const int*, int, int, do
 __global__ void cap_guard_kernel(int* seg_offs, int nseg, long long cap, int* err) {
   __shared__ int over;
   if (threadIdx.x == 0) {
-    over = (long long)seg_offs[nseg] > cap;
+    over = (long long)seg_offs[nseg] > cap || (*(volatile int*)err & SG_ERR_PAIR_CAPACITY) != 0;
     if (over) atomicOr(err, SG_ERR_PAIR_CAPACITY);
   }
   __syncthreads();

@@ -299,3 +299,23 @@ def test_invalid_inputs_are_reported():
     # the handle stays usable after an error
     ok = model.compute(structures(synth.concat([synth.random_box(8, side=5.0, seed=1)])), energy=True)
     assert torch.isfinite(ok["e_struct"]).all()
+
+
+def test_pair_list_dense_corner_cluster():
+    """Atoms squeezed into one corner of a large cell: far more neighbours per atom than the
+    cell's mean density predicts, so the library's first neighbour sweep overflows its
+    per-atom slots and is redone with the measured count.  The pair list must still equal
+    the oracle's exactly."""
+    base = synth.random_box(300, density=0.15, dmin=1.2, seed=41)
+    batch = synth.concat([base])
+    batch.pos[:] = batch.pos * 0.55          # same cell, 6x the local density
+    P = Params(r_cut=5.0, r_soft=4.5, sigma_r0=0.5, sigma_p0=0.5, n_max=6, l_max=6)
+    m = model_for(params_dict(P), "mixed")
+    m.compute(structures(batch), desc=True)
+    gi, gj, gs = m.pairs()
+    oi, oj, os_ = oracle_pairs(batch, P.r_cut)
+    assert len(gi) == len(oi)
+    np.testing.assert_array_equal(gi, oi)
+    np.testing.assert_array_equal(gj, oj)
+    np.testing.assert_array_equal(gs, os_)
+    assert len(gi) / 300 > 2.0 * 0.15 * 4.18879 * 125  # well above the mean-density estimate
