@@ -423,11 +423,12 @@ __device__ __forceinline__ Vec4<T> pair_vector(const double* __restrict__ pos, c
 template <typename T>
 __global__ void place_kernel(int n, int nsp, int maxn, const double* __restrict__ pos,
                              const int* __restrict__ species, NbrBuffers b, Vec4<T>* rout) {
-  extern __shared__ unsigned long long sk[];
+  extern __shared__ __align__(16) unsigned long long sk[];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * (blockDim.x >> 5) + wib;
-  unsigned long long* keys = sk + (size_t)wib * maxn;
-  unsigned char* spc = reinterpret_cast<unsigned char*>(sk + (size_t)(blockDim.x >> 5) * maxn) +
+  const int kstride = maxn + 2;  // one padding key, 16-byte aligned rows
+  unsigned long long* keys = sk + (size_t)wib * kstride;
+  unsigned char* spc = reinterpret_cast<unsigned char*>(sk + (size_t)(blockDim.x >> 5) * kstride) +
                        (size_t)wib * maxn;
   if (i >= n) return;
   const int cnt = min(b.slot_count[i], maxn);
@@ -438,11 +439,22 @@ __global__ void place_kernel(int n, int nsp, int maxn, const double* __restrict_
     spc[e] = (unsigned char)(nsp > 1 ? species[(int)(k >> 24)] : 0);
   }
   __syncwarp();
+  if ((cnt & 1) && lane == 0) keys[cnt] = ~0ull;  // pad to an even count for pairwise reads
+  __syncwarp();
+  const ulonglong2* k2 = reinterpret_cast<const ulonglong2*>(keys);
+  const int n2 = (cnt + 1) >> 1;
   for (int e = lane; e < cnt; e += 32) {
     const unsigned long long k = keys[e];
     const int s = spc[e];
     int rank = 0;
-    for (int o = 0; o < cnt; ++o) rank += (keys[o] < k) & (spc[o] == s);
+    if (nsp == 1) {
+      for (int o = 0; o < n2; ++o) {
+        const ulonglong2 kk = k2[o];
+        rank += (kk.x < k) + (kk.y < k);
+      }
+    } else {
+      for (int o = 0; o < cnt; ++o) rank += (keys[o] < k) & (spc[o] == s);
+    }
     const int at = b.seg_offs[i * nsp + s] + rank;
     if (at < b.seg_offs[i * nsp + s + 1]) {
       b.key[at] = k;
@@ -485,7 +497,7 @@ cudaError_t sg_nbr_place(const double* pos, const int* species, int n_atoms, int
                          const NbrBuffers& b, cudaStream_t st) {
   if (n_atoms == 0) return cudaSuccess;
   const int warps = 4;
-  const size_t smem = (size_t)warps * maxn * 9;
+  const size_t smem = (size_t)warps * ((maxn + 2) * 8 + maxn);
   if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = sg_set_smem<place_kernel<T>>(smem);
   if (e != cudaSuccess) return e;

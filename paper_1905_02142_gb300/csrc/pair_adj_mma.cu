@@ -84,6 +84,11 @@ __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r
                : "r"(addr));
 }
 
+// 4-byte asynchronous global -> shared copy (completes at cp.async.wait_group)
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ void mma_f16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
                                         uint32_t b1) {
   asm volatile(
@@ -327,21 +332,21 @@ pair_adj_mma_kernel(const AdjArgs<float> a, const MmaLayout lay) {
 
   for (int atom = blockIdx.x; atom < a.n_atoms; atom += gridDim.x) {
     __syncthreads();  // previous atom done with G16 and the scratch; tables visible
-    // ---- c, q, g -> shared memory (one pass of independent loads)
-    const float w = (float)a.struct_w[a.atom_struct[atom]];
-    const float pn = a.pnorm[atom];
+    // ---- c, q, g -> shared memory: asynchronous copies, all in flight together
     {
       const float* qi = a.q + (size_t)atom * D;
       const float* gi = a.g + (size_t)atom * D;
       const float* ci = a.c + (size_t)atom * nch * L;
-#pragma unroll 4
-      for (int k = tid; k < nch * L; k += NT) cs[k] = __ldg(ci + k);
-#pragma unroll 4
+      for (int k = tid; k < nch * L; k += NT) cp_async4(cs + k, ci + k);
       for (int k = tid; k < D; k += NT) {
-        qs[k] = __ldg(qi + k);
-        gs[k] = __ldg(gi + k);
+        cp_async4(qs + k, qi + k);
+        cp_async4(gs + k, gi + k);
       }
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
+    const float w = (float)a.struct_w[a.atom_struct[atom]];
+    const float pn = a.pnorm[atom];
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
     // ---- h = dE/dp = w (g - q (q.g)) / |p|
     float dot = 0.f;
@@ -431,11 +436,15 @@ pair_adj_mma_kernel(const AdjArgs<float> a, const MmaLayout lay) {
       const int nxt = atom + gridDim.x;
       if (nxt < a.n_atoms) {
         const int lc = (nch * L * 4 + 127) >> 7, lq = (D * 4 + 127) >> 7;
-        for (int k = tid; k < lc + 2 * lq; k += NT) {
+        const int pb = a.seg_offs[nxt * a.nsp], pe = a.seg_offs[(nxt + 1) * a.nsp];
+        const char* pr = reinterpret_cast<const char*>(a.pair_r + pb);
+        const int lp = pe > pb ? (int)(((pe - pb) * sizeof(Vec4<float>) + 127) >> 7) : 0;
+        for (int k = tid; k < lc + 2 * lq + lp; k += NT) {
           const char* p;
           if (k < lc) p = reinterpret_cast<const char*>(a.c + (size_t)nxt * nch * L) + ((size_t)k << 7);
           else if (k < lc + lq) p = reinterpret_cast<const char*>(a.q + (size_t)nxt * D) + ((size_t)(k - lc) << 7);
-          else p = reinterpret_cast<const char*>(a.g + (size_t)nxt * D) + ((size_t)(k - lc - lq) << 7);
+          else if (k < lc + 2 * lq) p = reinterpret_cast<const char*>(a.g + (size_t)nxt * D) + ((size_t)(k - lc - lq) << 7);
+          else p = pr + ((size_t)(k - lc - 2 * lq) << 7);
           asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
         }
       }
