@@ -138,6 +138,53 @@ def algorithmic_flops(stage, n_pairs, n_atoms, w):
     return None
 
 
+def algorithmic_bytes(stage, n_pairs, n_atoms, w):
+    """Minimum DRAM bytes per launch of the memory-bound stages (definitions in the design doc)."""
+    L = (w.l_max + 1) ** 2
+    nch = w.n_max * w.n_species
+    d = nch * (nch + 1) // 2 * (w.l_max + 1)
+    if stage == "neighbours":      # positions in; key, j, separation vector, reverse index out
+        return 24.0 * n_atoms + (8 + 4 + 16 + 4) * n_pairs
+    if stage == "power_spectrum":  # c in, q out (FP32)
+        return 4.0 * (nch * L + d) * n_atoms
+    if stage == "finish":          # dE/dr twice, reverse index, forces out
+        return (2 * 16 + 4) * n_pairs + 24.0 * n_atoms
+    return None
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), float(pk["bf16_tflops"]), "measured (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, 1900.0, "fallback"
+
+
+def stage_rooflines(stages, n_pairs, n_atoms, w, sm_mhz):
+    """Per-stage roofline: achieved algorithmic rate over the stage's own bound."""
+    hbm, tc, src = load_peaks()
+    alu = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    out = {}
+    for k, ms in stages.items():
+        if ms <= 0:
+            continue
+        t = ms / 1e3
+        if k in ("gap_forward", "gap_backward"):
+            a = algorithmic_flops(k, n_pairs, n_atoms, w) / t / 1e12
+            out[k] = {"bound": "tensor", "achieved": a, "peak": tc, "unit": "TFLOP/s",
+                      "frac": a / tc, "peak_source": "FP16 dense = BF16 " + src}
+        elif k in ("pair_forward", "pair_adjoint"):
+            a = algorithmic_flops(k, n_pairs, n_atoms, w) / t / 1e12
+            out[k] = {"bound": "alu", "achieved": a, "peak": alu, "unit": "TFLOP/s",
+                      "frac": a / alu, "peak_source": FP32_PEAK_NOTE}
+        else:
+            a = algorithmic_bytes(k, n_pairs, n_atoms, w) / t / 1e9
+            out[k] = {"bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
+                      "frac": a / hbm, "peak_source": "copy bandwidth " + src}
+    return out
+
+
 # --------------------------------------------------------------------------- arms
 def profiled_traffic(w, stage, n_atoms):
     """DRAM bytes per launch of the dominant kernel from the committed ncu summary
@@ -383,6 +430,7 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "stated_err": STATED_ERR,
         "stages_ms": {k: round(v, 4) for k, v in stages.items()},
+        "stages_roofline": stage_rooflines(stages, n_pairs, n, w, sm_mhz),
         "graph": graph,
         "batched": batched,
         "fp64_path": fp64,
