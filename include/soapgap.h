@@ -177,6 +177,35 @@ int soapgap_sync_status(soapgap_handle* h, void* stream);
  * the warps chosen (0 on the FP64 path, which has nothing to tune).  Synchronises. */
 int soapgap_autotune(soapgap_handle* h, const soapgap_batch* batch, int32_t* choice, void* stream);
 
+/* Verlet skin (neighbour-list reuse).  skin >= 0 (A); 0 (the default) builds the list at
+ * every call.  With skin > 0 the list holds all pairs within r_cut + skin and is rebuilt only
+ * when an atom has moved by skin/2 or more since the positions of the last build (checked on
+ * the device at every call), or when the batch shape or a cell changed.  Between rebuilds
+ * every pair's separation is recomputed from its (j, S) and the current positions, and pairs
+ * beyond r_cut contribute exactly nothing, so results equal those of a fresh list up to the
+ * order of floating-point sums.  Asynchronous calls take the decision on the device (and
+ * are therefore capturable); the cell and the species must not change between them.
+ * soapgap_export_pairs returns the list (pairs within r_cut + skin).  Setting the skin
+ * forces a rebuild at the next call. */
+int soapgap_set_skin(soapgap_handle* h, double skin);
+
+/* Whether the last soapgap_compute rebuilt the neighbour list: 1 yes, 0 reused (skin),
+ * -1 decided on the device (asynchronous call with a skin). */
+int soapgap_last_rebuild(const soapgap_handle* h, int32_t* rebuilt);
+
+/* Velocity-Verlet half step for molecular dynamics around the evaluation (units: A, fs,
+ * amu, eV; 1 eV/(A amu) = 0.009648533212 A/fs^2), enqueued on `stream` (capturable):
+ *   v += (dt/2) F / m                           (drift = 0: the closing kick)
+ *   v += (dt/2) F / m;  x += dt v;  wrap       (drift != 0: kick and drift)
+ * where an atom whose fractional coordinates leave [0, 1) is mapped back into its cell.
+ * pos [n_atoms][3], vel [n_atoms][3] DEVICE double, updated in place; forces [n_atoms][3]
+ * DEVICE double (F = -dE/dx, as written by soapgap_compute); inv_mass [n_atoms] DEVICE
+ * double (1/amu).  Needs a preceding soapgap_compute of the same batch shape (it uses that
+ * call's cells).  One step: verlet(drift=1), compute(FORCES), verlet(drift=0). */
+int soapgap_verlet(soapgap_handle* h, const soapgap_batch* batch, double* pos, double* vel,
+                   const double* forces, const double* inv_mass, double dt, int32_t drift,
+                   void* stream);
+
 /* Adjoint of the last ENERGY evaluation on this handle, for the same batch:
  * dE_dEstruct [n_struct] DEVICE double (weights of each structure's energy);
  * grad_pos [n_atoms][3] DEVICE double receives d(sum_s w_s E_s)/dx (i.e. minus the

@@ -68,6 +68,10 @@ SIGNATURES = {
     "soapgap_sync_status": (ctypes.c_int, [c_void_p, c_void_p]),
     "soapgap_autotune": (ctypes.c_int, [c_void_p, ctypes.POINTER(Batch), ctypes.POINTER(c_int32),
                                         c_void_p]),
+    "soapgap_set_skin": (ctypes.c_int, [c_void_p, c_double]),
+    "soapgap_last_rebuild": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_int32)]),
+    "soapgap_verlet": (ctypes.c_int, [c_void_p, ctypes.POINTER(Batch), c_void_p, c_void_p, c_void_p,
+                                      c_void_p, c_double, c_int32, c_void_p]),
     "soapgap_last_error": (ctypes.c_char_p, [c_void_p]),
     "soapgap_destroy": (None, [c_void_p]),
 }

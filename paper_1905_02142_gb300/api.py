@@ -146,6 +146,25 @@ class SoapGap:
             _ptr(out.get("virial")), st))
         return out
 
+    def set_skin(self, skin: float):
+        """Verlet skin in A (0 disables neighbour-list reuse); see soapgap_set_skin."""
+        self._check(self.lib.soapgap_set_skin(self.h, float(skin)))
+
+    def last_rebuild(self) -> int:
+        """1 if the last compute rebuilt the neighbour list, 0 if it reused it, -1 if the
+        device decided (asynchronous call with a skin)."""
+        r = ctypes.c_int32()
+        self._check(self.lib.soapgap_last_rebuild(self.h, ctypes.byref(r)))
+        return int(r.value)
+
+    def verlet(self, s: "Structures", vel, forces, inv_mass, dt, drift: bool, stream=None):
+        """Velocity-Verlet half step in place on s.pos and vel (see soapgap_verlet)."""
+        st = (stream or torch.cuda.current_stream(s.pos.device)).cuda_stream
+        b = s.c_batch()
+        self._check(self.lib.soapgap_verlet(self.h, ctypes.byref(b), _ptr(s.pos), _ptr(vel),
+                                            _ptr(forces), _ptr(inv_mass), float(dt),
+                                            1 if drift else 0, st))
+
     def sync_status(self, stream=None):
         """Wait for the stream; raise SoapGapError if the last asynchronous call flagged a
         device-side error (pair capacity, atom outside its cell, coincident atoms)."""
@@ -272,3 +291,56 @@ class CapturedEvaluation:
     def replay(self):
         self.graph.replay()
         return self.out
+
+
+AMU_A2_PER_FS2_IN_EV = 103.642697  # 1 amu A^2 / fs^2 in eV
+
+
+class VelocityVerlet:
+    """Microcanonical molecular dynamics around the evaluation (units A, fs, amu, eV).
+
+    Each step: kick + drift (library kernel), forces and energies at the new positions
+    (soapgap_compute; the neighbour list is reused while the model's Verlet skin allows),
+    closing kick.  With capture=True one step is captured in a CUDA graph and replayed.
+    """
+
+    def __init__(self, model: SoapGap, s: Structures, masses, dt: float, vel=None,
+                 capture: bool = False):
+        self.model, self.s, self.dt = model, s, float(dt)
+        dev = s.pos.device
+        m = torch.as_tensor(np.asarray(masses, dtype=np.float64), device=dev).reshape(-1)
+        if m.numel() == 1:
+            m = m.expand(s.n_atoms).contiguous()
+        self.mass = m
+        self.inv_mass = (1.0 / m).contiguous()
+        self.vel = (torch.zeros((s.n_atoms, 3), dtype=torch.float64, device=dev) if vel is None
+                    else torch.as_tensor(vel, dtype=torch.float64, device=dev).clone().contiguous())
+        self.out = model.compute(s, energy=True, forces=True)
+        self.f = self.out["forces"].clone()     # forces of the current positions
+        self.graph = None
+        if capture:
+            # the synchronous compute above sized the workspace of the captured calls
+            torch.cuda.synchronize()
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph):
+                self._step(asynchronous=True)
+
+    def _step(self, asynchronous):
+        self.model.verlet(self.s, self.vel, self.f, self.inv_mass, self.dt, drift=True)
+        self.out = self.model.compute(self.s, energy=True, forces=True, asynchronous=asynchronous)
+        self.f.copy_(self.out["forces"])
+        self.model.verlet(self.s, self.vel, self.f, self.inv_mass, self.dt, drift=False)
+
+    def step(self, n: int = 1):
+        for _ in range(n):
+            if self.graph is not None:
+                self.graph.replay()
+            else:
+                self._step(asynchronous=False)
+        return self
+
+    def potential_energy(self) -> float:
+        return float(self.out["e_struct"].sum())
+
+    def kinetic_energy(self) -> float:
+        return float(0.5 * AMU_A2_PER_FS2_IN_EV * (self.mass[:, None] * self.vel ** 2).sum())

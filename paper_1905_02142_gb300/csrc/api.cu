@@ -97,6 +97,14 @@ struct soapgap_handle {
   Buf geom, atom_offs, atom_struct, atom_bin, atom_bin4, atom_slot, bin_count, bin_start, bin_atoms, binpos,
       atom_hi, atom_lo;
   Buf seg_count, seg_offs, scan_tmp, key_tmp, key, pair_j, pair_r, rev, dedr, slot_count, max_count;
+  // Verlet skin: the list holds pairs within r_cut + skin and is reused while no atom has
+  // moved by skin/2 since the positions pos_ref of its build
+  double skin = 0.0;
+  Buf pos_ref, skin_flag;
+  bool ref_valid = false;
+  int ref_atoms = -1, ref_struct = -1;
+  std::vector<double> ref_cell;
+  int last_rebuild = -1;    // 1 / 0 for synchronous calls, -1 when decided on the device
   int slot_maxn = 0;        // slot capacity per atom of the last synchronous neighbour search
   int cur_maxn = 0;         // slot capacity used by the current call
   int slot_maxn_est = 0;    // estimate for the current batch (from its densities)
@@ -363,7 +371,7 @@ static int setup_geometry(soapgap_handle* h, const soapgap_batch* b) {
     CK(h, cudaMallocHost(&h->h_geom, sizeof(StructGeom) * (size_t)S));
     h->h_geom_cap = S;
   }
-  const double rc = h->prm.r_cut;
+  const double rc = h->prm.r_cut + h->skin;  // list radius
   int bins = 0, max_atoms = 0;
   double slot_est = 0.0;
   for (int s = 0; s < S; ++s) {
@@ -544,7 +552,33 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
   nb.seg_offs = (int*)h->seg_offs.p;
   nb.scan_tmp = (int*)h->scan_tmp.p;
   nb.err = (int*)h->err.p;
-  if (!backward) {
+  nb.run = nullptr;
+  nb.rc2_mask = h->skin > 0.0 ? h->prm.r_cut * h->prm.r_cut : 0.0;
+  // Verlet skin: reuse the list while no atom has moved by skin/2 since its build
+  bool rebuild = true, device_decides = false;
+  if (!backward && h->skin > 0.0) {
+    ENS(h, h->skin_flag, sizeof(int));
+    ENS(h, h->pos_ref, sizeof(double) * 3 * N1n);
+    const bool same = h->ref_valid && h->ref_atoms == N && h->ref_struct == S &&
+                      h->ref_cell.size() == (size_t)9 * S &&
+                      std::memcmp(h->ref_cell.data(), b->cell_host, sizeof(double) * 9 * S) == 0;
+    if (same) {
+      CK(h, cudaMemsetAsync(h->skin_flag.p, 0, sizeof(int), st));
+      CK(h, sg_skin_check(b->pos, (const double*)h->pos_ref.p, N, 0.5 * h->skin, (int*)h->skin_flag.p, st));
+      if (h->async_call) {
+        device_decides = true;
+        nb.run = (const int*)h->skin_flag.p;
+      } else {
+        CK(h, cudaMemcpyAsync(h->h_count, h->skin_flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(h, cudaStreamSynchronize(st));
+        rebuild = h->h_count[0] != 0;
+      }
+    } else if (h->async_call) {
+      return fail(h, SOAPGAP_E_STATE, "no neighbour list to reuse for an asynchronous call: make one synchronous call with the same batch first");
+    }
+  }
+  h->last_rebuild = device_decides ? -1 : (rebuild ? 1 : 0);
+  if (!backward && (rebuild || device_decides)) {
     // one sweep over the candidates into per-atom slot arrays; a synchronous call retries
     // once with the measured largest count if the density estimate was too small
     int maxn = h->async_call ? h->slot_maxn : h->slot_maxn_est;
@@ -558,7 +592,7 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     for (int attempt = 0; attempt < 2; ++attempt) {
       ENS(h, h->key_tmp, 8 * N1n * (size_t)maxn);
       nb.key_tmp = (unsigned long long*)h->key_tmp.p;
-      CK(h, sg_nbr_slots(b->pos, b->species, N, nsp, h->prm.r_cut, maxn, nb, st));
+      CK(h, sg_nbr_slots(b->pos, b->species, N, nsp, h->prm.r_cut + h->skin, maxn, nb, st));
       if (h->async_call) break;
       CK(h, cudaMemcpyAsync(h->h_count, (int*)h->seg_offs.p + N * nsp, sizeof(int), cudaMemcpyDeviceToHost, st));
       CK(h, cudaMemcpyAsync(h->h_count + 1, h->max_count.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -580,7 +614,7 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     mark(h, EV_NB1, st);
   }
   long long P = h->last_pairs;
-  if (h->async_call && !backward) {
+  if (h->async_call && !backward) {  // (with a skin, the guard itself runs only on rebuilds)
     // the pair count is not read back: the pair buffers' capacity bounds it, and a
     // device-side guard empties every segment (and flags SG_ERR_PAIR_CAPACITY) if the
     // count exceeds it or a slot array overflowed
@@ -596,7 +630,7 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
       cap = std::min(cap, (long long)(h->dedr.cap / sizeof(Vec4<T>)));
     }
     P = cap;
-    CK(h, sg_nbr_cap_guard((int*)h->seg_offs.p, N * nsp, P, (int*)h->err.p, st));
+    CK(h, sg_nbr_cap_guard((int*)h->seg_offs.p, N * nsp, P, (int*)h->err.p, st, nb.run));
   }
   const size_t Pc = (size_t)std::max(P, 1LL);
   ENS(h, h->key, 8 * Pc);
@@ -617,11 +651,26 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
   ENS(h, h->pnorm, es * N1);
   if (!backward) {
     mark(h, EV_FILL0, st);
-    {
+    if (rebuild || device_decides) {
       cudaError_t e = sg_nbr_place<T>(b->pos, b->species, N, nsp, h->cur_maxn, nb, st);
       if (e == cudaErrorInvalidConfiguration)
         return fail(h, SOAPGAP_E_UNSUPPORTED, "too many neighbours per atom for the pair sort");
       CK(h, e);
+    }
+    if (h->skin > 0.0) {
+      if (device_decides) {
+        // reuse steps refresh the separations; rebuild steps take the new reference
+        CK(h, sg_nbr_refresh<T>(b->pos, N, nsp, nb, (const int*)h->skin_flag.p, st));
+        CK(h, sg_skin_ref_update(b->pos, (double*)h->pos_ref.p, N, (const int*)h->skin_flag.p, st));
+      } else if (!rebuild) {
+        CK(h, sg_nbr_refresh<T>(b->pos, N, nsp, nb, nullptr, st));
+      } else {
+        CK(h, cudaMemcpyAsync(h->pos_ref.p, b->pos, sizeof(double) * 3 * (size_t)N, cudaMemcpyDeviceToDevice, st));
+        h->ref_valid = true;
+        h->ref_atoms = N;
+        h->ref_struct = S;
+        h->ref_cell.assign(b->cell_host, b->cell_host + 9 * (size_t)S);
+      }
     }
     mark(h, EV_FWD0, st);
     h->stage_ran[0] = h->stage_ran[1] = h->stage_ran[2] = true;
@@ -905,7 +954,7 @@ extern "C" void soapgap_destroy(soapgap_handle* h) {
                  &h->binpos, &h->atom_hi, &h->atom_lo, &h->seg_count, &h->seg_offs, &h->scan_tmp, &h->key_tmp,
                  &h->key, &h->pair_j, &h->pair_r, &h->rev, &h->dedr, &h->c, &h->q, &h->pnorm,
                  &h->e_atom, &h->eps_part, &h->kp, &h->g, &h->vir_atom, &h->struct_w, &h->err,
-                 &h->finish_part, &h->slot_count, &h->max_count,
+                 &h->finish_part, &h->slot_count, &h->max_count, &h->pos_ref, &h->skin_flag,
                  &h->cen_tmp, &h->host_in_pos, &h->host_in_species, &h->host_q, &h->host_pnorm,
                  &h->host_e_atom, &h->host_e_struct, &h->host_forces, &h->host_virial};
   for (Buf* b : bufs)
@@ -984,6 +1033,37 @@ extern "C" int soapgap_autotune(soapgap_handle* h, const soapgap_batch* batch, i
     if (best) h->adj_warps[adj_key(h, N, h->last_pairs)] = best;
   }
   if (choice) *choice = best;
+  h->msg.clear();
+  return SOAPGAP_OK;
+}
+
+extern "C" int soapgap_set_skin(soapgap_handle* h, double skin) {
+  if (!h) return SOAPGAP_E_INVALID_ARG;
+  if (!(skin >= 0.0) || !std::isfinite(skin)) return fail(h, SOAPGAP_E_INVALID_ARG, "skin must be >= 0");
+  h->skin = skin;
+  h->ref_valid = false;  // the next call rebuilds with the new list radius
+  h->msg.clear();
+  return SOAPGAP_OK;
+}
+
+extern "C" int soapgap_last_rebuild(const soapgap_handle* h, int32_t* rebuilt) {
+  if (!h || !rebuilt) return SOAPGAP_E_INVALID_ARG;
+  *rebuilt = h->last_rebuild;
+  return SOAPGAP_OK;
+}
+
+extern "C" int soapgap_verlet(soapgap_handle* h, const soapgap_batch* batch, double* pos, double* vel,
+                              const double* forces, const double* inv_mass, double dt, int32_t drift,
+                              void* stream) {
+  if (!h) return SOAPGAP_E_INVALID_ARG;
+  int rc = check_batch(h, batch);
+  if (rc != SOAPGAP_OK) return rc;
+  if (!pos || !vel || !forces || !inv_mass || !std::isfinite(dt))
+    return fail(h, SOAPGAP_E_INVALID_ARG, "verlet needs pos, vel, forces, inv_mass and a finite dt");
+  if (h->fw_atoms != batch->n_atoms || h->fw_struct != batch->n_struct)
+    return fail(h, SOAPGAP_E_STATE, "verlet needs a preceding evaluation of the same batch");
+  CK(h, sg_verlet(batch->n_atoms, pos, vel, forces, inv_mass, dt, drift != 0,
+                  (const int*)h->atom_struct.p, (const StructGeom*)h->geom.p, (cudaStream_t)stream));
   h->msg.clear();
   return SOAPGAP_OK;
 }

@@ -159,3 +159,58 @@ template cudaError_t sg_finish<float>(int, int, int, const int64_t*, const int*,
 template cudaError_t sg_finish<double>(int, int, int, const int64_t*, const int*, const int*,
                                        const Vec4<double>*, const double*, int, const double*,
                                        double*, double*, double*, double*, bool, int, double*, cudaStream_t);
+
+// ---------------------------------------------------------------- velocity Verlet
+// Units: positions A, velocities A/fs, forces eV/A, masses amu, time fs.
+// 1 eV/(A amu) = 0.009648533212 A/fs^2.
+#define SG_EV_PER_AMU_A2_FS2 0.009648533212
+
+// kick: v += (dt/2) F/m;  with drift: then x += dt v, and an atom whose fractional
+// coordinates left [0, 1) is mapped back into its cell (x = f h with f mod 1)
+__global__ void verlet_kernel(int n, double* __restrict__ pos, double* __restrict__ vel,
+                              const double* __restrict__ forces, const double* __restrict__ inv_mass,
+                              double dt, int drift, const int* __restrict__ atom_struct,
+                              const StructGeom* __restrict__ geom) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double kick = 0.5 * dt * SG_EV_PER_AMU_A2_FS2 * inv_mass[i];
+  double v[3], x[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) v[c] = vel[3 * i + c] + kick * forces[3 * i + c];
+  if (drift) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) x[c] = pos[3 * i + c] + dt * v[c];
+    const StructGeom& g = geom[atom_struct[i]];
+    double f[3];
+    bool out = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      f[k] = x[0] * g.hinv[k] + x[1] * g.hinv[3 + k] + x[2] * g.hinv[6 + k];
+      out |= !(f[k] >= 0.0 && f[k] < 1.0);
+    }
+    if (out) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        f[k] -= floor(f[k]);
+        if (f[k] >= 1.0) f[k] = 0.0;
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) x[c] = f[0] * g.h[c] + f[1] * g.h[3 + c] + f[2] * g.h[6 + c];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) pos[3 * i + c] = x[c];
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) vel[3 * i + c] = v[c];
+}
+
+cudaError_t sg_verlet(int n, double* pos, double* vel, const double* forces, const double* inv_mass,
+                      double dt, bool drift, const int* atom_struct, const StructGeom* geom,
+                      cudaStream_t st) {
+  if (n > 0) {
+    verlet_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, pos, vel, forces, inv_mass, dt, drift ? 1 : 0,
+                                                    atom_struct, geom);
+    ++sg_kernel_launches;
+  }
+  return cudaGetLastError();
+}

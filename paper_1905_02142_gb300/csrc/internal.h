@@ -72,9 +72,14 @@ struct NbrBuffers {
   int* rev;                  // [cap]
   int* scan_tmp;             // scan scratch
   int* err;                  // device error word
+  const int* run;            // if set and *run == 0, the list-building kernels return at once
+                             // (neighbour-list reuse decided on the device)
+  double rc2_mask;           // > 0: pairs with |r|^2 >= rc2_mask get |r| = -1 (beyond r_cut
+                             // in a list built with a skin); 0: no masking
 };
 size_t sg_scan_tmp_ints(int n);
-cudaError_t sg_exclusive_scan(const int* in, int* out, int n, int* tmp, cudaStream_t st);
+cudaError_t sg_exclusive_scan(const int* in, int* out, int n, int* tmp, cudaStream_t st,
+                              const int* run = nullptr);
 cudaError_t sg_nbr_bin(const double* pos, int n_atoms, int n_bins, const NbrBuffers& b,
                        cudaStream_t st);
 // one sweep over the candidates: per-atom slot arrays of keys (capacity maxn), counts per
@@ -83,7 +88,18 @@ cudaError_t sg_nbr_slots(const double* pos, const int* species, int n_atoms, int
                          int maxn, const NbrBuffers& b, cudaStream_t st);
 // asynchronous calls: empty all segments and flag SG_ERR_PAIR_CAPACITY if seg_offs[nseg] > cap
 // or a slot array overflowed
-cudaError_t sg_nbr_cap_guard(int* seg_offs, int nseg, long long cap, int* err, cudaStream_t st);
+cudaError_t sg_nbr_cap_guard(int* seg_offs, int nseg, long long cap, int* err, cudaStream_t st,
+                             const int* run = nullptr);
+// Verlet skin: rebuild[0] |= 1 if an atom moved by skin/2 or more since the positions `ref`
+// of the last build; refresh recomputes every pair's separation from its key and the current
+// positions (masked beyond r_cut), unless *rebuilt; ref_update copies pos to ref if *rebuild
+cudaError_t sg_skin_check(const double* pos, const double* ref, int n, double half_skin,
+                          int* rebuild, cudaStream_t st);
+template <typename T>
+cudaError_t sg_nbr_refresh(const double* pos, int n_atoms, int nsp, const NbrBuffers& b,
+                           const int* rebuilt, cudaStream_t st);
+cudaError_t sg_skin_ref_update(const double* pos, double* ref, int n, const int* rebuild,
+                               cudaStream_t st);
 // keys ranked into their segments with j and the separation vectors, then the reverse index
 template <typename T>
 cudaError_t sg_nbr_place(const double* pos, const int* species, int n_atoms, int nsp, int maxn,
@@ -175,6 +191,10 @@ int sg_adj_batches_per_atom(long long n_pairs, int n_atoms, int nsp);
 // ---------------------------------------------------------------- forces.cu
 // chunks per structure of the two-level per-structure sums (part: [S][chunks][10] doubles)
 int sg_finish_chunks(int max_struct_atoms);
+// velocity-Verlet half step (kick; with drift also the position update and cell wrap)
+cudaError_t sg_verlet(int n, double* pos, double* vel, const double* forces, const double* inv_mass,
+                      double dt, bool drift, const int* atom_struct, const StructGeom* geom,
+                      cudaStream_t st);
 template <typename T>
 cudaError_t sg_finish(int n_atoms, int n_struct, int nsp, const int64_t* atom_offs_dev,
                       const int* seg_offs, const int* rev, const Vec4<T>* dedr,

@@ -17,7 +17,8 @@
 #define SCAN_BLOCK 1024
 size_t sg_scan_tmp_ints(int n) { return (size_t)(n + SCAN_BLOCK - 1) / SCAN_BLOCK + 1; }
 
-__global__ void scan_block_sums(const int* in, int n, int* sums) {
+__global__ void scan_block_sums(const int* in, int n, int* sums, const int* run) {
+  if (run && *run == 0) return;
   __shared__ int sh[32];
   int i = blockIdx.x * SCAN_BLOCK + threadIdx.x;
   int v = 0;
@@ -37,7 +38,8 @@ __global__ void scan_block_sums(const int* in, int n, int* sums) {
 }
 
 // single block: exclusive scan of the block sums in place (nb <= a few thousand)
-__global__ void scan_sums(int* sums, int nb) {
+__global__ void scan_sums(int* sums, int nb, const int* run) {
+  if (run && *run == 0) return;
   __shared__ int carry;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
@@ -64,7 +66,8 @@ __global__ void scan_sums(int* sums, int nb) {
   if (threadIdx.x == 0) sums[nb] = carry;
 }
 
-__global__ void scan_apply(const int* in, int* out, int n, const int* sums) {
+__global__ void scan_apply(const int* in, int* out, int n, const int* sums, const int* run) {
+  if (run && *run == 0) return;
   __shared__ int sh[SCAN_BLOCK];
   const int base = blockIdx.x * SCAN_BLOCK;
   for (int k = threadIdx.x; k < SCAN_BLOCK; k += blockDim.x) sh[k] = (base + k < n) ? in[base + k] : 0;
@@ -92,21 +95,23 @@ __global__ void scan_apply(const int* in, int* out, int n, const int* sums) {
 }
 
 // out[0..n] = exclusive scan of in[0..n-1], out[n] = total.  tmp: sg_scan_tmp_ints(n) ints.
-cudaError_t sg_exclusive_scan(const int* in, int* out, int n, int* tmp, cudaStream_t st) {
+cudaError_t sg_exclusive_scan(const int* in, int* out, int n, int* tmp, cudaStream_t st,
+                              const int* run) {
   if (n <= 0) {
-    cudaMemsetAsync(out, 0, sizeof(int), st);
+    if (!run) cudaMemsetAsync(out, 0, sizeof(int), st);
     return cudaGetLastError();
   }
   const int nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
-  scan_block_sums<<<nb, 256, 0, st>>>(in, n, tmp);
-  scan_sums<<<1, 1024, 0, st>>>(tmp, nb);
-  scan_apply<<<nb, 256, 0, st>>>(in, out, n, tmp);
+  scan_block_sums<<<nb, 256, 0, st>>>(in, n, tmp, run);
+  scan_sums<<<1, 1024, 0, st>>>(tmp, nb, run);
+  scan_apply<<<nb, 256, 0, st>>>(in, out, n, tmp, run);
   sg_kernel_launches += 3;
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- binning
 __global__ void bin_assign(const double* __restrict__ pos, int n, NbrBuffers b) {
+  if (b.run && *b.run == 0) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const StructGeom& g = b.geom[b.atom_struct[i]];
@@ -129,6 +134,7 @@ __global__ void bin_assign(const double* __restrict__ pos, int n, NbrBuffers b) 
 }
 
 __global__ void bin_fill(const double* __restrict__ pos, int n, NbrBuffers b, float4* binpos) {
+  if (b.run && *b.run == 0) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int at = b.bin_start[b.atom_bin[i]] + b.atom_slot[i];
@@ -148,7 +154,7 @@ cudaError_t sg_nbr_bin(const double* pos, int n_atoms, int n_bins, const NbrBuff
     bin_assign<<<(n_atoms + 255) / 256, 256, 0, st>>>(pos, n_atoms, b);
     ++sg_kernel_launches;
   }
-  cudaError_t e = sg_exclusive_scan(b.bin_count, b.bin_start, n_bins, b.scan_tmp, st);
+  cudaError_t e = sg_exclusive_scan(b.bin_count, b.bin_start, n_bins, b.scan_tmp, st, b.run);
   if (e != cudaSuccess) return e;
   if (n_atoms > 0) {
     bin_fill<<<(n_atoms + 255) / 256, 256, 0, st>>>(pos, n_atoms, b, b.binpos);
@@ -335,6 +341,7 @@ struct FillSlots {
 __global__ void fill_slots_kernel(const double* __restrict__ pos, const int* __restrict__ species,
                                   int n, int nsp, double rc, int maxn, NbrBuffers b,
                                   const float4* binpos) {
+  if (b.run && *b.run == 0) return;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n) return;
@@ -367,7 +374,7 @@ cudaError_t sg_nbr_slots(const double* pos, const int* species, int n_atoms, int
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return sg_exclusive_scan(b.seg_count, b.seg_offs, n_atoms * nsp, b.scan_tmp, st);
+  return sg_exclusive_scan(b.seg_count, b.seg_offs, n_atoms * nsp, b.scan_tmp, st, b.run);
 }
 
 // Separation r = x_j + S.h - x_i of pair (i, j, S), exactly antisymmetric under
@@ -400,7 +407,26 @@ __device__ __forceinline__ Vec4<T> pair_vector(const double* __restrict__ pos, c
     v.x = out[0];
     v.y = out[1];
     v.z = out[2];
-    v.w = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
+    const float d2f = v.x * v.x + v.y * v.y + v.z * v.z;
+    v.w = sqrtf(d2f);
+    if (b.rc2_mask > 0.0) {
+      // beyond r_cut (list built with a skin): decided like the list itself, FP32 away from
+      // the cutoff (the double-float vector is within 2 ulp), the FP64 expression near it
+      const float rc2f = (float)b.rc2_mask;
+      bool beyond;
+      if (fabsf(d2f - rc2f) > 16.f * 5.9604645e-8f * rc2f) {
+        beyond = d2f >= rc2f;
+      } else {
+        double s[3], r[3], d2;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          s[c] = __dadd_rn(__dadd_rn(__dmul_rn((double)S1, g.h[c]), __dmul_rn((double)S2, g.h[3 + c])),
+                           __dmul_rn((double)S3, g.h[6 + c]));
+        exact_sep(pos, i, j, s, canon, r, d2);
+        beyond = d2 >= b.rc2_mask;
+      }
+      if (beyond) v.w = -1.f;
+    }
   } else {
     double s[3], r[3], d2;
 #pragma unroll
@@ -411,7 +437,7 @@ __device__ __forceinline__ Vec4<T> pair_vector(const double* __restrict__ pos, c
     v.x = r[0];
     v.y = r[1];
     v.z = r[2];
-    v.w = sqrt(d2);
+    v.w = (b.rc2_mask > 0.0 && d2 >= b.rc2_mask) ? -1.0 : sqrt(d2);
   }
   return v;
 }
@@ -424,6 +450,7 @@ template <typename T>
 __global__ void place_kernel(int n, int nsp, int maxn, const double* __restrict__ pos,
                              const int* __restrict__ species, NbrBuffers b, Vec4<T>* rout) {
   extern __shared__ __align__(16) unsigned long long sk[];
+  if (b.run && *b.run == 0) return;
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * (blockDim.x >> 5) + wib;
   const int kstride = maxn + 2;  // one padding key, 16-byte aligned rows
@@ -469,6 +496,7 @@ __global__ void place_kernel(int n, int nsp, int maxn, const double* __restrict_
 
 // reverse index: pair (i, j, S) -> position of (j, i, -S) in segment (j, species(i))
 __global__ void rev_kernel(int n, int nsp, const int* __restrict__ species, NbrBuffers b) {
+  if (b.run && *b.run == 0) return;
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= n) return;
@@ -518,7 +546,8 @@ template cudaError_t sg_nbr_place<double>(const double*, const int*, int, int, i
 // Pair-capacity guard of asynchronous calls: if the pair count (the last offset) exceeds
 // the capacity, every segment is emptied and SG_ERR_PAIR_CAPACITY is raised, so that no
 // later kernel indexes past the pair buffers.  One block: the decision is taken once.
-__global__ void cap_guard_kernel(int* seg_offs, int nseg, long long cap, int* err) {
+__global__ void cap_guard_kernel(int* seg_offs, int nseg, long long cap, int* err, const int* run) {
+  if (run && *run == 0) return;
   __shared__ int over;
   if (threadIdx.x == 0) {
     over = (long long)seg_offs[nseg] > cap || (*(volatile int*)err & SG_ERR_PAIR_CAPACITY) != 0;
@@ -529,8 +558,91 @@ __global__ void cap_guard_kernel(int* seg_offs, int nseg, long long cap, int* er
   for (int k = threadIdx.x; k <= nseg; k += blockDim.x) seg_offs[k] = 0;
 }
 
-cudaError_t sg_nbr_cap_guard(int* seg_offs, int nseg, long long cap, int* err, cudaStream_t st) {
-  cap_guard_kernel<<<1, 1024, 0, st>>>(seg_offs, nseg, cap, err);
+cudaError_t sg_nbr_cap_guard(int* seg_offs, int nseg, long long cap, int* err, cudaStream_t st,
+                             const int* run) {
+  cap_guard_kernel<<<1, 1024, 0, st>>>(seg_offs, nseg, cap, err, run);
   ++sg_kernel_launches;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- Verlet skin
+__global__ void skin_check_kernel(const double* __restrict__ pos, const double* __restrict__ ref, int n,
+                                  double h2, int* rebuild) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double dx = pos[3 * i] - ref[3 * i], dy = pos[3 * i + 1] - ref[3 * i + 1],
+               dz = pos[3 * i + 2] - ref[3 * i + 2];
+  if (dx * dx + dy * dy + dz * dz >= h2) *rebuild = 1;
+}
+
+cudaError_t sg_skin_check(const double* pos, const double* ref, int n, double half_skin,
+                          int* rebuild, cudaStream_t st) {
+  if (n > 0) {
+    skin_check_kernel<<<(n + 255) / 256, 256, 0, st>>>(pos, ref, n, half_skin * half_skin, rebuild);
+    ++sg_kernel_launches;
+  }
+  return cudaGetLastError();
+}
+
+// every pair of the (reused) list: separation from its key and the current positions
+template <typename T>
+__global__ void refresh_kernel(int n, int nsp, const double* __restrict__ pos, NbrBuffers b,
+                               const int* rebuilt, Vec4<T>* rout) {
+  if (rebuilt && *rebuilt) return;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  const int beg = b.seg_offs[i * nsp], end = b.seg_offs[(i + 1) * nsp];
+  for (int p = beg + lane; p < end; p += 32) {
+    const unsigned long long k = b.key[p];
+    const int j = (int)(k >> 24);
+    const int s1 = (int)((k >> 16) & 255) - 128, s2 = (int)((k >> 8) & 255) - 128,
+              s3 = (int)(k & 255) - 128;
+    rout[p] = pair_vector<T>(pos, b, i, j, s1, s2, s3);
+  }
+}
+
+// FP32 high / low words of the current positions (the double-float separations read them)
+__global__ void split_positions_kernel(const double* __restrict__ pos, int n, NbrBuffers b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+  const float xh = (float)x, yh = (float)y, zh = (float)z;
+  b.atom_hi[i] = make_float4(xh, yh, zh, 0.f);
+  b.atom_lo[i] = make_float4((float)(x - (double)xh), (float)(y - (double)yh), (float)(z - (double)zh), 0.f);
+}
+
+template <typename T>
+cudaError_t sg_nbr_refresh(const double* pos, int n_atoms, int nsp, const NbrBuffers& b,
+                           const int* rebuilt, cudaStream_t st) {
+  if (n_atoms == 0) return cudaSuccess;
+  if constexpr (sizeof(T) == 4) {
+    split_positions_kernel<<<(n_atoms + 255) / 256, 256, 0, st>>>(pos, n_atoms, b);
+    ++sg_kernel_launches;
+  }
+  const int threads = 128;
+  const long long blocks = ((long long)n_atoms * 32 + threads - 1) / threads;
+  refresh_kernel<T><<<(unsigned)blocks, threads, 0, st>>>(n_atoms, nsp, pos, b, rebuilt,
+                                                          reinterpret_cast<Vec4<T>*>(b.pair_r));
+  ++sg_kernel_launches;
+  return cudaGetLastError();
+}
+template cudaError_t sg_nbr_refresh<float>(const double*, int, int, const NbrBuffers&, const int*,
+                                           cudaStream_t);
+template cudaError_t sg_nbr_refresh<double>(const double*, int, int, const NbrBuffers&, const int*,
+                                            cudaStream_t);
+
+__global__ void skin_ref_kernel(const double* __restrict__ pos, double* ref, int n3, const int* rebuild) {
+  if (rebuild && *rebuild == 0) return;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n3) ref[k] = pos[k];
+}
+
+cudaError_t sg_skin_ref_update(const double* pos, double* ref, int n, const int* rebuild,
+                               cudaStream_t st) {
+  if (n > 0) {
+    skin_ref_kernel<<<(3 * n + 255) / 256, 256, 0, st>>>(pos, ref, 3 * n, rebuild);
+    ++sg_kernel_launches;
+  }
   return cudaGetLastError();
 }

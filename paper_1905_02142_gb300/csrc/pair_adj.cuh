@@ -135,8 +135,10 @@ pair_adj_kernel(const AdjArgs<T> a, int smem_per_warp) {
         T bn[NC], dbn[NC];
         T ux = 0, uy = 0, uz = 1, r = 1, inv = 1;
         Vec4<T> v{};
-        if (valid) {
-          v = a.pair_r[pidx];
+        if (valid) v = a.pair_r[pidx];
+        // |r| < 0 marks a pair beyond r_cut in a list built with a skin: dE/dr = 0
+        const bool live = valid && v.w >= T(0);
+        if (live) {
           r = v.w;
           inv = T(1) / r;
           ux = v.x * inv; uy = v.y * inv; uz = v.z * inv;
@@ -236,7 +238,8 @@ pair_adj_kernel(const AdjArgs<T> a, int smem_per_warp) {
             }
           }
         }
-        if (valid) {
+        if (valid && !live) a.dedr[pidx] = Vec4<T>{T(0), T(0), T(0), T(0)};
+        if (live) {
           const T hdot = hx * ux + hy * uy + hz * uz;
           Vec4<T> o;
           o.x = ux * srad + (hx - hdot * ux) * inv;

@@ -465,8 +465,10 @@ pair_adj_mma_kernel(const AdjArgs<float> a, const MmaLayout lay) {
         const bool valid = pidx < end;
         float ux = 0.f, uy = 0.f, uz = 1.f, r = 1.f, inv_r = 1.f;
         Vec4<float> v{};
-        if (valid) {
-          v = a.pair_r[pidx];
+        if (valid) v = a.pair_r[pidx];
+        // |r| < 0 marks a pair beyond r_cut in a list built with a skin: dE/dr = 0
+        const bool live = valid && v.w >= 0.f;
+        if (live) {
           r = v.w;
           inv_r = 1.f / r;
           ux = v.x * inv_r;
@@ -481,7 +483,7 @@ pair_adj_mma_kernel(const AdjArgs<float> a, const MmaLayout lay) {
           float bmax = 0.f;
 #pragma unroll
           for (int n = 0; n < NC; ++n) {
-            const bool on = valid && (EXACT || n < nmax);
+            const bool on = live && (EXACT || n < nmax);
             bn[n] = on ? f[n] : 0.f;
             dbn[n] = on ? df[n] : 0.f;
             bmax = fmaxf(bmax, fmaxf(fabsf(bn[n]), fabsf(dbn[n])));
@@ -617,7 +619,8 @@ pair_adj_mma_kernel(const AdjArgs<float> a, const MmaLayout lay) {
           }
         }
         }  // rolled sweep
-        if (valid) {
+        if (valid && !live) a.dedr[pidx] = Vec4<float>{0.f, 0.f, 0.f, 0.f};
+        if (live) {
           const float inv_s = ldexpf(1.f, eg + eb - 28);
           srad *= inv_s;
           hx *= inv_s;

@@ -47,8 +47,10 @@ pair_fwd_kernel(const FwdArgs<T> a) {
         const int pidx = base + lane;
         if (pidx < end) {
           const Vec4<T> v = a.pair_r[pidx];
-          const T r = v.w, inv = T(1) / r;
-          const T ux = v.x * inv, uy = v.y * inv, uz = v.z * inv;
+          // |r| < 0 marks a pair beyond r_cut in a list built with a skin: no contribution
+          const bool live = v.w >= T(0);
+          const T r = live ? v.w : T(1), inv = T(1) / r;
+          const T ux = live ? v.x * inv : T(0), uy = live ? v.y * inv : T(0), uz = live ? v.z * inv : T(1);
           T bn[NC], il[LC + 1];
           if constexpr (TABLE) {
             float f[NC + LC + 1];
@@ -70,7 +72,7 @@ pair_fwd_kernel(const FwdArgs<T> a) {
               il[l] = (l <= a.lmax) ? (T)(ild[l] * (a.p.eq08 ? (2.0 * l + 1.0) : 1.0)) * FOUR_PI : T(0);
           }
 #pragma unroll
-          for (int n = 0; n < NP; ++n) b_s[lane * NP + n] = (n < NC) ? bn[n] : T(0);
+          for (int n = 0; n < NP; ++n) b_s[lane * NP + n] = (n < NC && live) ? bn[n] : T(0);
           T* arow = a_s + lane * AS;
           for_each_ylm<T, LC>(ux, uy, uz, a.yc, [&](int l, int m, T y) { arow[lm_index(l, m)] = il[l] * y; });
         }
