@@ -12,8 +12,10 @@
  * the energy of each structure, the forces -dE/dx and the virial -dE/dstrain.
  *
  * Conventions
- *   - Lengths in Angstrom.  cell rows are the lattice vectors; positions must lie inside
- *     their cell (fractional coordinates in [0, 1)), otherwise SOAPGAP_E_INVALID_ARG.
+ *   - Lengths in Angstrom.  cell rows are the lattice vectors.  Positions may lie anywhere:
+ *     the neighbour search maps an atom whose fractional coordinates are outside
+ *     [-1e-9, 1 + 1e-9) into its cell (x - n h) first, and atoms already inside are used
+ *     exactly as given.  A non-finite position gives SOAPGAP_E_INVALID_ARG.
  *   - Neighbours: every atom j in every periodic image S with |x_j + S.h - x_i| < r_cut
  *     (strict), except (i, i, S = 0); atom i itself enters once as the central term.
  *   - Species map to separate density channels: channel = species(j) * n_max + n.
@@ -51,7 +53,7 @@ extern "C" {
 
 /* return codes */
 #define SOAPGAP_OK 0
-#define SOAPGAP_E_INVALID_ARG (-1) /* bad pointer, size, parameter, or atom outside cell */
+#define SOAPGAP_E_INVALID_ARG (-1) /* bad pointer, size, parameter, non-finite position */
 #define SOAPGAP_E_UNSUPPORTED (-2) /* n_max or l_max outside the supported range        */
 #define SOAPGAP_E_CAPACITY (-3)    /* a fixed-size buffer is too small (see message)    */
 #define SOAPGAP_E_CUDA (-4)        /* a CUDA runtime call or kernel failed              */
@@ -105,7 +107,7 @@ typedef struct soapgap_params {
  *                  atom_offs_host[n_struct] = n_atoms; atoms of structure s are
  *                  atom_offs_host[s] .. atom_offs_host[s+1]-1
  *   cell_host      [n_struct][3][3] host double, rows = lattice vectors, det != 0
- *   pos            [n_atoms][3] DEVICE double, Cartesian, inside the cell
+ *   pos            [n_atoms][3] DEVICE double, Cartesian (see the conventions above)
  *   species        [n_atoms] DEVICE int32 in [0, n_species)                          */
 typedef struct soapgap_batch {
     int32_t n_struct;
@@ -161,12 +163,12 @@ int soapgap_compute(soapgap_handle* h, const soapgap_batch* batch, uint32_t flag
  *     replay); the cell and atom_offs are taken at call (capture) time through the
  *     handle's pinned staging, so the handle must not be used for another batch shape
  *     between replays of a captured graph;
- *   - device-detected errors (atom outside its cell, coincident atoms, pair capacity) are
+ *   - device-detected errors (non-finite position, coincident atoms, pair capacity) are
  *     reported by soapgap_sync_status, not by the return value. */
 
 /* Wait for `stream` and report the device error word of the last asynchronous call:
  * SOAPGAP_OK, SOAPGAP_E_CAPACITY (pair buffers too small), SOAPGAP_E_INVALID_ARG (atom
- * outside its cell, coincident atoms) or SOAPGAP_E_CUDA; soapgap_last_error has the text. */
+ * non-finite position, coincident atoms) or SOAPGAP_E_CUDA; soapgap_last_error has the text. */
 int soapgap_sync_status(soapgap_handle* h, void* stream);
 
 /* Autotuner: runs one synchronous ENERGY|FORCES|VIRIAL evaluation of `batch` (device
@@ -195,13 +197,13 @@ int soapgap_last_rebuild(const soapgap_handle* h, int32_t* rebuilt);
 
 /* Velocity-Verlet half step for molecular dynamics around the evaluation (units: A, fs,
  * amu, eV; 1 eV/(A amu) = 0.009648533212 A/fs^2), enqueued on `stream` (capturable):
- *   v += (dt/2) F / m                           (drift = 0: the closing kick)
- *   v += (dt/2) F / m;  x += dt v;  wrap       (drift != 0: kick and drift)
- * where an atom whose fractional coordinates leave [0, 1) is mapped back into its cell.
+ *   v += (dt/2) F / m                  (drift = 0: the closing kick)
+ *   v += (dt/2) F / m;  x += dt v      (drift != 0: kick and drift)
+ * Positions are not wrapped (the neighbour search maps them into their cells itself, and
+ * unwrapped positions keep a Verlet-skin list valid when atoms cross a cell face).
  * pos [n_atoms][3], vel [n_atoms][3] DEVICE double, updated in place; forces [n_atoms][3]
  * DEVICE double (F = -dE/dx, as written by soapgap_compute); inv_mass [n_atoms] DEVICE
- * double (1/amu).  Needs a preceding soapgap_compute of the same batch shape (it uses that
- * call's cells).  One step: verlet(drift=1), compute(FORCES), verlet(drift=0). */
+ * double (1/amu).  One step: verlet(drift=1), compute(FORCES), verlet(drift=0). */
 int soapgap_verlet(soapgap_handle* h, const soapgap_batch* batch, double* pos, double* vel,
                    const double* forces, const double* inv_mass, double dt, int32_t drift,
                    void* stream);

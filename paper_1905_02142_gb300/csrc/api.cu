@@ -100,7 +100,8 @@ struct soapgap_handle {
   // Verlet skin: the list holds pairs within r_cut + skin and is reused while no atom has
   // moved by skin/2 since the positions pos_ref of its build
   double skin = 0.0;
-  Buf pos_ref, skin_flag;
+  Buf pos_ref, skin_flag, live_count, live_offs, live_idx;
+  Buf pos_w, img;           // positions mapped into their cells at the last build, and n_i
   bool ref_valid = false;
   int ref_atoms = -1, ref_struct = -1;
   std::vector<double> ref_cell;
@@ -450,7 +451,7 @@ __global__ void fill_ones(double* w, int n) {
 
 static std::string device_error_text(int code) {
   std::string m;
-  if (code & SG_ERR_OUTSIDE_CELL) m += "an atom lies outside its cell (fractional coordinate not in [0,1)); ";
+  if (code & SG_ERR_OUTSIDE_CELL) m += "a position is not finite; ";
   if (code & SG_ERR_COINCIDENT) m += "two atoms coincide (zero separation); ";
   if (code & SG_ERR_PAIR_CAPACITY) m += "pair buffer overflow; ";
   if (code & SG_ERR_NO_REVERSE) m += "pair list not symmetric; ";
@@ -475,7 +476,10 @@ static AdjArgs<T> adj_args(soapgap_handle* h, int N, const int* species) {
   auto it = h->adj_warps.find(adj_key(h, N, h->last_pairs));
   aa.warps = it == h->adj_warps.end() ? 0 : it->second;
   aa.species = species; aa.atom_struct = (const int*)h->atom_struct.p;
-  aa.struct_w = (const double*)h->struct_w.p; aa.seg_offs = (const int*)h->seg_offs.p;
+  aa.struct_w = (const double*)h->struct_w.p;
+  aa.list_offs = (const int*)h->seg_offs.p;
+  aa.seg_offs = h->skin > 0.0 ? (const int*)h->live_offs.p : (const int*)h->seg_offs.p;
+  aa.pair_idx = h->skin > 0.0 ? (const int*)h->live_idx.p : nullptr;
   aa.pair_r = (const Vec4<T>*)h->pair_r.p; aa.table = (const float*)h->table.p; aa.ti = h->ti;
   aa.p = h->dp;
   if constexpr (sizeof(T) == 4) { aa.yc = h->yc32; aa.bc = h->bc32; }
@@ -586,13 +590,18 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
       return fail(h, SOAPGAP_E_STATE, "no neighbour slots for an asynchronous call: make one synchronous call with the same batch first");
     ENS(h, h->slot_count, sizeof(int) * N1n);
     ENS(h, h->max_count, sizeof(int));
+    ENS(h, h->pos_w, sizeof(double) * 3 * N1n);
+    ENS(h, h->img, sizeof(int4) * N1n);
     nb.slot_count = (int*)h->slot_count.p;
     nb.max_count = (int*)h->max_count.p;
-    CK(h, sg_nbr_bin(b->pos, N, h->n_bins, nb, st));
+    // the list is built from the positions mapped into their cells (identical for atoms
+    // already inside)
+    CK(h, sg_nbr_wrap(b->pos, N, nb, (double*)h->pos_w.p, (int4*)h->img.p, st));
+    CK(h, sg_nbr_bin((const double*)h->pos_w.p, N, h->n_bins, nb, st));
     for (int attempt = 0; attempt < 2; ++attempt) {
       ENS(h, h->key_tmp, 8 * N1n * (size_t)maxn);
       nb.key_tmp = (unsigned long long*)h->key_tmp.p;
-      CK(h, sg_nbr_slots(b->pos, b->species, N, nsp, h->prm.r_cut + h->skin, maxn, nb, st));
+      CK(h, sg_nbr_slots((const double*)h->pos_w.p, b->species, N, nsp, h->prm.r_cut + h->skin, maxn, nb, st));
       if (h->async_call) break;
       CK(h, cudaMemcpyAsync(h->h_count, (int*)h->seg_offs.p + N * nsp, sizeof(int), cudaMemcpyDeviceToHost, st));
       CK(h, cudaMemcpyAsync(h->h_count + 1, h->max_count.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -629,6 +638,10 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
       if (!h->dedr.p) return fail(h, SOAPGAP_E_STATE, "no pair buffers for an asynchronous call: make one synchronous call with the same batch first");
       cap = std::min(cap, (long long)(h->dedr.cap / sizeof(Vec4<T>)));
     }
+    if (h->skin > 0.0) {
+      if (!h->live_idx.p) return fail(h, SOAPGAP_E_STATE, "no pair buffers for an asynchronous call: make one synchronous call with the same batch first");
+      cap = std::min(cap, (long long)(h->live_idx.cap / sizeof(int)));
+    }
     P = cap;
     CK(h, sg_nbr_cap_guard((int*)h->seg_offs.p, N * nsp, P, (int*)h->err.p, st, nb.run));
   }
@@ -652,19 +665,25 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
   if (!backward) {
     mark(h, EV_FILL0, st);
     if (rebuild || device_decides) {
-      cudaError_t e = sg_nbr_place<T>(b->pos, b->species, N, nsp, h->cur_maxn, nb, st);
+      cudaError_t e = sg_nbr_place<T>((const double*)h->pos_w.p, b->species, N, nsp, h->cur_maxn, nb, st);
       if (e == cudaErrorInvalidConfiguration)
         return fail(h, SOAPGAP_E_UNSUPPORTED, "too many neighbours per atom for the pair sort");
       CK(h, e);
     }
     if (h->skin > 0.0) {
+      // every call: current separations of the whole list and the list of live pairs
+      // (within r_cut), which the pair kernels and the force gather then use
+      ENS(h, h->live_count, sizeof(int) * N1n * nsp);
+      ENS(h, h->live_offs, sizeof(int) * (N1n * nsp + 1));
+      ENS(h, h->live_idx, sizeof(int) * Pc);
+      NbrBuffers nr = nb;  // positions as given, with the cell images of the last build
+      nr.img = (const int4*)h->img.p;
+      nr.run = nullptr;
+      CK(h, sg_nbr_refresh<T>(b->pos, N, nsp, nr, (int*)h->live_count.p, (int*)h->live_offs.p,
+                              (int*)h->live_idx.p, st));
       if (device_decides) {
-        // reuse steps refresh the separations; rebuild steps take the new reference
-        CK(h, sg_nbr_refresh<T>(b->pos, N, nsp, nb, (const int*)h->skin_flag.p, st));
         CK(h, sg_skin_ref_update(b->pos, (double*)h->pos_ref.p, N, (const int*)h->skin_flag.p, st));
-      } else if (!rebuild) {
-        CK(h, sg_nbr_refresh<T>(b->pos, N, nsp, nb, nullptr, st));
-      } else {
+      } else if (rebuild) {
         CK(h, cudaMemcpyAsync(h->pos_ref.p, b->pos, sizeof(double) * 3 * (size_t)N, cudaMemcpyDeviceToDevice, st));
         h->ref_valid = true;
         h->ref_atoms = N;
@@ -676,7 +695,9 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     h->stage_ran[0] = h->stage_ran[1] = h->stage_ran[2] = true;
     FwdArgs<T> fa{};
     fa.n_atoms = N; fa.nsp = nsp; fa.nmax = h->prm.n_max; fa.lmax = h->prm.l_max;
-    fa.species = b->species; fa.seg_offs = nb.seg_offs; fa.pair_r = (const Vec4<T>*)h->pair_r.p;
+    fa.species = b->species; fa.pair_r = (const Vec4<T>*)h->pair_r.p;
+    fa.seg_offs = h->skin > 0.0 ? (const int*)h->live_offs.p : nb.seg_offs;
+    fa.pair_idx = h->skin > 0.0 ? (const int*)h->live_idx.p : nullptr;
     fa.table = (const float*)h->table.p; fa.ti = h->ti; fa.p = h->dp;
     if constexpr (sizeof(T) == 4) { fa.yc = h->yc32; fa.bc = h->bc32; }
     else { fa.yc = h->yc64; fa.bc = h->bc64; }
@@ -747,7 +768,9 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     double* v_out = (backward || (flags & SOAPGAP_VIRIAL)) ? virial : nullptr;
     double* es_out = backward ? nullptr : e_struct;
     ENS(h, h->finish_part, sizeof(double) * 10 * (size_t)S * h->finish_chunks);
-    CK(h, sg_finish<T>(N, S, nsp, (const int64_t*)h->atom_offs.p, nb.seg_offs, (const int*)h->rev.p,
+    CK(h, sg_finish<T>(N, S, nsp, (const int64_t*)h->atom_offs.p,
+                       h->skin > 0.0 ? (const int*)h->live_offs.p : nb.seg_offs,
+                       h->skin > 0.0 ? (const int*)h->live_idx.p : nullptr, (const int*)h->rev.p,
                        (const Vec4<T>*)h->dedr.p, (const T*)h->eps_part.p, tiles,
                        v_out ? (const T*)h->vir_atom.p : nullptr, (T*)h->e_atom.p, es_out, f_out,
                        v_out, !backward, h->finish_chunks, (double*)h->finish_part.p, st));
@@ -954,7 +977,7 @@ extern "C" void soapgap_destroy(soapgap_handle* h) {
                  &h->binpos, &h->atom_hi, &h->atom_lo, &h->seg_count, &h->seg_offs, &h->scan_tmp, &h->key_tmp,
                  &h->key, &h->pair_j, &h->pair_r, &h->rev, &h->dedr, &h->c, &h->q, &h->pnorm,
                  &h->e_atom, &h->eps_part, &h->kp, &h->g, &h->vir_atom, &h->struct_w, &h->err,
-                 &h->finish_part, &h->slot_count, &h->max_count, &h->pos_ref, &h->skin_flag,
+                 &h->finish_part, &h->slot_count, &h->max_count, &h->pos_ref, &h->skin_flag, &h->live_count, &h->live_offs, &h->live_idx, &h->pos_w, &h->img,
                  &h->cen_tmp, &h->host_in_pos, &h->host_in_species, &h->host_q, &h->host_pnorm,
                  &h->host_e_atom, &h->host_e_struct, &h->host_forces, &h->host_virial};
   for (Buf* b : bufs)
@@ -1060,10 +1083,7 @@ extern "C" int soapgap_verlet(soapgap_handle* h, const soapgap_batch* batch, dou
   if (rc != SOAPGAP_OK) return rc;
   if (!pos || !vel || !forces || !inv_mass || !std::isfinite(dt))
     return fail(h, SOAPGAP_E_INVALID_ARG, "verlet needs pos, vel, forces, inv_mass and a finite dt");
-  if (h->fw_atoms != batch->n_atoms || h->fw_struct != batch->n_struct)
-    return fail(h, SOAPGAP_E_STATE, "verlet needs a preceding evaluation of the same batch");
-  CK(h, sg_verlet(batch->n_atoms, pos, vel, forces, inv_mass, dt, drift != 0,
-                  (const int*)h->atom_struct.p, (const StructGeom*)h->geom.p, (cudaStream_t)stream));
+  CK(h, sg_verlet(batch->n_atoms, pos, vel, forces, inv_mass, dt, drift != 0, (cudaStream_t)stream));
   h->msg.clear();
   return SOAPGAP_OK;
 }

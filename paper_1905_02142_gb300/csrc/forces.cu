@@ -37,6 +37,7 @@ template <> struct SumAcc<float> {
 
 template <typename T>
 __global__ void atom_finish_kernel(int n, int nsp, const int* __restrict__ seg_offs,
+                                   const int* __restrict__ pair_idx,
                                    const int* __restrict__ rev, const Vec4<T>* __restrict__ dedr,
                                    const T* __restrict__ eps_part, int n_tiles, T* e_atom,
                                    double* forces, double fsign) {
@@ -53,7 +54,8 @@ __global__ void atom_finish_kernel(int n, int nsp, const int* __restrict__ seg_o
   if (forces) {
     SumAcc<T> f0, f1, f2;
     const int beg = seg_offs[i * nsp], end = seg_offs[(i + 1) * nsp];
-    for (int p = beg + lane; p < end; p += 32) {
+    for (int k = beg + lane; k < end; k += 32) {
+      const int p = pair_idx ? pair_idx[k] : k;
       const Vec4<T> a = dedr[p], b = dedr[rev[p]];
       f0.add(a.x);
       f0.add(-b.x);
@@ -134,13 +136,13 @@ int sg_finish_chunks(int max_struct_atoms) {
 
 template <typename T>
 cudaError_t sg_finish(int n_atoms, int n_struct, int nsp, const int64_t* atom_offs_dev,
-                      const int* seg_offs, const int* rev, const Vec4<T>* dedr,
+                      const int* seg_offs, const int* pair_idx, const int* rev, const Vec4<T>* dedr,
                       const T* eps_part, int n_tiles, const T* vir_atom, T* e_atom,
                       double* e_struct, double* forces, double* virial, bool sign_force,
                       int chunks, double* part, cudaStream_t st) {
   if (n_atoms > 0 && ((eps_part && e_atom) || forces)) {
     atom_finish_kernel<T><<<(n_atoms * 32 + 255) / 256, 256, 0, st>>>(
-        n_atoms, nsp, seg_offs, rev, dedr, eps_part, n_tiles, e_atom, forces,
+        n_atoms, nsp, seg_offs, pair_idx, rev, dedr, eps_part, n_tiles, e_atom, forces,
         sign_force ? 1.0 : -1.0);
     ++sg_kernel_launches;
   }
@@ -153,10 +155,10 @@ cudaError_t sg_finish(int n_atoms, int n_struct, int nsp, const int64_t* atom_of
   return cudaGetLastError();
 }
 
-template cudaError_t sg_finish<float>(int, int, int, const int64_t*, const int*, const int*,
+template cudaError_t sg_finish<float>(int, int, int, const int64_t*, const int*, const int*, const int*,
                                       const Vec4<float>*, const float*, int, const float*, float*,
                                       double*, double*, double*, bool, int, double*, cudaStream_t);
-template cudaError_t sg_finish<double>(int, int, int, const int64_t*, const int*, const int*,
+template cudaError_t sg_finish<double>(int, int, int, const int64_t*, const int*, const int*, const int*,
                                        const Vec4<double>*, const double*, int, const double*,
                                        double*, double*, double*, double*, bool, int, double*, cudaStream_t);
 
@@ -165,51 +167,27 @@ template cudaError_t sg_finish<double>(int, int, int, const int64_t*, const int*
 // 1 eV/(A amu) = 0.009648533212 A/fs^2.
 #define SG_EV_PER_AMU_A2_FS2 0.009648533212
 
-// kick: v += (dt/2) F/m;  with drift: then x += dt v, and an atom whose fractional
-// coordinates left [0, 1) is mapped back into its cell (x = f h with f mod 1)
+// kick: v += (dt/2) F/m;  with drift: then x += dt v.  Positions are not wrapped: the
+// neighbour-list build maps them into their cells itself, and unwrapped positions keep a
+// Verlet-skin list valid when atoms cross a cell face.
 __global__ void verlet_kernel(int n, double* __restrict__ pos, double* __restrict__ vel,
                               const double* __restrict__ forces, const double* __restrict__ inv_mass,
-                              double dt, int drift, const int* __restrict__ atom_struct,
-                              const StructGeom* __restrict__ geom) {
+                              double dt, int drift) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double kick = 0.5 * dt * SG_EV_PER_AMU_A2_FS2 * inv_mass[i];
-  double v[3], x[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) v[c] = vel[3 * i + c] + kick * forces[3 * i + c];
-  if (drift) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) x[c] = pos[3 * i + c] + dt * v[c];
-    const StructGeom& g = geom[atom_struct[i]];
-    double f[3];
-    bool out = false;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      f[k] = x[0] * g.hinv[k] + x[1] * g.hinv[3 + k] + x[2] * g.hinv[6 + k];
-      out |= !(f[k] >= 0.0 && f[k] < 1.0);
-    }
-    if (out) {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        f[k] -= floor(f[k]);
-        if (f[k] >= 1.0) f[k] = 0.0;
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) x[c] = f[0] * g.h[c] + f[1] * g.h[3 + c] + f[2] * g.h[6 + c];
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) pos[3 * i + c] = x[c];
+  for (int c = 0; c < 3; ++c) {
+    const double v = vel[3 * i + c] + kick * forces[3 * i + c];
+    vel[3 * i + c] = v;
+    if (drift) pos[3 * i + c] += dt * v;
   }
-#pragma unroll
-  for (int c = 0; c < 3; ++c) vel[3 * i + c] = v[c];
 }
 
 cudaError_t sg_verlet(int n, double* pos, double* vel, const double* forces, const double* inv_mass,
-                      double dt, bool drift, const int* atom_struct, const StructGeom* geom,
-                      cudaStream_t st) {
+                      double dt, bool drift, cudaStream_t st) {
   if (n > 0) {
-    verlet_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, pos, vel, forces, inv_mass, dt, drift ? 1 : 0,
-                                                    atom_struct, geom);
+    verlet_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, pos, vel, forces, inv_mass, dt, drift ? 1 : 0);
     ++sg_kernel_launches;
   }
   return cudaGetLastError();

@@ -72,6 +72,9 @@ struct NbrBuffers {
   int* rev;                  // [cap]
   int* scan_tmp;             // scan scratch
   int* err;                  // device error word
+  const int4* img;           // if set: cell image n_i of each atom at the last build (the list
+                             // was built from x - n_i h); separations then use the positions
+                             // as given with the shift S - n_j + n_i
   const int* run;            // if set and *run == 0, the list-building kernels return at once
                              // (neighbour-list reuse decided on the device)
   double rc2_mask;           // > 0: pairs with |r|^2 >= rc2_mask get |r| = -1 (beyond r_cut
@@ -80,6 +83,10 @@ struct NbrBuffers {
 size_t sg_scan_tmp_ints(int n);
 cudaError_t sg_exclusive_scan(const int* in, int* out, int n, int* tmp, cudaStream_t st,
                               const int* run = nullptr);
+// positions mapped into their cells for the list build: pos_w = x - n h with n = floor of the
+// fractional coordinates (n = 0, pos_w = x exactly, for atoms inside up to 1e-9), img = n
+cudaError_t sg_nbr_wrap(const double* pos, int n_atoms, const NbrBuffers& b, double* pos_w,
+                        int4* img, cudaStream_t st);
 cudaError_t sg_nbr_bin(const double* pos, int n_atoms, int n_bins, const NbrBuffers& b,
                        cudaStream_t st);
 // one sweep over the candidates: per-atom slot arrays of keys (capacity maxn), counts per
@@ -92,12 +99,13 @@ cudaError_t sg_nbr_cap_guard(int* seg_offs, int nseg, long long cap, int* err, c
                              const int* run = nullptr);
 // Verlet skin: rebuild[0] |= 1 if an atom moved by skin/2 or more since the positions `ref`
 // of the last build; refresh recomputes every pair's separation from its key and the current
-// positions (masked beyond r_cut), unless *rebuilt; ref_update copies pos to ref if *rebuild
+// positions (|r| < 0 beyond r_cut) and lists the live pairs of each segment (live_offs
+// [N*nsp + 1], live_idx: indices into the full list); ref_update copies pos to ref if *rebuild
 cudaError_t sg_skin_check(const double* pos, const double* ref, int n, double half_skin,
                           int* rebuild, cudaStream_t st);
 template <typename T>
 cudaError_t sg_nbr_refresh(const double* pos, int n_atoms, int nsp, const NbrBuffers& b,
-                           const int* rebuilt, cudaStream_t st);
+                           int* live_count, int* live_offs, int* live_idx, cudaStream_t st);
 cudaError_t sg_skin_ref_update(const double* pos, double* ref, int n, const int* rebuild,
                                cudaStream_t st);
 // keys ranked into their segments with j and the separation vectors, then the reverse index
@@ -109,7 +117,8 @@ cudaError_t sg_nbr_place(const double* pos, const int* species, int n_atoms, int
 template <typename T> struct FwdArgs {
   int n_atoms, nsp, nmax, lmax;
   const int* species;
-  const int* seg_offs;
+  const int* seg_offs;      // segment offsets of the pairs to use
+  const int* pair_idx;      // if set: index into pair_r of each of those pairs (live pairs)
   const Vec4<T>* pair_r;
   const float* table;     // table path
   TableInfo ti;
@@ -167,7 +176,9 @@ template <typename T> struct AdjArgs {
   const int* species;
   const int* atom_struct;
   const double* struct_w;   // [S] dE/dE_struct
-  const int* seg_offs;
+  const int* seg_offs;      // segment offsets of the pairs to use
+  const int* pair_idx;      // if set: index into pair_r / dedr of each of those pairs
+  const int* list_offs;     // segment offsets of the full list (prefetch ranges)
   const Vec4<T>* pair_r;
   const float* table;
   TableInfo ti;
@@ -191,13 +202,12 @@ int sg_adj_batches_per_atom(long long n_pairs, int n_atoms, int nsp);
 // ---------------------------------------------------------------- forces.cu
 // chunks per structure of the two-level per-structure sums (part: [S][chunks][10] doubles)
 int sg_finish_chunks(int max_struct_atoms);
-// velocity-Verlet half step (kick; with drift also the position update and cell wrap)
+// velocity-Verlet half step (kick; with drift also the position update)
 cudaError_t sg_verlet(int n, double* pos, double* vel, const double* forces, const double* inv_mass,
-                      double dt, bool drift, const int* atom_struct, const StructGeom* geom,
-                      cudaStream_t st);
+                      double dt, bool drift, cudaStream_t st);
 template <typename T>
 cudaError_t sg_finish(int n_atoms, int n_struct, int nsp, const int64_t* atom_offs_dev,
-                      const int* seg_offs, const int* rev, const Vec4<T>* dedr,
+                      const int* seg_offs, const int* pair_idx, const int* rev, const Vec4<T>* dedr,
                       const T* eps_part, int n_tiles, const T* vir_atom, T* e_atom,
                       double* e_struct, double* forces, double* virial, bool sign_force,
                       int chunks, double* part, cudaStream_t st);

@@ -117,16 +117,13 @@ __global__ void bin_assign(const double* __restrict__ pos, int n, NbrBuffers b) 
   const StructGeom& g = b.geom[b.atom_struct[i]];
   double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
   int bi[3];
-  bool bad = false;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     double f = x * g.hinv[k] + y * g.hinv[3 + k] + z * g.hinv[6 + k];
-    if (!(f >= -1e-9 && f < 1.0 + 1e-9)) bad = true;
-    int c = (int)floor(f * g.nb[k]);
-    c = c < 0 ? 0 : (c >= g.nb[k] ? g.nb[k] - 1 : c);
+    f = f * g.nb[k];
+    int c = (f >= 0.0) ? (f < (double)g.nb[k] ? (int)f : g.nb[k] - 1) : 0;
     bi[k] = c;
   }
-  if (bad) atomicOr(b.err, SG_ERR_OUTSIDE_CELL);
   int id = g.bin_off + (bi[0] * g.nb[1] + bi[1]) * g.nb[2] + bi[2];
   b.atom_bin[i] = id;
   b.atom_bin4[i] = make_int4(bi[0], bi[1], bi[2], id);
@@ -145,6 +142,49 @@ __global__ void bin_fill(const double* __restrict__ pos, int n, NbrBuffers b, fl
   binpos[at] = make_float4(xh, yh, zh, __int_as_float(i));
   b.atom_hi[i] = make_float4(xh, yh, zh, 0.f);
   b.atom_lo[i] = lo;
+}
+
+__global__ void wrap_kernel(const double* __restrict__ pos, int n, NbrBuffers b, double* pos_w,
+                            int4* img) {
+  if (b.run && *b.run == 0) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const StructGeom& g = b.geom[b.atom_struct[i]];
+  const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+  double nk[3];
+  bool moved = false, finite = true;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double f = x * g.hinv[k] + y * g.hinv[3 + k] + z * g.hinv[6 + k];
+    finite &= isfinite(f);
+    nk[k] = (f >= -1e-9 && f < 1.0 + 1e-9) ? 0.0 : floor(f);
+    moved |= nk[k] != 0.0;
+  }
+  if (!finite) {
+    atomicOr(b.err, SG_ERR_OUTSIDE_CELL);
+    nk[0] = nk[1] = nk[2] = 0.0;
+    moved = false;
+  }
+  double w[3] = {x, y, z};
+  if (moved) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      w[c] = __dsub_rn(w[c], __dadd_rn(__dadd_rn(__dmul_rn(nk[0], g.h[c]), __dmul_rn(nk[1], g.h[3 + c])),
+                                        __dmul_rn(nk[2], g.h[6 + c])));
+  }
+  pos_w[3 * i] = w[0];
+  pos_w[3 * i + 1] = w[1];
+  pos_w[3 * i + 2] = w[2];
+  img[i] = make_int4((int)nk[0], (int)nk[1], (int)nk[2], 0);
+}
+
+cudaError_t sg_nbr_wrap(const double* pos, int n_atoms, const NbrBuffers& b, double* pos_w,
+                        int4* img, cudaStream_t st) {
+  if (n_atoms > 0) {
+    wrap_kernel<<<(n_atoms + 255) / 256, 256, 0, st>>>(pos, n_atoms, b, pos_w, img);
+    ++sg_kernel_launches;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t sg_nbr_bin(const double* pos, int n_atoms, int n_bins, const NbrBuffers& b,
@@ -387,6 +427,13 @@ __device__ __forceinline__ Vec4<T> pair_vector(const double* __restrict__ pos, c
                                                int i, int j, int S1, int S2, int S3) {
   const StructGeom& g = b.geom[b.atom_struct[i]];
   const bool canon = (j > i) || (j == i && lex_positive(S1, S2, S3));
+  if (b.img) {
+    // list built from x - n h: with the positions as given the same pair has shift S - n_j + n_i
+    const int4 ni = b.img[i], nj = b.img[j];
+    S1 += ni.x - nj.x;
+    S2 += ni.y - nj.y;
+    S3 += ni.z - nj.z;
+  }
   Vec4<T> v;
   if constexpr (sizeof(T) == 4) {
     const int pa = canon ? j : i, pb = canon ? i : j;
@@ -584,24 +631,6 @@ cudaError_t sg_skin_check(const double* pos, const double* ref, int n, double ha
   return cudaGetLastError();
 }
 
-// every pair of the (reused) list: separation from its key and the current positions
-template <typename T>
-__global__ void refresh_kernel(int n, int nsp, const double* __restrict__ pos, NbrBuffers b,
-                               const int* rebuilt, Vec4<T>* rout) {
-  if (rebuilt && *rebuilt) return;
-  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (i >= n) return;
-  const int beg = b.seg_offs[i * nsp], end = b.seg_offs[(i + 1) * nsp];
-  for (int p = beg + lane; p < end; p += 32) {
-    const unsigned long long k = b.key[p];
-    const int j = (int)(k >> 24);
-    const int s1 = (int)((k >> 16) & 255) - 128, s2 = (int)((k >> 8) & 255) - 128,
-              s3 = (int)(k & 255) - 128;
-    rout[p] = pair_vector<T>(pos, b, i, j, s1, s2, s3);
-  }
-}
-
 // FP32 high / low words of the current positions (the double-float separations read them)
 __global__ void split_positions_kernel(const double* __restrict__ pos, int n, NbrBuffers b) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -612,24 +641,77 @@ __global__ void split_positions_kernel(const double* __restrict__ pos, int n, Nb
   b.atom_lo[i] = make_float4((float)(x - (double)xh), (float)(y - (double)yh), (float)(z - (double)zh), 0.f);
 }
 
+// Lists built with a skin, at every call: each pair's separation from its key and the
+// current positions (|r| < 0 beyond r_cut), and the number of live pairs of each
+// (centre, species) segment.  One warp per segment.
+template <typename T>
+__global__ void refresh_kernel(int nseg, int nsp, const double* __restrict__ pos, NbrBuffers b,
+                               int* live_count, Vec4<T>* rout) {
+  const int seg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (seg >= nseg) return;
+  const int i = seg / nsp;
+  const int beg = b.seg_offs[seg], end = b.seg_offs[seg + 1];
+  int live = 0;
+  for (int base = beg; base < end; base += 32) {
+    const int p = base + lane;
+    bool ok = false;
+    if (p < end) {
+      const unsigned long long k = b.key[p];
+      const int j = (int)(k >> 24);
+      const int s1 = (int)((k >> 16) & 255) - 128, s2 = (int)((k >> 8) & 255) - 128,
+                s3 = (int)(k & 255) - 128;
+      const Vec4<T> v = pair_vector<T>(pos, b, i, j, s1, s2, s3);
+      rout[p] = v;
+      ok = v.w >= T(0);
+    }
+    live += __popc(__ballot_sync(0xffffffffu, ok));
+  }
+  if (lane == 0) live_count[seg] = live;
+}
+
+// live pairs of each segment, in list (key) order: indices into the full list
+template <typename T>
+__global__ void live_fill_kernel(int nseg, NbrBuffers b, const int* __restrict__ live_offs,
+                                 int* live_idx) {
+  const int seg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (seg >= nseg) return;
+  const int beg = b.seg_offs[seg], end = b.seg_offs[seg + 1];
+  const Vec4<T>* pr = reinterpret_cast<const Vec4<T>*>(b.pair_r);
+  int at = live_offs[seg];
+  for (int base = beg; base < end; base += 32) {
+    const int p = base + lane;
+    const bool ok = p < end && pr[p].w >= T(0);
+    const unsigned mask = __ballot_sync(0xffffffffu, ok);
+    if (ok) live_idx[at + __popc(mask & ((1u << lane) - 1u))] = p;
+    at += __popc(mask);
+  }
+}
+
 template <typename T>
 cudaError_t sg_nbr_refresh(const double* pos, int n_atoms, int nsp, const NbrBuffers& b,
-                           const int* rebuilt, cudaStream_t st) {
+                           int* live_count, int* live_offs, int* live_idx, cudaStream_t st) {
   if (n_atoms == 0) return cudaSuccess;
   if constexpr (sizeof(T) == 4) {
     split_positions_kernel<<<(n_atoms + 255) / 256, 256, 0, st>>>(pos, n_atoms, b);
     ++sg_kernel_launches;
   }
+  const int nseg = n_atoms * nsp;
   const int threads = 128;
-  const long long blocks = ((long long)n_atoms * 32 + threads - 1) / threads;
-  refresh_kernel<T><<<(unsigned)blocks, threads, 0, st>>>(n_atoms, nsp, pos, b, rebuilt,
+  const long long blocks = ((long long)nseg * 32 + threads - 1) / threads;
+  refresh_kernel<T><<<(unsigned)blocks, threads, 0, st>>>(nseg, nsp, pos, b, live_count,
                                                           reinterpret_cast<Vec4<T>*>(b.pair_r));
+  ++sg_kernel_launches;
+  cudaError_t e = sg_exclusive_scan(live_count, live_offs, nseg, b.scan_tmp, st);
+  if (e != cudaSuccess) return e;
+  live_fill_kernel<T><<<(unsigned)blocks, threads, 0, st>>>(nseg, b, live_offs, live_idx);
   ++sg_kernel_launches;
   return cudaGetLastError();
 }
-template cudaError_t sg_nbr_refresh<float>(const double*, int, int, const NbrBuffers&, const int*,
+template cudaError_t sg_nbr_refresh<float>(const double*, int, int, const NbrBuffers&, int*, int*, int*,
                                            cudaStream_t);
-template cudaError_t sg_nbr_refresh<double>(const double*, int, int, const NbrBuffers&, const int*,
+template cudaError_t sg_nbr_refresh<double>(const double*, int, int, const NbrBuffers&, int*, int*, int*,
                                             cudaStream_t);
 
 __global__ void skin_ref_kernel(const double* __restrict__ pos, double* ref, int n3, const int* rebuild) {

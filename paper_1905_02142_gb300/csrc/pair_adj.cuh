@@ -135,7 +135,8 @@ pair_adj_kernel(const AdjArgs<T> a, int smem_per_warp) {
         T bn[NC], dbn[NC];
         T ux = 0, uy = 0, uz = 1, r = 1, inv = 1;
         Vec4<T> v{};
-        if (valid) v = a.pair_r[pidx];
+        const int pp = (valid && a.pair_idx) ? a.pair_idx[pidx] : pidx;  // index in the full list
+        if (valid) v = a.pair_r[pp];
         // |r| < 0 marks a pair beyond r_cut in a list built with a skin: dE/dr = 0
         const bool live = valid && v.w >= T(0);
         if (live) {
@@ -238,7 +239,7 @@ pair_adj_kernel(const AdjArgs<T> a, int smem_per_warp) {
             }
           }
         }
-        if (valid && !live) a.dedr[pidx] = Vec4<T>{T(0), T(0), T(0), T(0)};
+        if (valid && !live) a.dedr[pp] = Vec4<T>{T(0), T(0), T(0), T(0)};
         if (live) {
           const T hdot = hx * ux + hy * uy + hz * uz;
           Vec4<T> o;
@@ -246,7 +247,7 @@ pair_adj_kernel(const AdjArgs<T> a, int smem_per_warp) {
           o.y = uy * srad + (hy - hdot * uy) * inv;
           o.z = uz * srad + (hz - hdot * uz) * inv;
           o.w = T(0);
-          a.dedr[pidx] = o;
+          a.dedr[pp] = o;
           const T gvec[3] = {o.x, o.y, o.z}, rvec[3] = {v.x, v.y, v.z};
 #pragma unroll
           for (int p = 0; p < 3; ++p)

@@ -436,7 +436,7 @@ pair_adj_mma_kernel(const AdjArgs<float> a, const MmaLayout lay) {
       const int nxt = atom + gridDim.x;
       if (nxt < a.n_atoms) {
         const int lc = (nch * L * 4 + 127) >> 7, lq = (D * 4 + 127) >> 7;
-        const int pb = a.seg_offs[nxt * a.nsp], pe = a.seg_offs[(nxt + 1) * a.nsp];
+        const int pb = a.list_offs[nxt * a.nsp], pe = a.list_offs[(nxt + 1) * a.nsp];
         const char* pr = reinterpret_cast<const char*>(a.pair_r + pb);
         const int lp = pe > pb ? (int)(((pe - pb) * sizeof(Vec4<float>) + 127) >> 7) : 0;
         for (int k = tid; k < lc + 2 * lq + lp; k += NT) {
@@ -465,7 +465,8 @@ pair_adj_mma_kernel(const AdjArgs<float> a, const MmaLayout lay) {
         const bool valid = pidx < end;
         float ux = 0.f, uy = 0.f, uz = 1.f, r = 1.f, inv_r = 1.f;
         Vec4<float> v{};
-        if (valid) v = a.pair_r[pidx];
+        const int pp = (valid && a.pair_idx) ? a.pair_idx[pidx] : pidx;  // index in the full list
+        if (valid) v = a.pair_r[pp];
         // |r| < 0 marks a pair beyond r_cut in a list built with a skin: dE/dr = 0
         const bool live = valid && v.w >= 0.f;
         if (live) {
@@ -619,7 +620,7 @@ pair_adj_mma_kernel(const AdjArgs<float> a, const MmaLayout lay) {
           }
         }
         }  // rolled sweep
-        if (valid && !live) a.dedr[pidx] = Vec4<float>{0.f, 0.f, 0.f, 0.f};
+        if (valid && !live) a.dedr[pp] = Vec4<float>{0.f, 0.f, 0.f, 0.f};
         if (live) {
           const float inv_s = ldexpf(1.f, eg + eb - 28);
           srad *= inv_s;
@@ -632,7 +633,7 @@ pair_adj_mma_kernel(const AdjArgs<float> a, const MmaLayout lay) {
           o.y = uy * srad + (hy - hdot * uy) * inv_r;
           o.z = uz * srad + (hz - hdot * uz) * inv_r;
           o.w = 0.f;
-          a.dedr[pidx] = o;
+          a.dedr[pp] = o;
           const float gv[3] = {o.x, o.y, o.z}, rv[3] = {v.x, v.y, v.z};
 #pragma unroll
           for (int p = 0; p < 3; ++p)

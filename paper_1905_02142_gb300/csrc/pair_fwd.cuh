@@ -46,7 +46,7 @@ pair_fwd_kernel(const FwdArgs<T> a) {
       for (int base = beg; base < end; base += 32) {
         const int pidx = base + lane;
         if (pidx < end) {
-          const Vec4<T> v = a.pair_r[pidx];
+          const Vec4<T> v = a.pair_r[a.pair_idx ? a.pair_idx[pidx] : pidx];
           // |r| < 0 marks a pair beyond r_cut in a list built with a skin: no contribution
           const bool live = v.w >= T(0);
           const T r = live ? v.w : T(1), inv = T(1) / r;

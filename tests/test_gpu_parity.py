@@ -286,11 +286,19 @@ def test_invalid_inputs_are_reported():
     from paper_1905_02142_gb300.api import SoapGapError
     P, qs, al, zeta = sparse_model("box64_n6l6")
     model = model_for(params_dict(P), "mixed", qs, al, zeta)
-    outside = synth.Structure(pos=np.array([[1.0, 1.0, 1.0], [9.5, 1.0, 1.0]]), cell=np.eye(3) * 8.0,
-                              species=np.zeros(2, np.int32))
+    # an atom displaced by lattice vectors is the same structure (mapped into its cell)
+    inside = synth.random_box(20, side=8.0, dmin=1.2, seed=12)
+    shifted = synth.Structure(pos=inside.pos + np.array([[8.0, -16.0, 0.0]] * 3 + [[0.0, 0.0, 0.0]] * 17),
+                              cell=inside.cell, species=inside.species)
+    a = model.compute(structures(synth.concat([inside])), energy=True, forces=True)
+    b = model.compute(structures(synth.concat([shifted])), energy=True, forces=True)
+    assert torch.allclose(a["e_struct"], b["e_struct"], rtol=1e-6, atol=0)
+    assert torch.allclose(a["forces"], b["forces"], rtol=0, atol=1e-6 * float(a["forces"].abs().max()))
+    bad = synth.Structure(pos=np.array([[1.0, 1.0, 1.0], [np.nan, 1.0, 1.0]]), cell=np.eye(3) * 8.0,
+                          species=np.zeros(2, np.int32))
     with pytest.raises(SoapGapError) as e:
-        model.compute(structures(synth.concat([outside])), desc=True)
-    assert "outside" in str(e.value)
+        model.compute(structures(synth.concat([bad])), desc=True)
+    assert "not finite" in str(e.value)
     same = synth.Structure(pos=np.array([[1.0, 1.0, 1.0], [1.0, 1.0, 1.0]]), cell=np.eye(3) * 8.0,
                            species=np.zeros(2, np.int32))
     with pytest.raises(SoapGapError) as e:
