@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--timing-grid", action="store_true",
                     help="descriptors-only throughput over (n_max, l_max) on the paper's timing box")
+    ap.add_argument("--no-md", action="store_true", help="skip the molecular-dynamics leg")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-structures workload (graph replay)")
     return ap.parse_args()
@@ -280,6 +281,39 @@ def timed_graph(model, s, flush, stream, warmup, steps):
             "how": "one CUDA graph per step: neighbour list to forces and virial, no host synchronisation"}
 
 
+def run_md(model, s, stream, steps, skin=0.4, dt=0.5, temperature=300.0):
+    """Velocity-Verlet dynamics of the workload box from a captured graph per step, with a
+    Verlet skin: one step = kick + drift, evaluation (energies, forces), closing kick."""
+    import torch
+
+    from paper_1905_02142_gb300.api import AMU_A2_PER_FS2_IN_EV, Structures, VelocityVerlet
+    mass = 12.011
+    rng = np.random.default_rng(7)
+    kT = 8.617333e-5 * temperature
+    vel = rng.normal(size=(s.n_atoms, 3)) * np.sqrt(kT / (mass * AMU_A2_PER_FS2_IN_EV))
+    vel -= vel.mean(axis=0)
+    s2 = Structures(s.pos.clone(), s.cell, s.species, s.atom_offs, device=s.pos.device)
+    model.set_skin(skin)
+    md = VelocityVerlet(model, s2, mass, dt=dt, vel=vel, capture=True)
+    md.step(5)
+    torch.cuda.synchronize()
+    e_start = md.potential_energy() + md.kinetic_energy()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    md.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    model.sync_status()
+    ms = e0.elapsed_time(e1) / steps
+    e_end = md.potential_energy() + md.kinetic_energy()
+    model.set_skin(0.0)
+    return {"ms_per_step": ms, "value": s.n_atoms / (ms / 1e3), "unit": "atom-steps/s",
+            "steps": steps, "dt_fs": dt, "skin_A": skin, "temperature_K": temperature,
+            "energy_change_eV_per_atom": (e_end - e_start) / s.n_atoms,
+            "how": "velocity Verlet, one CUDA graph per step, neighbour list reused within the skin"}
+
+
 def run_batched(args, dev, flush, stream):
     """The batched workload (many periodic structures of uneven size, one launch per kernel)
     evaluated from a captured CUDA graph after autotuning; energies, forces and virial."""
@@ -450,6 +484,7 @@ def run_ours(args, rank, world, local_rank):
                 "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
                 "peak_source": FP32_PEAK_NOTE + f" ({sm_mhz:.0f} MHz)",
                 "flops_per_launch": flops}
+    md = run_md(model, s, stream, max(args.steps, 20)) if not args.no_md else None
     batched = None
     if world == 1 and not args.no_batched:
         batched = run_batched(args, dev, flush, stream)
@@ -472,6 +507,7 @@ def run_ours(args, rank, world, local_rank):
         "stages_ms": {k: round(v, 4) for k, v in stages.items()},
         "stages_roofline": stage_rooflines(stages, n_pairs, n, w, sm_mhz),
         "graph": graph,
+        "md": md,
         "batched": batched,
         "fp64_path": fp64,
         "roofline": roofline,
