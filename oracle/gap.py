@@ -10,6 +10,14 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
               position and lattice vector; for pair separations this equals
               -sum_pairs (dE/dr_ij)_a (r_ij)_b.
 
+Fitting side (Sec. IV.A: the alpha_s are fitted to the energies of N_t environments and
+their 3 N_t force components, with the environments of the sparse set as basis):
+  kernel_matrix       k(i, s) for descriptor rows against the sparse set (K_NM; with the
+                      sparse rows themselves, K_MM)
+  structure_rows      sum of k(i, s) over each structure's atoms (energy rows)
+  kernel_gradients    dk[k, a, s] = d/dx_{k,a} of that sum for the structure of atom k
+                      (force rows: a model with weights alpha has F_k = -dk[k] @ alpha)
+
 The paper gives no derivative formulas (it states its implementation lacks kernel
 derivatives), so forces and virial here are the exact derivatives of the energy,
 taken by PyTorch autograd through the same FP64 operations that compute it.
@@ -40,6 +48,56 @@ def local_energies(q: torch.Tensor, q_sparse: torch.Tensor, alpha: torch.Tensor,
                    zeta: float) -> torch.Tensor:
     """eps_i = sum_s alpha_s (q_i . q_s)^zeta for packed descriptors q [N, D], q_sparse [M, D]."""
     return kernel_power(q @ q_sparse.T, zeta) @ alpha
+
+
+def kernel_matrix(q, q_sparse, zeta: float) -> torch.Tensor:
+    """k(i, s) = (q_i . q_s)^zeta for rows q [N, D] against q_sparse [M, D]: [N, M]."""
+    return kernel_power(torch.as_tensor(q, dtype=DT) @ torch.as_tensor(q_sparse, dtype=DT).T, zeta)
+
+
+def structure_rows(k_atom, atom_offs) -> torch.Tensor:
+    """Per-structure sums of kernel rows: out[t, s] = sum over atoms i of t of k_atom[i, s]."""
+    k_atom = torch.as_tensor(k_atom, dtype=DT)
+    offs = np.asarray(atom_offs)
+    return torch.stack([k_atom[offs[t]:offs[t + 1]].sum(dim=0) for t in range(len(offs) - 1)])
+
+
+def kernel_gradients(batch, P: Params, q_sparse, zeta: float, atoms=None, sparse=None, W=None,
+                     chunk: int = 64) -> np.ndarray:
+    """dk[k, a, s] = d/dx_{k,a} sum_{i in the structure of k} (q_i . q_s)^zeta for the listed
+    atoms k (default: all, in index order) and sparse environments s (default: all).
+
+    Only centres i that can depend on x_k contribute: k itself and every atom with k among
+    its neighbours (any image); their descriptors are taken with autograd through the same
+    FP64 operations as the energy, one backward pass per sparse environment.
+    Returns [len(atoms), 3, len(sparse)] (NumPy FP64).
+    """
+    if W is None:
+        W = basis.orthonormaliser(P.n_max, P.r_cut, P.sigma_r0)
+    qs_all = torch.as_tensor(np.asarray(q_sparse), dtype=DT)
+    sparse = np.arange(len(qs_all)) if sparse is None else np.asarray(sparse, dtype=np.int64)
+    qs = qs_all[torch.as_tensor(sparse)]
+    if atoms is None:
+        atoms = np.arange(batch.n_atoms)
+        centers = atoms
+    else:
+        atoms = np.asarray(atoms, dtype=np.int64)
+        near = neighbours.batch_pairs(batch, P.r_cut, centers=np.unique(atoms))
+        centers = np.unique(np.concatenate([atoms, near["j"]]))
+    pairs = neighbours.batch_pairs(batch, P.r_cut, centers=centers)
+    pos = torch.as_tensor(batch.pos, dtype=DT).clone().requires_grad_(True)
+    cell = torch.as_tensor(batch.cell, dtype=DT)
+    grad = torch.zeros((len(sparse), batch.n_atoms, 3), dtype=DT)
+    for c0 in range(0, len(centers), chunk):
+        cc = centers[c0:c0 + chunk]
+        sel = (pairs["i"] >= cc[0]) & (pairs["i"] <= cc[-1])
+        sub = {k: v[sel] for k, v in pairs.items()}
+        q = _local_descriptor(P, W, pos, cell, batch.species, cc, sub)
+        k = kernel_matrix(q, qs, zeta)                       # [chunk, Ms]
+        for t in range(len(sparse)):
+            g, = torch.autograd.grad(k[:, t].sum(), pos, retain_graph=t + 1 < len(sparse))
+            grad[t] += g
+    return grad[:, torch.as_tensor(atoms), :].permute(1, 2, 0).numpy()
 
 
 def sparse_set(batch, P: Params, indices, W=None) -> np.ndarray:

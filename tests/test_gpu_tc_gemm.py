@@ -19,8 +19,8 @@ def model():
     return SoapGap(r_cut=4.0, n_max=4, l_max=2, precision="mixed")
 
 
-@pytest.mark.parametrize("m,n,k", [(128, 128, 64), (300, 200, 128), (129, 257, 192),
-                                   (1000, 640, 1920), (64, 130, 4096)])
+@pytest.mark.parametrize("m,n,k", [(128, 128, 64), (300, 200, 128), (129, 257, 192), (300, 256, 128),
+                                   (1000, 640, 1920), (64, 130, 4096), (20000, 1024, 192)])
 def test_tc_gemm_matches_fp32_product(model, m, n, k):
     g = torch.Generator(device="cuda").manual_seed(m * 7 + n * 3 + k)
     a = torch.randn(m, k, device="cuda", generator=g).half()
