@@ -72,6 +72,15 @@ extern "C" {
 #define SOAPGAP_ASYNC 32u  /* no allocation and no host synchronisation: capturable in a
                               CUDA graph (see soapgap_compute)                         */
 
+/* soapgap_design flags (rows of the sparse-GAP fitting matrices) */
+#define SOAPGAP_DESIGN_K 64u       /* kernel rows k_atom                        */
+#define SOAPGAP_DESIGN_KSTRUCT 128u /* per-structure energy rows k_struct       */
+#define SOAPGAP_DESIGN_DK 256u     /* force rows dk                             */
+
+/* Stages reported by soapgap_design_times, in this order. */
+#define SOAPGAP_N_DESIGN_STAGES 4  /* descriptors (neighbours to q), kernel_rows (with the
+                                      per-structure sums), jacobian, force_rows */
+
 /* Stages reported by soapgap_stage_times, in this order. */
 #define SOAPGAP_N_STAGES 7 /* neighbours, pair_forward, power_spectrum, gap_forward,
                               gap_backward, pair_adjoint, finish */
@@ -215,6 +224,39 @@ int soapgap_verlet(soapgap_handle* h, const soapgap_batch* batch, double* pos, d
  * Returns SOAPGAP_E_STATE without a preceding ENERGY evaluation. */
 int soapgap_backward(soapgap_handle* h, const soapgap_batch* batch, const double* dE_dEstruct,
                      double* grad_pos, double* virial, void* stream);
+
+/* Rows of the sparse-GAP fitting matrices for a batch of training structures (Sec. IV.A:
+ * the weights alpha_s are fitted to the energies and forces of N_t training environments,
+ * with the sparse set as basis; kernel of Sec. I), against the sparse set of the last
+ * soapgap_set_model (its alpha and the model's energies are not used):
+ *   k_atom[i][s]    = k(i, s) = (q_i . q_s)^zeta                      (SOAPGAP_DESIGN_K)
+ *   k_struct[t][s]  = sum over the atoms i of structure t of k(i, s) (SOAPGAP_DESIGN_KSTRUCT)
+ *   dk[k][a][s]     = d/dx_{k,a} of sum over i in the structure of atom k of k(i, s)
+ *                                                                     (SOAPGAP_DESIGN_DK)
+ * so that a model with weights alpha has E_t = k_struct[t] . alpha and the force
+ * F_{k,a} = -dk[k][a] . alpha.  Layouts: k_atom [n_atoms][M], dk [n_atoms][3][M] DEVICE,
+ * float for MIXED, double for FP64; k_struct [n_struct][M] DEVICE double.  Outputs not
+ * requested may be NULL.  flags may add SOAPGAP_TIMING (soapgap_design_times).
+ * Precision (MIXED): kernel rows from the same split tensor-core products as the energy
+ * (relative error ~1e-7); force rows from single FP16 products of the centred sparse rows
+ * with power-of-two scaled FP16 descriptor Jacobians (RMS relative error ~1e-4).
+ * Workspace: the Jacobian columns, 3 (P + n_atoms) of them for P neighbour pairs, each of
+ * D padded to 64 halves (MIXED) or D doubles (FP64), plus 24 (MIXED) or 40 (FP64) bytes
+ * each, and n_atoms x M weights.  Synchronises `stream`; SOAPGAP_E_STATE without a model,
+ * SOAPGAP_E_UNSUPPORTED if the descriptor is too large for the Jacobian kernel's shared
+ * memory or the column count exceeds 2^31. */
+int soapgap_design(soapgap_handle* h, const soapgap_batch* batch, uint32_t flags, void* k_atom,
+                   double* k_struct, void* dk, void* stream);
+
+/* Device time in milliseconds of each stage of the last soapgap_design call made with
+ * SOAPGAP_TIMING: ms[SOAPGAP_N_DESIGN_STAGES] host double (0 for stages that did not run). */
+int soapgap_design_times(const soapgap_handle* h, double* ms);
+
+/* Kernel rows of any descriptors against the sparse set of the last soapgap_set_model:
+ * k[i][s] = (q_i . q_s)^zeta.  q [n][D] DEVICE (float for MIXED, double for FP64; rows as
+ * written by soapgap_compute with SOAPGAP_DESC), k [n][M] DEVICE of the same type.  With
+ * the sparse rows themselves this is the K_MM block of the fit.  Synchronises `stream`. */
+int soapgap_kernel_rows(soapgap_handle* h, const void* q, int32_t n, void* k, void* stream);
 
 /* Same as soapgap_compute, but pos/species and every output are HOST pointers; the
  * library copies inputs to its workspace and results back on `stream` and returns

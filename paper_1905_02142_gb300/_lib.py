@@ -23,6 +23,11 @@ FORCES = 4
 VIRIAL = 8
 TIMING = 16
 ASYNC = 32
+DESIGN_K = 64
+DESIGN_KSTRUCT = 128
+DESIGN_DK = 256
+N_DESIGN_STAGES = 4
+DESIGN_STAGES = ("descriptors", "kernel_rows", "jacobian", "force_rows")
 N_STAGES = 7
 STAGES = ("neighbours", "pair_forward", "power_spectrum", "gap_forward", "gap_backward",
           "pair_adjoint", "finish")
@@ -72,6 +77,10 @@ SIGNATURES = {
     "soapgap_last_rebuild": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_int32)]),
     "soapgap_verlet": (ctypes.c_int, [c_void_p, ctypes.POINTER(Batch), c_void_p, c_void_p, c_void_p,
                                       c_void_p, c_double, c_int32, c_void_p]),
+    "soapgap_design": (ctypes.c_int, [c_void_p, ctypes.POINTER(Batch), c_uint32, c_void_p, c_void_p,
+                                      c_void_p, c_void_p]),
+    "soapgap_design_times": (ctypes.c_int, [c_void_p, c_void_p]),
+    "soapgap_kernel_rows": (ctypes.c_int, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "soapgap_last_error": (ctypes.c_char_p, [c_void_p]),
     "soapgap_destroy": (None, [c_void_p]),
 }

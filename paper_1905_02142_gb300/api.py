@@ -146,6 +146,50 @@ class SoapGap:
             _ptr(out.get("virial")), st))
         return out
 
+    def design(self, s: Structures, *, k_atom=False, k_struct=False, dk=False, timing=False,
+               stream=None):
+        """Rows of the sparse-GAP fitting matrices for the structures ``s`` against the
+        sparse set of set_model (see soapgap_design): dict with k_atom [N, M],
+        k_struct [S, M] and dk [N, 3, M] CUDA tensors as requested; a model with weights
+        alpha has E = k_struct @ alpha and forces -dk @ alpha."""
+        if self.m == 0:
+            raise SoapGapError(L.E_STATE, "no sparse set: call set_model first")
+        dev = s.pos.device
+        n, ns, m = s.n_atoms, s.n_struct, self.m
+        flags = (L.DESIGN_K if k_atom else 0) | (L.DESIGN_KSTRUCT if k_struct else 0) | \
+            (L.DESIGN_DK if dk else 0) | (L.TIMING if timing else 0)
+        out = {}
+        if k_atom:
+            out["k_atom"] = torch.empty((n, m), dtype=self.dtype, device=dev)
+        if k_struct:
+            out["k_struct"] = torch.empty((ns, m), dtype=torch.float64, device=dev)
+        if dk:
+            out["dk"] = torch.empty((n, 3, m), dtype=self.dtype, device=dev)
+        st = (stream or torch.cuda.current_stream(dev)).cuda_stream
+        b = s.c_batch()
+        self._check(self.lib.soapgap_design(self.h, ctypes.byref(b), flags, _ptr(out.get("k_atom")),
+                                            _ptr(out.get("k_struct")), _ptr(out.get("dk")), st))
+        return out
+
+    def design_times(self) -> dict:
+        """Device milliseconds per stage of the last design(timing=True) call."""
+        ms = np.zeros(L.N_DESIGN_STAGES)
+        self._check(self.lib.soapgap_design_times(self.h, ms.ctypes.data))
+        return dict(zip(L.DESIGN_STAGES, ms.tolist()))
+
+    def kernel_rows(self, q: torch.Tensor, stream=None) -> torch.Tensor:
+        """k[i, s] = (q_i . q_s)^zeta of descriptor rows q [n, D] (CUDA, the handle's dtype)
+        against the sparse set; with the sparse rows themselves, the K_MM block."""
+        if self.m == 0:
+            raise SoapGapError(L.E_STATE, "no sparse set: call set_model first")
+        q = q.to(self.dtype).contiguous()
+        if q.ndim != 2 or q.shape[1] != self.dim:
+            raise ValueError(f"q must be [n, {self.dim}]")
+        k = torch.empty((q.shape[0], self.m), dtype=self.dtype, device=q.device)
+        st = (stream or torch.cuda.current_stream(q.device)).cuda_stream
+        self._check(self.lib.soapgap_kernel_rows(self.h, _ptr(q), q.shape[0], _ptr(k), st))
+        return k
+
     def set_skin(self, skin: float):
         """Verlet skin in A (0 disables neighbour-list reuse); see soapgap_set_skin."""
         self._check(self.lib.soapgap_set_skin(self.h, float(skin)))

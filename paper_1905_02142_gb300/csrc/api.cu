@@ -8,6 +8,7 @@
 #include <limits>
 #include <map>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/soapgap.h"
@@ -134,6 +135,12 @@ struct soapgap_handle {
   bool ev_made = false, timed = false;
   bool stage_ran[SOAPGAP_N_STAGES] = {};
   long long launches = 0;
+  // fitting-matrix rows (soapgap_design): kernel rows when not returned, force-row weights,
+  // Jacobian columns and their (owner, target) and (qbar.J, q.J, 1/scale) records
+  Buf dk_k, dk_wv, dk_J, dk_at, dk_v;
+  cudaEvent_t dev_ev[SOAPGAP_N_DESIGN_STAGES + 1] = {};
+  bool dev_made = false, dev_timed = false;
+  bool dstage_ran[SOAPGAP_N_DESIGN_STAGES] = {};
 };
 
 // event slots: 0/1 neighbour search before the size read-back, 2/3 the fill after it,
@@ -979,7 +986,8 @@ extern "C" void soapgap_destroy(soapgap_handle* h) {
                  &h->e_atom, &h->eps_part, &h->kp, &h->g, &h->vir_atom, &h->struct_w, &h->err,
                  &h->finish_part, &h->slot_count, &h->max_count, &h->pos_ref, &h->skin_flag, &h->live_count, &h->live_offs, &h->live_idx, &h->pos_w, &h->img,
                  &h->cen_tmp, &h->host_in_pos, &h->host_in_species, &h->host_q, &h->host_pnorm,
-                 &h->host_e_atom, &h->host_e_struct, &h->host_forces, &h->host_virial};
+                 &h->host_e_atom, &h->host_e_struct, &h->host_forces, &h->host_virial,
+                 &h->dk_k, &h->dk_wv, &h->dk_J, &h->dk_at, &h->dk_v};
   for (Buf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (h->h_err) cudaFreeHost(h->h_err);
@@ -989,6 +997,8 @@ extern "C" void soapgap_destroy(soapgap_handle* h) {
   if (h->h_err_async) cudaFreeHost(h->h_err_async);
   if (h->ev_made)
     for (int k = 0; k < 10; ++k) cudaEventDestroy(h->ev[k]);
+  if (h->dev_made)
+    for (int k = 0; k <= SOAPGAP_N_DESIGN_STAGES; ++k) cudaEventDestroy(h->dev_ev[k]);
   delete h;
 }
 
@@ -1084,6 +1094,181 @@ extern "C" int soapgap_verlet(soapgap_handle* h, const soapgap_batch* batch, dou
   if (!pos || !vel || !forces || !inv_mass || !std::isfinite(dt))
     return fail(h, SOAPGAP_E_INVALID_ARG, "verlet needs pos, vel, forces, inv_mass and a finite dt");
   CK(h, sg_verlet(batch->n_atoms, pos, vel, forces, inv_mass, dt, drift != 0, (cudaStream_t)stream));
+  h->msg.clear();
+  return SOAPGAP_OK;
+}
+
+// ---------------------------------------------------------------- fitting-matrix rows
+static void dmark(soapgap_handle* h, int slot, cudaStream_t st) {
+  if (h->dev_timed) cudaEventRecord(h->dev_ev[slot], st);
+}
+
+template <typename T>
+static int design(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* k_atom, double* k_struct,
+                  void* dk, cudaStream_t st) {
+  using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+  const size_t es = sizeof(T);
+  dmark(h, 0, st);
+  int rc = run<T>(h, b, SOAPGAP_DESC, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                  false, st);
+  if (rc != SOAPGAP_OK) return rc;
+  h->dstage_ran[0] = true;
+  const int N = b->n_atoms, S = b->n_struct, M = h->M, D = h->D;
+  const bool want_k = (flags & SOAPGAP_DESIGN_K) != 0, want_ks = (flags & SOAPGAP_DESIGN_KSTRUCT) != 0;
+  const bool want_dk = (flags & SOAPGAP_DESIGN_DK) != 0;
+  dmark(h, 1, st);
+  if (want_ks) CK(h, cudaMemsetAsync(k_struct, 0, sizeof(double) * (size_t)S * M, st));
+  if (want_dk && N > 0) CK(h, cudaMemsetAsync(dk, 0, es * (size_t)N * 3 * M, st));
+  const size_t N1 = (size_t)std::max(N, 1);
+  const int ldw = h->mixed ? h->tcm.mp : M;
+  T* kbuf = (T*)k_atom;
+  if (!want_k) {
+    ENS(h, h->dk_k, es * N1 * M);
+    kbuf = (T*)h->dk_k.p;
+  }
+  T2* wv = nullptr;
+  if (want_dk) {
+    ENS(h, h->dk_wv, sizeof(T2) * N1 * ldw);
+    wv = (T2*)h->dk_wv.p;
+  }
+  if (N > 0 && (want_k || want_ks || want_dk)) {
+    h->dstage_ran[1] = true;
+    if constexpr (sizeof(T) == 4) {
+      const GapTcModel& tm = h->tcm;
+      ENS(h, h->A16, sizeof(__half) * N1 * 3 * tm.dp);
+      ENS(h, h->nrm, sizeof(float) * N1);
+      ENS(h, h->uq, sizeof(float) * N1);
+      CK(h, sg_gap_tc_prepare((const float*)h->q.p, N, D, tm.dp, tm.qbar, (__half*)h->A16.p, (float*)h->nrm.p,
+                              (float*)h->uq.p, st));
+      CK(h, sg_tc_kernel_rows(tm, (const __half*)h->A16.p, (const float*)h->nrm.p, (const float*)h->uq.p, N, M,
+                              (const float*)h->pnorm.p, kbuf, wv, (int*)h->err.p, st));
+    } else {
+      CK(h, sg_kernel_rows_f64((const double*)h->q.p, N, (const double*)h->qs.p, M, D, h->zeta,
+                               (const double*)h->pnorm.p, kbuf, wv, ldw, st));
+    }
+    if (want_ks) CK(h, sg_struct_rows<T>(kbuf, N, M, (const int*)h->atom_struct.p, k_struct, st));
+  }
+  dmark(h, 2, st);
+  if (want_dk && N > 0) {
+    h->dstage_ran[2] = h->dstage_ran[3] = true;
+    const long long P = h->last_pairs;
+    const long long ncols = 3 * (P + N);
+    if (ncols > 0x7fffffffLL - 256)
+      return fail(h, SOAPGAP_E_UNSUPPORTED, "too many Jacobian columns (3 (pairs + atoms) >= 2^31): split the batch");
+    const int ld = h->mixed ? h->tcm.dp : D;
+    ENS(h, h->dk_J, (size_t)ncols * ld * (h->mixed ? sizeof(__half) : sizeof(double)));
+    ENS(h, h->dk_at, sizeof(int2) * (size_t)ncols);
+    ENS(h, h->dk_v, sizeof(Vec4<T>) * (size_t)ncols);
+    JacArgs<T> ja{};
+    ja.n_atoms = N;
+    ja.nsp = h->prm.n_species;
+    ja.nmax = h->prm.n_max;
+    ja.lmax = h->prm.l_max;
+    ja.dim = D;
+    ja.ld = ld;
+    ja.seg_offs = (const int*)h->seg_offs.p;
+    ja.rev = (const int*)h->rev.p;
+    ja.pair_j = (const int*)h->pair_j.p;
+    ja.pair_r = (const Vec4<T>*)h->pair_r.p;
+    ja.table = (const float*)h->table.p;
+    ja.ti = h->ti;
+    ja.p = h->dp;
+    if constexpr (sizeof(T) == 4) {
+      ja.yc = h->yc32;
+      ja.bc = h->bc32;
+      ja.qbar = h->tcm.qbar;
+    } else {
+      ja.yc = h->yc64;
+      ja.bc = h->bc64;
+      ja.qbar = nullptr;
+    }
+    ja.c = (const T*)h->c.p;
+    ja.q = (const T*)h->q.p;
+    ja.J = h->dk_J.p;
+    ja.col_at = (int2*)h->dk_at.p;
+    ja.col_v = (Vec4<T>*)h->dk_v.p;
+    cudaError_t e = sg_design_jacobian<T>(ja, h->cls, h->mixed, st);
+    if (e == cudaErrorInvalidConfiguration)
+      return fail(h, SOAPGAP_E_UNSUPPORTED, "descriptor too large for the Jacobian kernel's shared memory");
+    CK(h, e);
+    dmark(h, 3, st);
+    if constexpr (sizeof(T) == 4)
+      CK(h, sg_tc_design_grad(h->tcm, M, (const __half*)h->dk_J.p, ncols, (const int2*)h->dk_at.p,
+                              (const float4*)h->dk_v.p, wv, (float*)dk, (int*)h->err.p, st));
+    else
+      CK(h, sg_design_grad_f64((const double*)h->qs.p, M, D, (const double*)h->dk_J.p, ncols,
+                               (const int2*)h->dk_at.p, (const Vec4<double>*)h->dk_v.p, wv, ldw, (double*)dk, st));
+  } else {
+    dmark(h, 3, st);
+  }
+  dmark(h, 4, st);
+  CK(h, cudaMemcpyAsync(h->h_err, h->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  if (*h->h_err) return fail(h, SOAPGAP_E_INVALID_ARG, device_error_text(*h->h_err));
+  h->msg.clear();
+  return SOAPGAP_OK;
+}
+
+extern "C" int soapgap_design(soapgap_handle* h, const soapgap_batch* batch, uint32_t flags, void* k_atom,
+                              double* k_struct, void* dk, void* stream) {
+  if (!h) return SOAPGAP_E_INVALID_ARG;
+  int rc = check_batch(h, batch);
+  if (rc != SOAPGAP_OK) return rc;
+  if (flags & ~(SOAPGAP_DESIGN_K | SOAPGAP_DESIGN_KSTRUCT | SOAPGAP_DESIGN_DK | SOAPGAP_TIMING))
+    return fail(h, SOAPGAP_E_INVALID_ARG, "unknown flag bits for soapgap_design");
+  if (!h->has_model) return fail(h, SOAPGAP_E_STATE, "no sparse set: call soapgap_set_model first");
+  if ((flags & SOAPGAP_DESIGN_K) && !k_atom) return fail(h, SOAPGAP_E_INVALID_ARG, "DESIGN_K needs k_atom");
+  if ((flags & SOAPGAP_DESIGN_KSTRUCT) && !k_struct)
+    return fail(h, SOAPGAP_E_INVALID_ARG, "DESIGN_KSTRUCT needs k_struct");
+  if ((flags & SOAPGAP_DESIGN_DK) && !dk) return fail(h, SOAPGAP_E_INVALID_ARG, "DESIGN_DK needs dk");
+  h->async_call = false;
+  h->timed = false;
+  h->dev_timed = (flags & SOAPGAP_TIMING) != 0;
+  for (int k = 0; k < SOAPGAP_N_DESIGN_STAGES; ++k) h->dstage_ran[k] = false;
+  if (h->dev_timed && !h->dev_made) {
+    for (int k = 0; k <= SOAPGAP_N_DESIGN_STAGES; ++k) CK(h, cudaEventCreate(&h->dev_ev[k]));
+    h->dev_made = true;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->mixed) return design<float>(h, batch, flags, k_atom, k_struct, dk, st);
+  return design<double>(h, batch, flags, k_atom, k_struct, dk, st);
+}
+
+extern "C" int soapgap_design_times(const soapgap_handle* h, double* ms) {
+  if (!h || !ms) return SOAPGAP_E_INVALID_ARG;
+  if (!h->dev_timed || !h->dev_made) return SOAPGAP_E_STATE;
+  for (int k = 0; k < SOAPGAP_N_DESIGN_STAGES; ++k) {
+    float t = 0.f;
+    ms[k] = 0.0;
+    if (h->dstage_ran[k] && cudaEventElapsedTime(&t, h->dev_ev[k], h->dev_ev[k + 1]) == cudaSuccess) ms[k] = t;
+  }
+  return SOAPGAP_OK;
+}
+
+extern "C" int soapgap_kernel_rows(soapgap_handle* h, const void* q, int32_t n, void* k, void* stream) {
+  if (!h) return SOAPGAP_E_INVALID_ARG;
+  if (!h->has_model) return fail(h, SOAPGAP_E_STATE, "no sparse set: call soapgap_set_model first");
+  if (n < 0 || (n > 0 && (!q || !k))) return fail(h, SOAPGAP_E_INVALID_ARG, "kernel_rows needs q, k and n >= 0");
+  if (n == 0) return SOAPGAP_OK;
+  h->async_call = false;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(h, cudaMemsetAsync(h->err.p, 0, sizeof(int), st));
+  if (h->mixed) {
+    const GapTcModel& tm = h->tcm;
+    CK(h, ensure(h->A16, sizeof(__half) * (size_t)n * 3 * tm.dp));
+    CK(h, ensure(h->nrm, sizeof(float) * (size_t)n));
+    CK(h, ensure(h->uq, sizeof(float) * (size_t)n));
+    CK(h, sg_gap_tc_prepare((const float*)q, n, h->D, tm.dp, tm.qbar, (__half*)h->A16.p, (float*)h->nrm.p,
+                            (float*)h->uq.p, st));
+    CK(h, sg_tc_kernel_rows(tm, (const __half*)h->A16.p, (const float*)h->nrm.p, (const float*)h->uq.p, n, h->M,
+                            nullptr, (float*)k, nullptr, (int*)h->err.p, st));
+  } else {
+    CK(h, sg_kernel_rows_f64((const double*)q, n, (const double*)h->qs.p, h->M, h->D, h->zeta, nullptr,
+                             (double*)k, nullptr, 0, st));
+  }
+  CK(h, cudaMemcpyAsync(h->h_err, h->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  if (*h->h_err) return fail(h, SOAPGAP_E_CUDA, device_error_text(*h->h_err));
   h->msg.clear();
   return SOAPGAP_OK;
 }

@@ -205,6 +205,102 @@ struct EpiGapBwd {
   __device__ void end(int, int) {}
 };
 
+// Kernel rows of the fitting matrices (atoms x sparse set): k(i, s) = S^zeta, and for the
+// force rows the weights (w, w S), w = zeta S^(zeta-1) / |p_i|; S as in EpiGapFwd.
+struct EpiKernelRows {
+  int rows, m, ldw, izeta;
+  float zeta;
+  const float *u, *nrm, *pnorm;      // [N]
+  const float4* col;                 // [Mp] as in EpiGapFwd
+  float* k;                          // [N][m]
+  float2* wv;                        // [N][ldw] or null
+  float ui, ni, ip;
+  __device__ void begin(int row) {
+    ui = row < rows ? u[row] : 0.f;
+    ni = row < rows ? nrm[row] : 0.f;
+    ip = (row < rows && wv) ? 1.f / pnorm[row] : 0.f;
+  }
+  __device__ void apply(int row, int col0, const uint32_t* v) {
+    if (row >= rows) return;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int s = col0 + j;
+      const float4 c = __ldg(col + s);
+      const float S = fmaf(ni * c.y, __uint_as_float(v[j]), ui + c.x);
+      float sz1;
+      switch (izeta) {
+        case 1: sz1 = 1.f; break;
+        case 2: sz1 = S; break;
+        case 3: sz1 = S * S; break;
+        case 4: sz1 = S * S * S; break;
+        default: sz1 = powf(fmaxf(S, 0.f), zeta - 1.f); break;
+      }
+      if (s < m) k[(size_t)row * m + s] = izeta > 0 ? sz1 * S : powf(fmaxf(S, 0.f), zeta);
+      if (wv) {
+        const float w = zeta * sz1 * ip;
+        wv[(size_t)row * ldw + s] = make_float2(w, w * S);
+      }
+    }
+  }
+  __device__ void end(int, int) {}
+};
+
+// Force rows of the fitting matrices: rows = sparse environments s, columns = descriptor
+// Jacobian columns ordered by target atom (see design.cu).  Per column (owner o, target t,
+// component a = col mod 3) the contribution is
+//   w_os (qbar.J + n_s 2^-e u_s.J) - (w S)_os q_o.J,
+// u_s.J from the tensor cores on the column scaled by 2^e; the running sums of one target
+// are added to dk[t][a][s] when the target changes (a target's columns are contiguous).
+struct EpiDesignGrad {
+  int m, ldw, ncols;
+  const float4* scol;                // [Mp] .y = n_s
+  const int2* col_at;                // [ncols] (owner, target)
+  const float4* col_v;               // [ncols] (qbar.J, q_owner.J, 2^-e, 0)
+  const float2* wv;                  // [N][ldw]
+  float* dk;                         // [N][3][m]
+  float ns;
+  int owner, target;
+  float2 w;
+  float acc[3];
+  __device__ void flush(int row) {
+    if (target >= 0) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (acc[a] != 0.f) atomicAdd(dk + ((size_t)target * 3 + a) * m + row, acc[a]);
+    }
+    acc[0] = acc[1] = acc[2] = 0.f;
+  }
+  __device__ void begin(int row) {
+    ns = row < m ? scol[row].y : 0.f;
+    owner = target = -1;
+    w = make_float2(0.f, 0.f);
+    acc[0] = acc[1] = acc[2] = 0.f;
+  }
+  __device__ void apply(int row, int col0, const uint32_t* v) {
+    if (row >= m) return;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int col = col0 + j;
+      if (col >= ncols) continue;
+      const int2 at = __ldg(col_at + col);
+      if (at.x != owner) {
+        owner = at.x;
+        w = __ldg(wv + (size_t)owner * ldw + row);
+      }
+      if (at.y != target) {
+        flush(row);
+        target = at.y;
+      }
+      const float4 cv = __ldg(col_v + col);
+      const float val = fmaf(w.x, fmaf(ns * cv.z, __uint_as_float(v[j]), cv.x), -w.y * cv.y);
+      acc[col % 3] += val;
+    }
+  }
+  __device__ void end(int row, int) {
+    if (row < m) flush(row);
+  }
+};
+
 // ------------------------------------------------------------------ the GEMM
 // Persistent, warp-specialised: one CTA per SM walks the output tiles (row-major over
 // [M/BM] x [N/BN], so CTAs running together share A rows in L2).
@@ -213,7 +309,9 @@ struct EpiGapBwd {
 //   warps 2..      : epilogue, EPI_WARPS warps; warp w reads TMEM lanes 32*(w%4) .. +31 and
 //                    a 1/(EPI_WARPS/4) share of the columns; it releases the buffer when done
 // so the epilogue of one tile overlaps the MMAs of the next.
-template <int BN, int STAGES, int EPI_WARPS, class Epi>
+// MFAST walks the tiles column-major instead ([N/BN] x [M/BM], m fastest): for a B far
+// larger than A, CTAs running together then share B tiles and B is read from memory once.
+template <int BN, int STAGES, int EPI_WARPS, class Epi, bool MFAST = false>
 __global__ void __launch_bounds__(32 * (2 + EPI_WARPS), 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                int num_kb, int m_tiles, int n_tiles, Epi epi, int* err) {
@@ -262,7 +360,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       int issued[STAGES];
       for (int s = 0; s < STAGES; ++s) issued[s] = 0;
       for (int t = blockIdx.x; t < total && !abort_flag; t += gridDim.x) {
-        const int m0 = (t / n_tiles) * BM, n0 = (t % n_tiles) * BN;
+        const int m0 = (MFAST ? t % m_tiles : t / n_tiles) * BM, n0 = (MFAST ? t / m_tiles : t % n_tiles) * BN;
         for (int kb = 0; kb < num_kb; ++kb, ++it) {
           const int s = it % STAGES, round = it / STAGES;
           if (round > 0 && !mbar_wait(&empty_bar[s], (round - 1) & 1)) {
@@ -330,7 +428,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         break;
       }
       fence_after();
-      const int m0 = (t / n_tiles) * BM, n0 = (t % n_tiles) * BN;
+      const int m0 = (MFAST ? t % m_tiles : t / n_tiles) * BM, n0 = (MFAST ? t / m_tiles : t % n_tiles) * BN;
       const int row = m0 + lg * 32 + lane;
       epi.begin(row);
 #pragma unroll 1
@@ -340,7 +438,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + col), v);
         epi.apply(row, n0 + col, v);
       }
-      epi.end(row, (t % n_tiles) * HALVES + half);
+      epi.end(row, (MFAST ? t / m_tiles : t % n_tiles) * HALVES + half);
       fence_before();
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty_bar[b])) : "memory");
@@ -371,12 +469,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2D FP16 row-major matrix [rows][cols] (cols a multiple of 64), tiles of box_rows x 64.
-bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int box_rows) {
+// 2D FP16 row-major matrix [rows][cols] (cols a multiple of 64) with row stride ld elements
+// (ld = cols when 0), tiles of box_rows x 64.
+bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int box_rows, int ld = 0) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld > 0 ? ld : cols) * 2};
   cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
@@ -384,20 +483,22 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int box_rows
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, int STAGES, int EPI_WARPS, class Epi>
+// C = A B^T over K = k; lda: row stride of A in elements (k when 0)
+template <int BN, int STAGES, int EPI_WARPS, bool MFAST = false, class Epi>
 cudaError_t launch_gemm(const void* A, int a_rows, const void* B, int b_rows, int k, Epi epi, int* err,
-                        cudaStream_t st) {
+                        cudaStream_t st, int lda = 0) {
   if (k % BK != 0 || a_rows <= 0 || b_rows <= 0) return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
-  if (!make_map(&ma, A, a_rows, k, BM) || !make_map(&mb, B, b_rows, k, BN)) return cudaErrorInvalidValue;
-  auto kern = tc_gemm_kernel<BN, STAGES, EPI_WARPS, Epi>;
+  if (!make_map(&ma, A, a_rows, k, BM, lda) || !make_map(&mb, B, b_rows, k, BN)) return cudaErrorInvalidValue;
+  auto kern = tc_gemm_kernel<BN, STAGES, EPI_WARPS, Epi, MFAST>;
   constexpr size_t smem = smem_bytes<BN, STAGES>();
-  cudaError_t e = sg_set_smem<tc_gemm_kernel<BN, STAGES, EPI_WARPS, Epi>>(smem);
+  cudaError_t e = sg_set_smem<tc_gemm_kernel<BN, STAGES, EPI_WARPS, Epi, MFAST>>(smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int m_tiles = (a_rows + BM - 1) / BM, n_tiles = (b_rows + BN - 1) / BN;
+  if ((long long)m_tiles * n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
   const int grid = std::min(sms, m_tiles * n_tiles);
   kern<<<grid, 32 * (2 + EPI_WARPS), smem, st>>>(ma, mb, k / BK, m_tiles, n_tiles, epi, err);
   ++sg_kernel_launches;
@@ -486,4 +587,39 @@ cudaError_t sg_tc_gemm_store(const __half* A, int m, const __half* B, int nn, in
                              cudaStream_t st) {
   EpiStore e{m, nn, C};
   return launch_gemm<128, 6, 4>(A, m, B, nn, k, e, err, st);
+}
+
+cudaError_t sg_tc_kernel_rows(const GapTcModel& md, const __half* A, const float* nrm, const float* uq, int n,
+                              int m, const float* pnorm, float* k, float2* wv, int* err, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  EpiKernelRows e{};
+  e.rows = n;
+  e.m = m;
+  e.ldw = md.mp;
+  e.izeta = md.izeta;
+  e.zeta = md.zeta;
+  e.u = uq;
+  e.nrm = nrm;
+  e.pnorm = pnorm;
+  e.col = md.col;
+  e.k = k;
+  e.wv = wv;
+  return launch_gemm<256, 4, 8>(A, n, md.B, md.mp, 3 * md.dp, e, err, st);
+}
+
+cudaError_t sg_tc_design_grad(const GapTcModel& md, int m, const __half* J, long long ncols, const int2* col_at,
+                              const float4* col_v, const float2* wv, float* dk, int* err, cudaStream_t st) {
+  if (ncols == 0) return cudaSuccess;
+  if (ncols > 0x7fffffffLL - 256) return cudaErrorInvalidValue;
+  EpiDesignGrad e{};
+  e.m = m;
+  e.ldw = md.mp;
+  e.ncols = (int)ncols;
+  e.scol = md.col;
+  e.col_at = col_at;
+  e.col_v = col_v;
+  e.wv = wv;
+  e.dk = dk;
+  // A = the unit centred sparse rows (the hi third of each row of B), K = dp
+  return launch_gemm<256, 4, 8, true>(md.B, md.mp, J, (int)ncols, md.dp, e, err, st, 3 * md.dp);
 }

@@ -199,6 +199,49 @@ cudaError_t sg_pair_adjoint_mma(const AdjArgs<float>& a, int cls, cudaStream_t s
 // 32-pair batches of a typical atom (sum over its neighbour-species segments)
 int sg_adj_batches_per_atom(long long n_pairs, int n_atoms, int nsp);
 
+// ---------------------------------------------------------------- design.cu
+// Columns of the force rows of the fitting matrices: J_ij = dp_i/dr_ij (3 per pair, stored
+// at the slot of the reverse pair in the target's range) and -sum_j J_ij (3 self columns per
+// atom, after the target's pairs): column range of atom k = [3 (o_k + k), 3 (o_(k+1) + k + 1)).
+template <typename T> struct JacArgs {
+  int n_atoms, nsp, nmax, lmax, dim;
+  int ld;                   // row length of a stored column (D padded to 64 for FP16, D for FP64)
+  const int* seg_offs;      // [N*nsp + 1] the full list
+  const int* rev;           // [P]
+  const int* pair_j;        // [P]
+  const Vec4<T>* pair_r;    // [P] (|r| < 0: masked pair, zero columns)
+  const float* table;       // table path
+  TableInfo ti;
+  DevParams p;              // recursion path
+  YlmCoef<T> yc;
+  BasisConst<T> bc;
+  const T* c;               // [N][nch][L]
+  const T* q;               // [N][D]
+  const float* qbar;        // [D] sparse-set mean (table path: centring of the products)
+  void* J;                  // [ncols][ld]: __half scaled by a power of two per column, or double
+  int2* col_at;             // [ncols] (owner atom, target atom)
+  Vec4<T>* col_v;           // [ncols] (qbar . J, q_owner . J, 1/scale, 0)
+};
+template <typename T> cudaError_t sg_design_jacobian(const JacArgs<T>& a, int cls, bool table,
+                                                     cudaStream_t st);
+// FP64 path: k[i][s] = (q_i.q_s)^zeta and, if wv, wv[i][s] = (w, w S) with
+// w = zeta S^(zeta-1) / |p_i| (row stride ldw)
+cudaError_t sg_kernel_rows_f64(const double* q, int n, const double* qs, int m, int d, double zeta,
+                               const double* pnorm, double* k, double2* wv, int ldw, cudaStream_t st);
+// FP64 path: dk[target][a][s] += w_os (q_s . J_col) - (w S)_os (q_o . J_col) for every column
+cudaError_t sg_design_grad_f64(const double* qs, int m, int d, const double* J, long long ncols,
+                               const int2* col_at, const Vec4<double>* col_v, const double2* wv, int ldw,
+                               double* dk, cudaStream_t st);
+// out[t][s] += sum over the atoms i of structure t of k[i][s]  (out zeroed by the caller)
+template <typename T>
+cudaError_t sg_struct_rows(const T* k, int n, int m, const int* atom_struct, double* out, cudaStream_t st);
+// mixed path (gap_tc.cu): kernel rows from the prepared FP16 split operands, and the force
+// rows from the FP16 columns on tensor cores
+cudaError_t sg_tc_kernel_rows(const GapTcModel& md, const __half* A, const float* nrm, const float* uq, int n,
+                              int m, const float* pnorm, float* k, float2* wv, int* err, cudaStream_t st);
+cudaError_t sg_tc_design_grad(const GapTcModel& md, int m, const __half* J, long long ncols, const int2* col_at,
+                              const float4* col_v, const float2* wv, float* dk, int* err, cudaStream_t st);
+
 // ---------------------------------------------------------------- forces.cu
 // chunks per structure of the two-level per-structure sums (part: [S][chunks][10] doubles)
 int sg_finish_chunks(int max_struct_atoms);

@@ -19,14 +19,6 @@
 #include "internal.h"
 #include "soapmath.cuh"
 
-// Coefficients of the normalised real-harmonic recursion, staged in shared memory so that
-// the (l, m) loops below can run rolled (small code, no instruction-cache pressure).
-template <typename T> struct YlmShared {
-  T seed[SG_MAX_LMAX + 2], s1[SG_MAX_LMAX + 2];
-  T a[SG_MAX_LMAX + 1][SG_MAX_LMAX + 2], b[SG_MAX_LMAX + 1][SG_MAX_LMAX + 2];
-  T d[SG_MAX_LMAX + 1][SG_MAX_LMAX + 2];
-};
-
 // EXACT: n_max == NC and l_max == LC (no runtime size guards in the channel loops).
 template <typename T, int NC, int LC, bool EXACT>
 __global__ void __launch_bounds__(SG_WARPS * 32)
@@ -50,18 +42,7 @@ pair_adj_kernel(const AdjArgs<T> a, int smem_per_warp) {
   const T FOUR_PI = (T)12.566370614359172;
   const T SQRT2 = (T)1.4142135623730951;
 
-  // recursion coefficients -> shared memory (once per block)
-  for (int k = threadIdx.x; k <= SG_MAX_LMAX; k += blockDim.x) {
-    ys.seed[k] = a.yc.seed[k];
-    ys.s1[k] = a.yc.s1[k];
-  }
-  if (threadIdx.x == 0) { ys.seed[SG_MAX_LMAX + 1] = T(0); ys.s1[SG_MAX_LMAX + 1] = T(0); }
-  for (int k = threadIdx.x; k < (SG_MAX_LMAX + 1) * (SG_MAX_LMAX + 2); k += blockDim.x) {
-    const int l = k / (SG_MAX_LMAX + 2), m = k - l * (SG_MAX_LMAX + 2);
-    ys.a[l][m] = m <= SG_MAX_LMAX ? a.yc.a[l][m] : T(0);
-    ys.b[l][m] = m <= SG_MAX_LMAX ? a.yc.b[l][m] : T(0);
-    ys.d[l][m] = m <= SG_MAX_LMAX ? a.yc.d[l][m] : T(0);
-  }
+  load_ylm_shared(ys, a.yc);  // recursion coefficients -> shared memory (once per block)
   __syncthreads();
 
   for (int atom = blockIdx.x * SG_WARPS + warp; atom < a.n_atoms; atom += gridDim.x * SG_WARPS) {

@@ -273,3 +273,31 @@ __device__ __forceinline__ void for_each_ylm_grad(T x, T y, T z, const YlmCoef<T
     }
   }
 }
+
+// Coefficients of the normalised real-harmonic recursion, staged in shared memory so that
+// (l, m) loops can run rolled (small code, no instruction-cache pressure).  Column
+// SG_MAX_LMAX + 1 is zero (the seed of the column past the last).
+template <typename T> struct YlmShared {
+  T seed[SG_MAX_LMAX + 2], s1[SG_MAX_LMAX + 2];
+  T a[SG_MAX_LMAX + 1][SG_MAX_LMAX + 2], b[SG_MAX_LMAX + 1][SG_MAX_LMAX + 2];
+  T d[SG_MAX_LMAX + 1][SG_MAX_LMAX + 2];
+};
+
+// Block-cooperative copy of the recursion coefficients into shared memory.
+template <typename T>
+__device__ inline void load_ylm_shared(YlmShared<T>& ys, const YlmCoef<T>& yc) {
+  for (int k = threadIdx.x; k <= SG_MAX_LMAX; k += blockDim.x) {
+    ys.seed[k] = yc.seed[k];
+    ys.s1[k] = yc.s1[k];
+  }
+  if (threadIdx.x == 0) {
+    ys.seed[SG_MAX_LMAX + 1] = T(0);
+    ys.s1[SG_MAX_LMAX + 1] = T(0);
+  }
+  for (int k = threadIdx.x; k < (SG_MAX_LMAX + 1) * (SG_MAX_LMAX + 2); k += blockDim.x) {
+    const int l = k / (SG_MAX_LMAX + 2), m = k - l * (SG_MAX_LMAX + 2);
+    ys.a[l][m] = m <= SG_MAX_LMAX ? yc.a[l][m] : T(0);
+    ys.b[l][m] = m <= SG_MAX_LMAX ? yc.b[l][m] : T(0);
+    ys.d[l][m] = m <= SG_MAX_LMAX ? yc.d[l][m] : T(0);
+  }
+}

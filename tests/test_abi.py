@@ -61,6 +61,9 @@ def test_null_handle_is_rejected(lib):
     d = ctypes.c_int32()
     assert lib.soapgap_descriptor_dim(None, ctypes.byref(d)) == L.E_INVALID_ARG
     assert lib.soapgap_compute(None, None, 0, None, None, None, None, None, None, None) == L.E_INVALID_ARG
+    assert lib.soapgap_design(None, None, 0, None, None, None, None) == L.E_INVALID_ARG
+    assert lib.soapgap_kernel_rows(None, None, 0, None, None) == L.E_INVALID_ARG
+    assert lib.soapgap_design_times(None, None) == L.E_INVALID_ARG
     lib.soapgap_destroy(None)
 
 
