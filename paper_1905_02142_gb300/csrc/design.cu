@@ -43,12 +43,15 @@ __device__ __forceinline__ T warp_max(T v) {
   return v;
 }
 
+constexpr int JB = 16;  // pairs per batch of the Jacobian kernel's radial phase
+
 // floats per warp region of the Jacobian kernel (multiple of 4 elements: Vec4 alignment)
 template <int NC, int LC>
 int jac_per_warp(int nsp, int nmax, int lmax, int dim) {
   constexpr int NP = (NC + 3) / 4 * 4, LP = (LC + 1 + 3) / 4 * 4;
   const int L = (lmax + 1) * (lmax + 1), nch = nsp * nmax, lp1 = lmax + 1;
-  const int n = 4 * L + 4 * nch * lp1 + nch * L + dim + 6 * dim + 2 * NP + 2 * LP;
+  const int jt = std::max(4 * L, 3 * dim);
+  const int n = 4 * nch * lp1 + 4 * JB + nch * L + dim + (jt + 3) / 4 * 4 + 3 * dim + JB * (2 * NP + 2 * LP) + 2 * JB;
   return (n + 3) / 4 * 4;
 }
 
@@ -64,42 +67,45 @@ design_jacobian_kernel(const JacArgs<T> a, int per_warp) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nsp = a.nsp, nmax = a.nmax, lmax = a.lmax, D = a.dim;
   const int L = (lmax + 1) * (lmax + 1), nch = nsp * nmax, lp1 = lmax + 1;
-  const int npair = nch * (nch + 1) / 2;
   YlmShared<T>& ys = *reinterpret_cast<YlmShared<T>*>(smem_raw);
   size_t off = al32(sizeof(YlmShared<T>));
-  int* pcdec = reinterpret_cast<int*>(smem_raw + off);
-  off += al32(sizeof(int) * npair);
+  int* ddec = reinterpret_cast<int*>(smem_raw + off);  // [D] c1 | c2 << 8 | l << 16
+  off += al32(sizeof(int) * D);
+  int* edec = reinterpret_cast<int*>(smem_raw + off);  // [nch * lp1] c | l << 8
+  off += al32(sizeof(int) * nch * lp1);
   float* qbar_s = reinterpret_cast<float*>(smem_raw + off);
   off += al32(sizeof(float) * (TABLE ? D : 1));
   T* wbase = reinterpret_cast<T*>(smem_raw + off) + (size_t)warp * per_warp;
-  Vec4<T>* Aw = reinterpret_cast<Vec4<T>*>(wbase);  // [L]   A_lm, grad A_lm
-  Vec4<T>* XZ = Aw + L;                              // [nch][lp1]  X, Z
-  T* cs = reinterpret_cast<T*>(XZ + nch * lp1);      // [nch][L]  c of the owner
+  constexpr int RW = 2 * NP + 2 * LP;                // radial record of one pair
+  const int jt = (max(4 * L, 3 * D) + 3) / 4 * 4;
+  Vec4<T>* XZ = reinterpret_cast<Vec4<T>*>(wbase);  // [nch][lp1]  X, Z
+  Vec4<T>* geo = XZ + nch * lp1;                     // [JB]  rhat, 1/r (< 0: masked pair)
+  T* Jt = reinterpret_cast<T*>(geo + JB);            // [3][D]  J of the current pair, and before
+  Vec4<T>* Aw = reinterpret_cast<Vec4<T>*>(Jt);      //   it [L] A_lm, grad A_lm (used up by X, Z)
+  T* cs = Jt + jt;                                   // [nch][L]  c of the owner
   T* qi = cs + nch * L;                              // [D]     q of the owner
-  T* Jt = qi + D;                                    // [3][D]  J of the current pair
-  T* Jacc = Jt + 3 * D;                              // [3][D]  -sum of J (self columns)
-  T* bs = Jacc + 3 * D;                              // [NP] b_n, [NP] b_n', [LP] A_l, [LP] A_l'
-  T* dbs = bs + NP;
-  T* ils = dbs + NP;
-  T* dils = ils + LP;
+  T* Jacc = qi + D;                                  // [3][D]  -sum of J (self columns)
+  T* rad = Jacc + 3 * D;                             // [JB][RW] b_n, b_n', A_l, A_l' per pair
+  int* pinfo = reinterpret_cast<int*>(rad + JB * RW);  // [JB][2] first column, neighbour
   const T SQRT2 = (T)1.4142135623730951;
 
   load_ylm_shared(ys, a.yc);
-  for (int pc = threadIdx.x; pc < npair; pc += blockDim.x) {
+  for (int d = threadIdx.x; d < D; d += blockDim.x) {
+    const int pc = d / lp1, l = d - pc * lp1;
     int c1 = 0, rem = pc;
     while (rem >= nch - c1) {
       rem -= nch - c1;
       ++c1;
     }
-    pcdec[pc] = c1 | ((c1 + rem) << 16);
+    ddec[d] = c1 | ((c1 + rem) << 8) | (l << 16);
   }
+  for (int e = threadIdx.x; e < nch * lp1; e += blockDim.x) edec[e] = (e / lp1) | ((e % lp1) << 8);
   if (TABLE)
     for (int d = threadIdx.x; d < D; d += blockDim.x) qbar_s[d] = a.qbar[d];
   __syncthreads();
 
-  // write the three columns of one pair (or self slot) from src[3][D]
-  auto emit3 = [&](const T* src, long long col0, int owner, int target) {
-    T mx[3], tb[3], tq[3];
+  // per-lane partials over the lane's entries of src[3][D]: max |J|, q_owner.J, qbar.J
+  auto partials = [&](const T* src, T* mx, T* tq, T* tb) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) { mx[c] = T(0); tb[c] = T(0); tq[c] = T(0); }
     for (int d = lane; d < D; d += 32) {
@@ -113,6 +119,9 @@ design_jacobian_kernel(const JacArgs<T> a, int per_warp) {
         tb[c] = fma(qb, v, tb[c]);
       }
     }
+  };
+  // write the three columns of one pair (or self slot) from src[3][D], given the partials
+  auto emit3 = [&](const T* src, long long col0, int owner, int target, T* mx, T* tq, T* tb) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       mx[c] = warp_max(mx[c]);
@@ -162,24 +171,34 @@ design_jacobian_kernel(const JacArgs<T> a, int per_warp) {
     for (int sj = 0; sj < nsp; ++sj) {
       const int beg = a.seg_offs[atom * nsp + sj], end = a.seg_offs[atom * nsp + sj + 1];
       const int blk0 = sj * nmax;
-      for (int p = beg; p < end; ++p) {
-        const Vec4<T> v = a.pair_r[p];
-        const int j = a.pair_j[p];
-        const long long col0 = 3LL * ((long long)a.rev[p] + j);
-        // |r| < 0 marks a pair beyond r_cut in a list built with a skin: zero columns
-        const bool live = v.w >= T(0);
-        const T r = live ? v.w : T(1), inv = T(1) / r;
-        const T ux = live ? v.x * inv : T(0), uy = live ? v.y * inv : T(0), uz = live ? v.z * inv : T(1);
-        if (live) {
-          // ---- radial terms (lane 0)
-          if (lane == 0) {
+      for (int base = beg; base < end; base += JB) {
+        // ---- per batch of JB pairs, one lane each: geometry, columns, radial terms
+        {
+          const int p = base + lane;
+          if (lane < JB && p < end) {
+            const Vec4<T> v = a.pair_r[p];
+            const int j = a.pair_j[p];
+            pinfo[2 * lane] = 3 * (a.rev[p] + j);
+            pinfo[2 * lane + 1] = j;
+            // |r| < 0 marks a pair beyond r_cut in a list built with a skin: zero columns
+            const bool live = v.w >= T(0);
+            const T r = live ? v.w : T(1), inv = T(1) / r;
+            geo[lane] = Vec4<T>{live ? v.x * inv : T(0), live ? v.y * inv : T(0), live ? v.z * inv : T(1),
+                                live ? inv : T(-1)};
+            T* rr = rad + lane * RW;
             if constexpr (TABLE) {
               float f[NC + LC + 1], df[NC + LC + 1];
               table_interp<NC, LC, true>(a.table, a.ti, (float)r, f, df);
 #pragma unroll
-              for (int n = 0; n < NC; ++n) { bs[n] = (T)f[n]; dbs[n] = (T)df[n]; }
+              for (int n = 0; n < NP; ++n) {
+                rr[n] = n < NC ? (T)f[n] : T(0);
+                rr[NP + n] = n < NC ? (T)df[n] : T(0);
+              }
 #pragma unroll
-              for (int l = 0; l <= LC; ++l) { ils[l] = (T)f[NC + l]; dils[l] = (T)df[NC + l]; }
+              for (int l = 0; l < LP; ++l) {
+                rr[2 * NP + l] = l <= LC ? (T)f[NC + l] : T(0);
+                rr[2 * NP + LP + l] = l <= LC ? (T)df[NC + l] : T(0);
+              }
             } else {
               using Dd = Dual<double>;
               Dd rd((double)r, 1.0);
@@ -193,8 +212,8 @@ design_jacobian_kernel(const JacArgs<T> a, int per_warp) {
                   bv = fma((double)a.bc.W[n][al], ba[al].v, bv);
                   bd = fma((double)a.bc.W[n][al], ba[al].d, bd);
                 }
-                bs[n] = (T)(n < nmax ? bv : 0.0);
-                dbs[n] = (T)(n < nmax ? bd : 0.0);
+                rr[n] = (T)(n < nmax ? bv : 0.0);
+                rr[NP + n] = (T)(n < nmax ? bd : 0.0);
               }
               Dd spp = a.p.s0p + a.p.ap * rd;
               Dd ild[LC + 1];
@@ -202,118 +221,140 @@ design_jacobian_kernel(const JacArgs<T> a, int per_warp) {
 #pragma unroll
               for (int l = 0; l <= LC; ++l) {
                 const double wl = (l <= lmax) ? 12.566370614359172 * (a.p.eq08 ? (2.0 * l + 1.0) : 1.0) : 0.0;
-                ils[l] = (T)(wl * ild[l].v);
-                dils[l] = (T)(wl * ild[l].d);
+                rr[2 * NP + l] = (T)(wl * ild[l].v);
+                rr[2 * NP + LP + l] = (T)(wl * ild[l].d);
               }
             }
           }
-          __syncwarp();
-          // ---- angular terms: lane m runs column m of the harmonic recursion
-          if (lane <= lmax) {
-            const int m = lane;
-            T cm = 1, sm = 0, cmm1 = 0, smm1 = 0;
-            for (int k = 1; k <= m; ++k) {
-              const T c2 = ux * cm - uy * sm, s2 = ux * sm + uy * cm;
-              cmm1 = cm;
-              smm1 = sm;
-              cm = c2;
-              sm = s2;
-            }
-            auto put = [&](int lm, T il, T dil, T y, T gx, T gy, T gz) {
-              const T gd = gx * ux + gy * uy + gz * uz;
-              const T rr = dil * y, tt = il * inv;
-              Aw[lm] = Vec4<T>{il * y, fma(rr, ux, tt * (gx - gd * ux)), fma(rr, uy, tt * (gy - gd * uy)),
-                               fma(rr, uz, tt * (gz - gd * uz))};
-            };
-            T a2 = 0, a1 = ys.seed[m], b2 = 0, b1 = ys.seed[m + 1];
-            const T fm = (T)m;
-            for (int l = m; l <= lmax; ++l) {
-              T pl, ql = T(0);
-              if (l == m) {
-                pl = a1;
-              } else {
-                pl = (l == m + 1) ? ys.s1[m] * uz * a1 : ys.a[l][m] * uz * a1 - ys.b[l][m] * a2;
-                a2 = a1;
-                a1 = pl;
-                if (l == m + 1) {
-                  ql = b1;
-                } else {
-                  ql = (l == m + 2) ? ys.s1[m + 1] * uz * b1 : ys.a[l][m + 1] * uz * b1 - ys.b[l][m + 1] * b2;
-                  b2 = b1;
-                  b1 = ql;
-                }
-              }
-              const T dz = ys.d[l][m] * ql;
-              const T il = ils[l], dil = dils[l];
-              const int l0 = l * l + l;
-              if (m == 0) {
-                put(l0, il, dil, pl, T(0), T(0), dz);
-              } else {
-                const T pm = fm * pl;
-                put(l0 + m, il, dil, pl * cm, pm * cmm1, -pm * smm1, dz * cm);
-                put(l0 - m, il, dil, pl * sm, pm * smm1, pm * cmm1, dz * sm);
-              }
-            }
-          }
-          __syncwarp();
-          // ---- X and Z for every channel and l
-          for (int e = lane; e < nch * lp1; e += 32) {
-            const int c2 = e / lp1, l = e - c2 * lp1;
-            const T* crow = cs + c2 * L;
-            T x = 0, zx = 0, zy = 0, zz = 0;
-            for (int lm = l * l; lm < (l + 1) * (l + 1); ++lm) {
-              const Vec4<T> w4 = Aw[lm];
-              const T cv = crow[lm];
-              x = fma(w4.x, cv, x);
-              zx = fma(w4.y, cv, zx);
-              zy = fma(w4.z, cv, zy);
-              zz = fma(w4.w, cv, zz);
-            }
-            XZ[e] = Vec4<T>{x, zx, zy, zz};
-          }
-          __syncwarp();
-          // ---- J over the packed entries (c1 <= c2, l)
-          for (int d = lane; d < D; d += 32) {
-            const int pc = d / lp1, l = d - pc * lp1;
-            const int cc = pcdec[pc];
-            const int c1 = cc & 0xffff, c2 = cc >> 16;
-            const int n1 = c1 - blk0, n2 = c2 - blk0;
-            T j0 = 0, j1 = 0, j2 = 0;
-            if ((unsigned)n1 < (unsigned)nmax) {
-              const Vec4<T> z = XZ[c2 * lp1 + l];
-              const T br = dbs[n1] * z.x, b0 = bs[n1];
-              j0 = fma(br, ux, b0 * z.y);
-              j1 = fma(br, uy, b0 * z.z);
-              j2 = fma(br, uz, b0 * z.w);
-            }
-            if ((unsigned)n2 < (unsigned)nmax) {
-              const Vec4<T> z = XZ[c1 * lp1 + l];
-              const T br = dbs[n2] * z.x, b0 = bs[n2];
-              j0 += fma(br, ux, b0 * z.y);
-              j1 += fma(br, uy, b0 * z.z);
-              j2 += fma(br, uz, b0 * z.w);
-            }
-            const T f = c1 == c2 ? T(1) : SQRT2;
-            j0 *= f;
-            j1 *= f;
-            j2 *= f;
-            Jt[d] = j0;
-            Jt[D + d] = j1;
-            Jt[2 * D + d] = j2;
-            Jacc[d] -= j0;
-            Jacc[D + d] -= j1;
-            Jacc[2 * D + d] -= j2;
-          }
-        } else {
-          for (int d = lane; d < 3 * D; d += 32) Jt[d] = T(0);
         }
         __syncwarp();
-        emit3(Jt, col0, atom, j);
-        __syncwarp();
+        const int cnt = min(JB, end - base);
+        for (int k = 0; k < cnt; ++k) {
+          const Vec4<T> g = geo[k];
+          const T* bs = rad + k * RW;
+          const T* dbs = bs + NP;
+          const T* ils = bs + 2 * NP;
+          const T* dils = ils + LP;
+          const T ux = g.x, uy = g.y, uz = g.z, inv = g.w;
+          T mx[3], tq[3], tb[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) { mx[c] = T(0); tq[c] = T(0); tb[c] = T(0); }
+          if (inv > T(0)) {
+            // ---- angular terms: lanes m and 16 + m run column m of the harmonic recursion,
+            // the first writing the +m (and m = 0) terms, the second the -m terms
+            const int m = lane & 15;
+            const bool neg = lane >= 16;
+            if (m <= lmax && !(neg && m == 0)) {
+              T cm = 1, sm = 0, cmm1 = 0, smm1 = 0;
+              for (int t = 1; t <= m; ++t) {
+                const T c2 = ux * cm - uy * sm, s2 = ux * sm + uy * cm;
+                cmm1 = cm;
+                smm1 = sm;
+                cm = c2;
+                sm = s2;
+              }
+              auto put = [&](int lm, T il, T dil, T y, T gx, T gy, T gz) {
+                const T gd = gx * ux + gy * uy + gz * uz;
+                const T rr = dil * y, tt = il * inv;
+                Aw[lm] = Vec4<T>{il * y, fma(rr, ux, tt * (gx - gd * ux)), fma(rr, uy, tt * (gy - gd * uy)),
+                                 fma(rr, uz, tt * (gz - gd * uz))};
+              };
+              T a2 = 0, a1 = ys.seed[m], b2 = 0, b1 = ys.seed[m + 1];
+              const T fm = (T)m;
+              for (int l = m; l <= lmax; ++l) {
+                T pl, ql = T(0);
+                if (l == m) {
+                  pl = a1;
+                } else {
+                  pl = (l == m + 1) ? ys.s1[m] * uz * a1 : ys.a[l][m] * uz * a1 - ys.b[l][m] * a2;
+                  a2 = a1;
+                  a1 = pl;
+                  if (l == m + 1) {
+                    ql = b1;
+                  } else {
+                    ql = (l == m + 2) ? ys.s1[m + 1] * uz * b1 : ys.a[l][m + 1] * uz * b1 - ys.b[l][m + 1] * b2;
+                    b2 = b1;
+                    b1 = ql;
+                  }
+                }
+                const T dz = ys.d[l][m] * ql;
+                const T il = ils[l], dil = dils[l];
+                const int l0 = l * l + l;
+                if (m == 0) {
+                  put(l0, il, dil, pl, T(0), T(0), dz);
+                } else {
+                  const T pm = fm * pl;
+                  if (!neg) put(l0 + m, il, dil, pl * cm, pm * cmm1, -pm * smm1, dz * cm);
+                  else put(l0 - m, il, dil, pl * sm, pm * smm1, pm * cmm1, dz * sm);
+                }
+              }
+            }
+            __syncwarp();
+            // ---- X and Z for every channel and l
+            for (int e = lane; e < nch * lp1; e += 32) {
+              const int ec = edec[e];
+              const int c2 = ec & 0xff, l = ec >> 8;
+              const T* crow = cs + c2 * L;
+              T x = 0, zx = 0, zy = 0, zz = 0;
+              for (int lm = l * l; lm < (l + 1) * (l + 1); ++lm) {
+                const Vec4<T> w4 = Aw[lm];
+                const T cv = crow[lm];
+                x = fma(w4.x, cv, x);
+                zx = fma(w4.y, cv, zx);
+                zy = fma(w4.z, cv, zy);
+                zz = fma(w4.w, cv, zz);
+              }
+              XZ[e] = Vec4<T>{x, zx, zy, zz};
+            }
+            __syncwarp();
+            // ---- J over the packed entries (c1 <= c2, l), with the lane's partials
+            for (int d = lane; d < D; d += 32) {
+              const int cc = ddec[d];
+              const int c1 = cc & 0xff, c2 = (cc >> 8) & 0xff, l = cc >> 16;
+              const int n1 = c1 - blk0, n2 = c2 - blk0;
+              T j0 = 0, j1 = 0, j2 = 0;
+              if ((unsigned)n1 < (unsigned)nmax) {
+                const Vec4<T> z = XZ[c2 * lp1 + l];
+                const T br = dbs[n1] * z.x, b0 = bs[n1];
+                j0 = fma(br, ux, b0 * z.y);
+                j1 = fma(br, uy, b0 * z.z);
+                j2 = fma(br, uz, b0 * z.w);
+              }
+              if ((unsigned)n2 < (unsigned)nmax) {
+                const Vec4<T> z = XZ[c1 * lp1 + l];
+                const T br = dbs[n2] * z.x, b0 = bs[n2];
+                j0 += fma(br, ux, b0 * z.y);
+                j1 += fma(br, uy, b0 * z.z);
+                j2 += fma(br, uz, b0 * z.w);
+              }
+              const T f = c1 == c2 ? T(1) : SQRT2;
+              const T jv[3] = {j0 * f, j1 * f, j2 * f};
+              const T qv = qi[d];
+              const T qb = TABLE ? (T)qbar_s[d] : T(0);
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                Jt[c * D + d] = jv[c];
+                Jacc[c * D + d] -= jv[c];
+                mx[c] = max(mx[c], abs(jv[c]));
+                tq[c] = fma(qv, jv[c], tq[c]);
+                tb[c] = fma(qb, jv[c], tb[c]);
+              }
+            }
+          } else {
+            for (int d = lane; d < 3 * D; d += 32) Jt[d] = T(0);
+          }
+          __syncwarp();
+          emit3(Jt, (long long)pinfo[2 * k], atom, pinfo[2 * k + 1], mx, tq, tb);
+          __syncwarp();
+        }
       }
     }
     const int ie = a.seg_offs[(atom + 1) * nsp];
-    emit3(Jacc, 3LL * ((long long)ie + atom), atom, atom);
+    {
+      T mx[3], tq[3], tb[3];
+      partials(Jacc, mx, tq, tb);
+      emit3(Jacc, 3LL * ((long long)ie + atom), atom, atom, mx, tq, tb);
+    }
   }
 }
 
@@ -321,8 +362,8 @@ template <typename T, int NC, int LC, bool TABLE>
 cudaError_t launch_jacobian(const JacArgs<T>& a, cudaStream_t st) {
   const int per_warp = jac_per_warp<NC, LC>(a.nsp, a.nmax, a.lmax, a.dim);
   const int nch = a.nsp * a.nmax;
-  const size_t head = al32(sizeof(YlmShared<T>)) + al32(sizeof(int) * (size_t)nch * (nch + 1) / 2) +
-                      al32(sizeof(float) * (TABLE ? a.dim : 1));
+  const size_t head = al32(sizeof(YlmShared<T>)) + al32(sizeof(int) * (size_t)a.dim) +
+                      al32(sizeof(int) * (size_t)nch * (a.lmax + 1)) + al32(sizeof(float) * (TABLE ? a.dim : 1));
   // up to SG_WARPS warps per block, fewer when their regions do not fit in 220 KB
   const size_t limit = 220 * 1024, warp_bytes = (size_t)per_warp * sizeof(T);
   if (head + warp_bytes > limit) return cudaErrorInvalidConfiguration;

@@ -19,6 +19,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -103,6 +104,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+
+// 16 and 8 consecutive columns of the warp's 32 lanes (no wait: see tmem_wait)
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld8_nw(uint32_t taddr, uint32_t* v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Columns an epilogue takes per TMEM read: Epi::CHUNK (24 or 32) if declared, else 32.
+template <class E, class = void> struct EpiChunk { static constexpr int value = 32; };
+template <class E> struct EpiChunk<E, std::void_t<decltype(E::CHUNK)>> { static constexpr int value = E::CHUNK; };
 
 // ------------------------------------------------------------------ epilogues
 struct EpiStore {  // C = A B^T (diagnostic)
@@ -259,41 +279,66 @@ struct EpiDesignGrad {
   const float2* wv;                  // [N][ldw]
   float* dk;                         // [N][3][m]
   float ns;
-  int owner, target;
-  float2 w;
-  float acc[3];
+  int target;
+  float acc0, acc1, acc2;
   __device__ void flush(int row) {
     if (target >= 0) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-        if (acc[a] != 0.f) atomicAdd(dk + ((size_t)target * 3 + a) * m + row, acc[a]);
+      float* o = dk + (size_t)target * 3 * m + row;
+      if (acc0 != 0.f) atomicAdd(o, acc0);
+      if (acc1 != 0.f) atomicAdd(o + m, acc1);
+      if (acc2 != 0.f) atomicAdd(o + 2 * m, acc2);
     }
-    acc[0] = acc[1] = acc[2] = 0.f;
+    acc0 = acc1 = acc2 = 0.f;
   }
   __device__ void begin(int row) {
     ns = row < m ? scol[row].y : 0.f;
-    owner = target = -1;
-    w = make_float2(0.f, 0.f);
-    acc[0] = acc[1] = acc[2] = 0.f;
+    target = -1;
+    acc0 = acc1 = acc2 = 0.f;
   }
+  // Tiles of 192 columns read 24 at a time, so every chunk starts at a column triple
+  // (the three components of one pair or self slot: one owner, one target).  Lane j < 24
+  // reads the record of column col0 + j (coalesced) and the records reach every lane by
+  // shuffles; the 8 owners' weights at this row are requested before the first use, so
+  // their latencies overlap.  All lanes take part (rows past m compute but do not write).
+  static constexpr int CHUNK = 24;
   __device__ void apply(int row, int col0, const uint32_t* v) {
-    if (row >= m) return;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool live = row < m;
+    const int mine = col0 + lane;
+    int2 at_l = make_int2(-1, -1);
+    float4 cv_l = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane < CHUNK && mine < ncols) {
+      at_l = __ldg(col_at + mine);
+      cv_l = __ldg(col_v + mine);
+    }
+    float2 w[CHUNK / 3];
+    int tg[CHUNK / 3];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const int col = col0 + j;
-      if (col >= ncols) continue;
-      const int2 at = __ldg(col_at + col);
-      if (at.x != owner) {
-        owner = at.x;
-        w = __ldg(wv + (size_t)owner * ldw + row);
+    for (int t = 0; t < CHUNK / 3; ++t) {
+      const int o = __shfl_sync(FULL, at_l.x, 3 * t);
+      tg[t] = __shfl_sync(FULL, at_l.y, 3 * t);
+      w[t] = (live && o >= 0) ? __ldg(wv + (size_t)o * ldw + row) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int t = 0; t < CHUNK / 3; ++t) {
+      if (tg[t] < 0) continue;  // past the last column (same for every lane)
+      if (tg[t] != target) {
+        if (live) flush(row);
+        target = tg[t];
       }
-      if (at.y != target) {
-        flush(row);
-        target = at.y;
+      float val[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int j = 3 * t + a;
+        const float cx = __shfl_sync(FULL, cv_l.x, j);
+        const float cy = __shfl_sync(FULL, cv_l.y, j);
+        const float cz = __shfl_sync(FULL, cv_l.z, j);
+        val[a] = fmaf(w[t].x, fmaf(ns * cz, __uint_as_float(v[j]), cx), -w[t].y * cy);
       }
-      const float4 cv = __ldg(col_v + col);
-      const float val = fmaf(w.x, fmaf(ns * cv.z, __uint_as_float(v[j]), cv.x), -w.y * cv.y);
-      acc[col % 3] += val;
+      acc0 += val[0];
+      acc1 += val[1];
+      acc2 += val[2];
     }
   }
   __device__ void end(int row, int) {
@@ -318,6 +363,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
   constexpr int HALVES = EPI_WARPS / 4;           // column groups per tile
   constexpr int COLS = BN / HALVES;               // columns per epilogue warp
+  constexpr int CH = EpiChunk<Epi>::value;        // columns per TMEM read
+  static_assert((CH == 32 || CH == 24) && COLS % CH == 0, "epilogue chunking");
+  // TMEM is allocated in powers of two (>= 32 columns): room for two BN-wide accumulators
+  constexpr uint32_t TMEM_COLS = 2 * BN <= 32 ? 32 : 2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 2 * BN <= 256 ? 256 : 512;
+  static_assert(2 * BN <= 512, "two accumulators must fit in tensor memory");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
@@ -345,7 +395,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"((uint32_t)(2 * BN))
+                 "r"(TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -432,10 +482,17 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       const int row = m0 + lg * 32 + lane;
       epi.begin(row);
 #pragma unroll 1
-      for (int c = 0; c < COLS / 32; ++c) {
-        uint32_t v[32];
-        const int col = half * COLS + c * 32;
-        tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + col), v);
+      for (int c = 0; c < COLS / CH; ++c) {
+        uint32_t v[CH];
+        const int col = half * COLS + c * CH;
+        const uint32_t ta = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + col);
+        if constexpr (CH == 32) {
+          tmem_ld32(ta, v);
+        } else {
+          tmem_ld16_nw(ta, v);
+          tmem_ld8_nw(ta + 16, v + 16);
+          tmem_wait();
+        }
         epi.apply(row, n0 + col, v);
       }
       epi.end(row, (MFAST ? t / m_tiles : t % n_tiles) * HALVES + half);
@@ -447,7 +504,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   fence_before();
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN))
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
                  : "memory");
 }
 
@@ -621,5 +678,5 @@ cudaError_t sg_tc_design_grad(const GapTcModel& md, int m, const __half* J, long
   e.wv = wv;
   e.dk = dk;
   // A = the unit centred sparse rows (the hi third of each row of B), K = dp
-  return launch_gemm<256, 4, 8, true>(md.B, md.mp, J, (int)ncols, md.dp, e, err, st, 3 * md.dp);
+  return launch_gemm<192, 5, 16, true>(md.B, md.mp, J, (int)ncols, md.dp, e, err, st, 3 * md.dp);
 }
