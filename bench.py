@@ -53,6 +53,10 @@ def parse():
                     help="descriptors-only throughput over (n_max, l_max) on the paper's timing box")
     ap.add_argument("--no-md", action="store_true", help="skip the molecular-dynamics leg")
     ap.add_argument("--no-design", action="store_true", help="skip the fitting-matrix leg")
+    ap.add_argument("--design-only", action="store_true",
+                    help="only the fitting-matrix leg (printed as its own JSON line)")
+    ap.add_argument("--design-structures", type=int, default=256,
+                    help="structures of the training-batch recipe in the fitting-matrix leg")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-structures workload (graph replay)")
     return ap.parse_args()
@@ -342,6 +346,9 @@ def run_design(args, dev, flush, stream):
 
     from paper_1905_02142_gb300.api import SoapGap, Structures
     wb = synth.get_workload("batch256_n8l8")
+    if args.design_structures != wb.n_struct:
+        wb = dataclasses.replace(wb, n_struct=args.design_structures,
+                                 name=f"{wb.name}@{args.design_structures}structures")
     pb = wb.params()
     bb = wb.structures()
     sb = Structures.from_batch(bb, device=dev)
@@ -610,6 +617,13 @@ def main():
         if args.timing_grid:
             if rank == 0:
                 run_timing_grid(args, torch.device("cuda", local_rank))
+            return
+        if args.design_only:
+            if rank == 0:
+                dev = torch.device("cuda", local_rank)
+                torch.cuda.set_device(dev)
+                flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+                print(json.dumps(run_design(args, dev, flush, torch.cuda.current_stream(dev))), flush=True)
             return
         run_ours(args, rank, world, local_rank)
     finally:

@@ -71,7 +71,7 @@ design_jacobian_kernel(const JacArgs<T> a, int per_warp) {
   size_t off = al32(sizeof(YlmShared<T>));
   int* ddec = reinterpret_cast<int*>(smem_raw + off);  // [D] c1 | c2 << 8 | l << 16
   off += al32(sizeof(int) * D);
-  int* edec = reinterpret_cast<int*>(smem_raw + off);  // [nch * lp1] c | l << 8
+  int* edec = reinterpret_cast<int*>(smem_raw + off);  // [nch * lp1] c | l << 8, by decreasing l
   off += al32(sizeof(int) * nch * lp1);
   float* qbar_s = reinterpret_cast<float*>(smem_raw + off);
   off += al32(sizeof(float) * (TABLE ? D : 1));
@@ -99,7 +99,8 @@ design_jacobian_kernel(const JacArgs<T> a, int per_warp) {
     }
     ddec[d] = c1 | ((c1 + rem) << 8) | (l << 16);
   }
-  for (int e = threadIdx.x; e < nch * lp1; e += blockDim.x) edec[e] = (e / lp1) | ((e % lp1) << 8);
+  // X/Z work items by decreasing l: the lanes of one round then sum over similar m ranges
+  for (int e = threadIdx.x; e < nch * lp1; e += blockDim.x) edec[e] = (e % nch) | ((lmax - e / nch) << 8);
   if (TABLE)
     for (int d = threadIdx.x; d < D; d += blockDim.x) qbar_s[d] = a.qbar[d];
   __syncthreads();
@@ -128,32 +129,46 @@ design_jacobian_kernel(const JacArgs<T> a, int per_warp) {
       tq[c] = warp_sum(tq[c]);
       tb[c] = warp_sum(tb[c]);
     }
+    T inv_scale[3] = {T(1), T(1), T(1)};
+    if constexpr (TABLE) {
+      // the three columns are contiguous rows of ld halves: 16-byte pieces over all lanes
+      float sc[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const long long col = col0 + c;
-      T inv_scale = T(1);
-      if constexpr (TABLE) {
+      for (int c = 0; c < 3; ++c) {
         const int e = mx[c] > T(0) ? 14 - ilogbf((float)mx[c]) : 0;
-        const float sc = ldexpf(1.f, e);
-        inv_scale = (T)ldexpf(1.f, -e);
-        __half* row = reinterpret_cast<__half*>(a.J) + (size_t)col * a.ld;
-        for (int k8 = lane * 8; k8 < a.ld; k8 += 256) {
-          __align__(16) __half h8[8];
+        sc[c] = ldexpf(1.f, e);
+        inv_scale[c] = (T)ldexpf(1.f, -e);
+      }
+      const int c8 = a.ld / 8;
+      __half* rows = reinterpret_cast<__half*>(a.J) + (size_t)col0 * a.ld;
+      for (int q = lane; q < 3 * c8; q += 32) {
+        const int c = (q >= c8) + (q >= 2 * c8);
+        const int k8 = (q - c * c8) * 8;
+        const float scc = c == 0 ? sc[0] : (c == 1 ? sc[1] : sc[2]);
+        const T* sp = src + c * D;
+        __align__(16) __half h8[8];
 #pragma unroll
-          for (int t = 0; t < 8; ++t) {
-            const int d = k8 + t;
-            h8[t] = __float2half_rn(d < D ? (float)src[c * D + d] * sc : 0.f);
-          }
-          *reinterpret_cast<uint4*>(row + k8) = *reinterpret_cast<const uint4*>(h8);
+        for (int t = 0; t < 8; ++t) {
+          const int d = k8 + t;
+          h8[t] = __float2half_rn(d < D ? (float)sp[d] * scc : 0.f);
         }
-      } else {
-        double* row = reinterpret_cast<double*>(a.J) + (size_t)col * a.ld;
-        for (int d = lane; d < a.ld; d += 32) row[d] = d < D ? (double)src[c * D + d] : 0.0;
+        *reinterpret_cast<uint4*>(rows + (size_t)q * 8) = *reinterpret_cast<const uint4*>(h8);
       }
-      if (lane == 0) {
-        a.col_at[col] = make_int2(owner, target);
-        a.col_v[col] = Vec4<T>{tb[c], tq[c], inv_scale, T(0)};
+    } else {
+      double* rows = reinterpret_cast<double*>(a.J) + (size_t)col0 * a.ld;
+      for (int q = lane; q < 3 * a.ld; q += 32) {
+        const int c = (q >= a.ld) + (q >= 2 * a.ld);
+        const int d = q - c * a.ld;
+        rows[q] = d < D ? (double)src[c * D + d] : 0.0;
       }
+    }
+    if (lane < 3) {
+      const int c = lane;
+      const T tbc = c == 0 ? tb[0] : (c == 1 ? tb[1] : tb[2]);
+      const T tqc = c == 0 ? tq[0] : (c == 1 ? tq[1] : tq[2]);
+      const T isc = c == 0 ? inv_scale[0] : (c == 1 ? inv_scale[1] : inv_scale[2]);
+      a.col_at[col0 + c] = make_int2(owner, target);
+      a.col_v[col0 + c] = Vec4<T>{tbc, tqc, isc, T(0)};
     }
   };
 
@@ -304,7 +319,7 @@ design_jacobian_kernel(const JacArgs<T> a, int per_warp) {
                 zy = fma(w4.z, cv, zy);
                 zz = fma(w4.w, cv, zz);
               }
-              XZ[e] = Vec4<T>{x, zx, zy, zz};
+              XZ[c2 * lp1 + l] = Vec4<T>{x, zx, zy, zz};
             }
             __syncwarp();
             // ---- J over the packed entries (c1 <= c2, l), with the lane's partials
@@ -372,6 +387,12 @@ cudaError_t launch_jacobian(const JacArgs<T>& a, cudaStream_t st) {
   auto kern = design_jacobian_kernel<T, NC, LC, TABLE>;
   cudaError_t e = sg_set_smem<design_jacobian_kernel<T, NC, LC, TABLE>>(smem);
   if (e != cudaSuccess) return e;
+  // all of the SM's shared memory for this kernel: one more block per SM for common sizes
+  static bool carved = false;
+  if (!carved) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    carved = true;
+  }
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
