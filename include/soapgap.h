@@ -238,11 +238,12 @@ int soapgap_backward(soapgap_handle* h, const soapgap_batch* batch, const double
  * float for MIXED, double for FP64; k_struct [n_struct][M] DEVICE double.  Outputs not
  * requested may be NULL.  flags may add SOAPGAP_TIMING (soapgap_design_times).
  * Precision (MIXED): kernel rows from the same split tensor-core products as the energy
- * (relative error ~1e-7); force rows from single FP16 products of the centred sparse rows
- * with power-of-two scaled FP16 descriptor Jacobians (RMS relative error ~1e-4).
+ * (relative error ~1e-7, on top of the descriptors' own error); force rows from single FP16
+ * products of the centred sparse rows with power-of-two scaled FP16 descriptor Jacobians
+ * projected orthogonally to the owner's descriptor (RMS relative error ~1e-4).
  * Workspace: the Jacobian columns, 3 (P + n_atoms) of them for P neighbour pairs, each of
- * D padded to 64 halves (MIXED) or D doubles (FP64), plus 24 (MIXED) or 40 (FP64) bytes
- * each, and n_atoms x M weights.  Synchronises `stream`; SOAPGAP_E_STATE without a model,
+ * D + 2 padded to 64 halves (MIXED) or D doubles (FP64), plus 24 (MIXED) or 40 (FP64)
+ * bytes each, and n_atoms x M weights.  Synchronises `stream`; SOAPGAP_E_STATE without a model,
  * SOAPGAP_E_UNSUPPORTED if the descriptor is too large for the Jacobian kernel's shared
  * memory or the column count exceeds 2^31. */
 int soapgap_design(soapgap_handle* h, const soapgap_batch* batch, uint32_t flags, void* k_atom,

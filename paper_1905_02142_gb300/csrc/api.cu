@@ -91,7 +91,7 @@ struct soapgap_handle {
   Buf qs, alpha;
   bool has_model = false;
   // tensor-core GAP operands of the sparse set (mixed path)
-  Buf tc_B, tc_BT, tc_cols, tc_qbar;
+  Buf tc_B, tc_BT, tc_cols, tc_qbar, tc_Ad;
   GapTcModel tcm{};
   Buf A16, nrm, uq, r_part, kp16;
   // workspace
@@ -345,6 +345,20 @@ extern "C" int soapgap_set_model(soapgap_handle* h, const double* q_sparse, cons
     CK(h, cudaMemcpy(h->tc_BT.p, BT.data(), BT.size() * sizeof(__half), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->tc_cols.p, cols.data(), cols.size() * sizeof(float), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->tc_qbar.p, qb.data(), qb.size() * sizeof(float), cudaMemcpyHostToDevice));
+    // force-row operand: centred sparse rows scaled by a power of two, two unit columns
+    const int dpd = (D + 2 + 63) / 64 * 64;
+    double dmax = 0.0;
+    for (int s = 0; s < m; ++s)
+      for (int k = 0; k < D; ++k) dmax = std::max(dmax, std::fabs(q_sparse[(size_t)s * D + k] - qbar[k]));
+    const double kd = dmax > 0 ? std::ldexp(1.0, -std::ilogb(dmax)) : 1.0;
+    std::vector<__half> Ad((size_t)mp * dpd, __float2half_rn(0.f));
+    for (int s = 0; s < m; ++s) {
+      __half* row = Ad.data() + (size_t)s * dpd;
+      for (int k = 0; k < D; ++k) row[k] = __float2half_rn((float)(kd * (q_sparse[(size_t)s * D + k] - qbar[k])));
+      row[D] = row[D + 1] = __float2half_rn((float)kd);
+    }
+    CK(h, ensure(h->tc_Ad, Ad.size() * sizeof(__half)));
+    CK(h, cudaMemcpy(h->tc_Ad.p, Ad.data(), Ad.size() * sizeof(__half), cudaMemcpyHostToDevice));
     GapTcModel& t = h->tcm;
     t.d = D;
     t.dp = dp;
@@ -357,6 +371,9 @@ extern "C" int soapgap_set_model(soapgap_handle* h, const double* q_sparse, cons
     t.BT = (const __half*)h->tc_BT.p;
     t.col = (const float4*)h->tc_cols.p;
     t.qbar = (const float*)h->tc_qbar.p;
+    t.dpd = dpd;
+    t.kd = (float)kd;
+    t.Ad = (const __half*)h->tc_Ad.p;
   } else {
     CK(h, cudaMemcpy(h->qs.p, q_sparse, nq * es, cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->alpha.p, alpha, (size_t)m * es, cudaMemcpyHostToDevice));
@@ -978,7 +995,7 @@ extern "C" const char* soapgap_last_error(const soapgap_handle* h) {
 
 extern "C" void soapgap_destroy(soapgap_handle* h) {
   if (!h) return;
-  Buf* bufs[] = {&h->tc_B, &h->tc_BT, &h->tc_cols, &h->tc_qbar, &h->A16, &h->nrm, &h->uq,
+  Buf* bufs[] = {&h->tc_B, &h->tc_BT, &h->tc_cols, &h->tc_qbar, &h->tc_Ad, &h->A16, &h->nrm, &h->uq,
                  &h->r_part, &h->kp16, &h->table, &h->qs, &h->alpha, &h->geom, &h->atom_offs, &h->atom_struct,
                  &h->atom_bin, &h->atom_bin4, &h->atom_slot, &h->bin_count, &h->bin_start, &h->bin_atoms,
                  &h->binpos, &h->atom_hi, &h->atom_lo, &h->seg_count, &h->seg_offs, &h->scan_tmp, &h->key_tmp,
@@ -1155,7 +1172,7 @@ static int design(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, voi
     const long long ncols = 3 * (P + N);
     if (ncols > 0x7fffffffLL - 256)
       return fail(h, SOAPGAP_E_UNSUPPORTED, "too many Jacobian columns (3 (pairs + atoms) >= 2^31): split the batch");
-    const int ld = h->mixed ? h->tcm.dp : D;
+    const int ld = h->mixed ? h->tcm.dpd : D;
     ENS(h, h->dk_J, (size_t)ncols * ld * (h->mixed ? sizeof(__half) : sizeof(double)));
     ENS(h, h->dk_at, sizeof(int2) * (size_t)ncols);
     ENS(h, h->dk_v, sizeof(Vec4<T>) * (size_t)ncols);

@@ -17,6 +17,13 @@
 // the sparse rows against all columns then applies the owner's weights and sums each
 // target's columns in its epilogue (gap_tc.cu for the mixed path, dgemm_nt_kernel here).
 //
+// Mixed path: since (q_s - S q_o) . J = q_s . J' with J' = J - q_o (q_o . J) (the part of J
+// orthogonal to q_o), the columns are projected in FP32 before they are rounded, and stored
+// as FP16 [2^e J' | hi, lo of 2^e qbar . J'] with one power of two per column triple.  The
+// sparse operand is [kd (q_s - qbar) | kd | kd], so the tensor cores return kd 2^e q_s . J'
+// with the large common part qbar . J' carried exactly; the epilogue only scales by
+// w_os 2^-e / kd.  FP64 path: unprojected columns and (w, w S) weights on q_s . J and q_o . J.
+//
 // Per pair, with c_(ch, lm) += b_n(r) A_lm(r_vec), A_lm = 4 pi ilexp_l Y_lm (Sec. II), for
 // the channels ch = (species(j), n) of the pair's block:
 //   X[c][l] = sum_m A_lm c_(c, lm),     Z[c][l] = sum_m grad A_lm c_(c, lm)
@@ -105,6 +112,7 @@ design_jacobian_kernel(const JacArgs<T> a, int per_warp) {
     for (int d = threadIdx.x; d < D; d += blockDim.x) qbar_s[d] = a.qbar[d];
   __syncthreads();
 
+  T qmx = 0, qbq = 0;  // per owner atom: max |q_o| and qbar . q_o (set in the atom loop)
   // per-lane partials over the lane's entries of src[3][D]: max |J|, q_owner.J, qbar.J
   auto partials = [&](const T* src, T* mx, T* tq, T* tb) {
 #pragma unroll
@@ -131,28 +139,46 @@ design_jacobian_kernel(const JacArgs<T> a, int per_warp) {
     }
     T inv_scale[3] = {T(1), T(1), T(1)};
     if constexpr (TABLE) {
-      // the three columns are contiguous rows of ld halves: 16-byte pieces over all lanes
-      float sc[3];
+      // Projected columns J' = J - q_o (q_o . J) (the force row then needs q_s . J' only,
+      // since (q_s - S q_o) . J = q_s . J'), followed by hi and lo of qbar . J' (the sparse
+      // operand carries two unit columns there).  One power-of-two scale per triple, from
+      // a bound on |J'| = |J - q_o t| <= max |J| + max |q_o| |t| and on |qbar . J'|.
+      float sc = 1.f, tbp[3];
+      {
+        float big = 0.f;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const int e = mx[c] > T(0) ? 14 - ilogbf((float)mx[c]) : 0;
-        sc[c] = ldexpf(1.f, e);
-        inv_scale[c] = (T)ldexpf(1.f, -e);
-      }
-      const int c8 = a.ld / 8;
-      __half* rows = reinterpret_cast<__half*>(a.J) + (size_t)col0 * a.ld;
-      for (int q = lane; q < 3 * c8; q += 32) {
-        const int c = (q >= c8) + (q >= 2 * c8);
-        const int k8 = (q - c * c8) * 8;
-        const float scc = c == 0 ? sc[0] : (c == 1 ? sc[1] : sc[2]);
-        const T* sp = src + c * D;
-        __align__(16) __half h8[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int d = k8 + t;
-          h8[t] = __float2half_rn(d < D ? (float)sp[d] * scc : 0.f);
+        for (int c = 0; c < 3; ++c) {
+          tbp[c] = (float)(tb[c] - qbq * tq[c]);
+          big = fmaxf(big, fmaxf((float)(mx[c] + qmx * abs(tq[c])), fabsf(tbp[c])));
         }
-        *reinterpret_cast<uint4*>(rows + (size_t)q * 8) = *reinterpret_cast<const uint4*>(h8);
+        const int e = big > 0.f ? 14 - ilogbf(big) : 0;
+        sc = ldexpf(1.f, e);
+        inv_scale[0] = inv_scale[1] = inv_scale[2] = (T)ldexpf(1.f, -e);
+      }
+      // consecutive lanes write consecutive half2 (shared-memory reads without bank conflicts)
+      const int h2 = a.ld / 2;
+      __half2* rows = reinterpret_cast<__half2*>(reinterpret_cast<__half*>(a.J) + (size_t)col0 * a.ld);
+      for (int q = lane; q < 3 * h2; q += 32) {
+        const int c = (q >= h2) + (q >= 2 * h2);
+        const int d = (q - c * h2) * 2;
+        const float tcs = (float)(c == 0 ? tq[0] : (c == 1 ? tq[1] : tq[2])) * sc;
+        const T* sp = src + c * D;
+        __half hv[2];
+        if (d + 1 < D) {
+          hv[0] = __float2half_rn(fmaf(-(float)qi[d], tcs, (float)sp[d] * sc));
+          hv[1] = __float2half_rn(fmaf(-(float)qi[d + 1], tcs, (float)sp[d + 1] * sc));
+        } else {
+          const float xb = (c == 0 ? tbp[0] : (c == 1 ? tbp[1] : tbp[2])) * sc;
+          const __half xh = __float2half_rn(xb);
+          const __half xl = __float2half_rn(xb - __half2float(xh));
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+            const int dd = d + t;
+            hv[t] = dd < D ? __float2half_rn(fmaf(-(float)qi[dd], tcs, (float)sp[dd] * sc))
+                           : (dd == D ? xh : (dd == D + 1 ? xl : __float2half_rn(0.f)));
+          }
+        }
+        rows[q] = __halves2half2(hv[0], hv[1]);
       }
     } else {
       double* rows = reinterpret_cast<double*>(a.J) + (size_t)col0 * a.ld;
@@ -178,10 +204,17 @@ design_jacobian_kernel(const JacArgs<T> a, int per_warp) {
     const T* ci = a.c + (size_t)atom * nch * L;
     for (int k = lane; k < nch * L; k += 32) cs[k] = ci[k];
     const T* qrow = a.q + (size_t)atom * D;
+    qmx = 0;
+    qbq = 0;
     for (int d = lane; d < D; d += 32) {
-      qi[d] = qrow[d];
+      const T qv = qrow[d];
+      qi[d] = qv;
+      qmx = max(qmx, abs(qv));
+      if (TABLE) qbq = fma((T)qbar_s[d], qv, qbq);
       Jacc[d] = Jacc[D + d] = Jacc[2 * D + d] = T(0);
     }
+    qmx = warp_max(qmx);
+    qbq = warp_sum(qbq);
     __syncwarp();
     for (int sj = 0; sj < nsp; ++sj) {
       const int beg = a.seg_offs[atom * nsp + sj], end = a.seg_offs[atom * nsp + sj + 1];

@@ -265,20 +265,22 @@ struct EpiKernelRows {
   __device__ void end(int, int) {}
 };
 
-// Force rows of the fitting matrices: rows = sparse environments s, columns = descriptor
-// Jacobian columns ordered by target atom (see design.cu).  Per column (owner o, target t,
-// component a = col mod 3) the contribution is
-//   w_os (qbar.J + n_s 2^-e u_s.J) - (w S)_os q_o.J,
-// u_s.J from the tensor cores on the column scaled by 2^e; the running sums of one target
-// are added to dk[t][a][s] when the target changes (a target's columns are contiguous).
+// Force rows of the fitting matrices: rows = sparse environments s, columns = projected
+// descriptor Jacobian columns J' (see design.cu) ordered by target atom.  With the sparse
+// operand [kd (q_s - qbar) | kd | kd] and the column [2^e J' | hi | lo of 2^e qbar.J'], the
+// accumulator is kd 2^e q_s.J', and the contribution of a column (owner o, target t,
+// component a = col mod 3) is w_os 2^-e / kd times it.  The running sums of one target are
+// added to dk[t][a][s] when the target changes (a target's columns are contiguous).
+// Tiles of 192 columns are read 24 at a time, so every chunk starts at a column triple (the
+// three components of one pair or self slot: one owner, one target, one scale).
 struct EpiDesignGrad {
+  static constexpr int CHUNK = 24;
   int m, ldw, ncols;
-  const float4* scol;                // [Mp] .y = n_s
+  float inv_kd;
   const int2* col_at;                // [ncols] (owner, target)
-  const float4* col_v;               // [ncols] (qbar.J, q_owner.J, 2^-e, 0)
-  const float2* wv;                  // [N][ldw]
+  const float4* col_v;               // [ncols] .z = 2^-e of the column's triple
+  const float2* wv;                  // [N][ldw] .x = w_os
   float* dk;                         // [N][3][m]
-  float ns;
   int target;
   float acc0, acc1, acc2;
   __device__ void flush(int row) {
@@ -290,35 +292,32 @@ struct EpiDesignGrad {
     }
     acc0 = acc1 = acc2 = 0.f;
   }
-  __device__ void begin(int row) {
-    ns = row < m ? scol[row].y : 0.f;
+  __device__ void begin(int) {
     target = -1;
     acc0 = acc1 = acc2 = 0.f;
   }
-  // Tiles of 192 columns read 24 at a time, so every chunk starts at a column triple
-  // (the three components of one pair or self slot: one owner, one target).  Lane j < 24
-  // reads the record of column col0 + j (coalesced) and the records reach every lane by
-  // shuffles; the 8 owners' weights at this row are requested before the first use, so
-  // their latencies overlap.  All lanes take part (rows past m compute but do not write).
-  static constexpr int CHUNK = 24;
+  // Lane 3t reads the record of triple t (coalesced); owner, target and scale reach every
+  // lane by shuffles, and the 8 owners' weights at this row are requested before the first
+  // use.  All lanes take part (rows past m compute but do not write).
   __device__ void apply(int row, int col0, const uint32_t* v) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const bool live = row < m;
     const int mine = col0 + lane;
     int2 at_l = make_int2(-1, -1);
-    float4 cv_l = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (lane < CHUNK && mine < ncols) {
+    float cz_l = 0.f;
+    if (lane < CHUNK && lane % 3 == 0 && mine < ncols) {
       at_l = __ldg(col_at + mine);
-      cv_l = __ldg(col_v + mine);
+      cz_l = __ldg(&col_v[mine].z);
     }
-    float2 w[CHUNK / 3];
+    float wk[CHUNK / 3];
     int tg[CHUNK / 3];
 #pragma unroll
     for (int t = 0; t < CHUNK / 3; ++t) {
       const int o = __shfl_sync(FULL, at_l.x, 3 * t);
+      const float cz = __shfl_sync(FULL, cz_l, 3 * t);
       tg[t] = __shfl_sync(FULL, at_l.y, 3 * t);
-      w[t] = (live && o >= 0) ? __ldg(wv + (size_t)o * ldw + row) : make_float2(0.f, 0.f);
+      wk[t] = (live && o >= 0) ? __ldg(&wv[(size_t)o * ldw + row].x) * (cz * inv_kd) : 0.f;
     }
 #pragma unroll
     for (int t = 0; t < CHUNK / 3; ++t) {
@@ -327,18 +326,9 @@ struct EpiDesignGrad {
         if (live) flush(row);
         target = tg[t];
       }
-      float val[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const int j = 3 * t + a;
-        const float cx = __shfl_sync(FULL, cv_l.x, j);
-        const float cy = __shfl_sync(FULL, cv_l.y, j);
-        const float cz = __shfl_sync(FULL, cv_l.z, j);
-        val[a] = fmaf(w[t].x, fmaf(ns * cz, __uint_as_float(v[j]), cx), -w[t].y * cy);
-      }
-      acc0 += val[0];
-      acc1 += val[1];
-      acc2 += val[2];
+      acc0 = fmaf(wk[t], __uint_as_float(v[3 * t]), acc0);
+      acc1 = fmaf(wk[t], __uint_as_float(v[3 * t + 1]), acc1);
+      acc2 = fmaf(wk[t], __uint_as_float(v[3 * t + 2]), acc2);
     }
   }
   __device__ void end(int row, int) {
@@ -672,11 +662,11 @@ cudaError_t sg_tc_design_grad(const GapTcModel& md, int m, const __half* J, long
   e.m = m;
   e.ldw = md.mp;
   e.ncols = (int)ncols;
-  e.scol = md.col;
+  e.inv_kd = 1.f / md.kd;
   e.col_at = col_at;
   e.col_v = col_v;
   e.wv = wv;
   e.dk = dk;
-  // A = the unit centred sparse rows (the hi third of each row of B), K = dp
-  return launch_gemm<192, 5, 16, true>(md.B, md.mp, J, (int)ncols, md.dp, e, err, st, 3 * md.dp);
+  // A = the scaled centred sparse rows with their two unit columns, K = dpd
+  return launch_gemm<192, 5, 16, true>(md.Ad, md.mp, J, (int)ncols, md.dpd, e, err, st);
 }

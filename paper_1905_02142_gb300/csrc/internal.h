@@ -157,6 +157,11 @@ struct GapTcModel {
   const float4* col;      // [mp]: (qbar.qbar + qbar.(q_s - qbar), |q_s - qbar|, alpha_s,
                           //        zeta alpha_s |q_s - qbar| / kappa), zero beyond M
   const float* qbar;      // [dp]
+  // force rows of the fitting matrices: A = [kd (q_s - qbar) | kd | kd | 0 ...] per sparse
+  // row, so that A . [J' | hi(qbar.J') | lo(qbar.J')] = kd q_s . J' (see design.cu)
+  int dpd;                // D + 2 padded to 64
+  float kd;               // power of two: max |kd (q_s - qbar)| in [1, 2)
+  const __half* Ad;       // [mp][dpd]
 };
 int sg_gap_tc_tiles(int m);
 cudaError_t sg_gap_tc_prepare(const float* q, int n, int d, int dp, const float* qbar, __half* A,
@@ -217,10 +222,11 @@ template <typename T> struct JacArgs {
   BasisConst<T> bc;
   const T* c;               // [N][nch][L]
   const T* q;               // [N][D]
-  const float* qbar;        // [D] sparse-set mean (table path: centring of the products)
-  void* J;                  // [ncols][ld]: __half scaled by a power of two per column, or double
+  const float* qbar;        // [D] sparse-set mean (table path)
+  void* J;                  // [ncols][ld]: table path __half [2^e J' | hi, lo of 2^e qbar.J' | 0],
+                            // J' = J - q_owner (q_owner . J), one e per column triple; FP64 path J
   int2* col_at;             // [ncols] (owner atom, target atom)
-  Vec4<T>* col_v;           // [ncols] (qbar . J, q_owner . J, 1/scale, 0)
+  Vec4<T>* col_v;           // [ncols] (qbar . J, q_owner . J, 2^-e, 0), unprojected J
 };
 template <typename T> cudaError_t sg_design_jacobian(const JacArgs<T>& a, int cls, bool table,
                                                      cudaStream_t st);
