@@ -377,7 +377,7 @@ def run_design(args, dev, flush, stream):
     n, ns, msp = bb.n_atoms, bb.n_struct, wb.n_sparse
     n_pairs = m.pair_count()
     d = wb.n_max * (wb.n_max + 1) // 2 * (wb.l_max + 1)
-    dp = (d + 63) // 64 * 64
+    dp = (d + 2 + 63) // 64 * 64  # stored column length: D entries, two carried terms, padding
     mp = (msp + 255) // 256 * 256
     ncols = 3 * (n_pairs + n)
     ms = float(np.mean(times))
