@@ -112,6 +112,36 @@ def test_design_rows_match_oracle(case, precision, oracle_rows):
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_design_edge_cases(precision):
+    """An empty structure, an isolated atom (no neighbour, no image within r_cut) and a
+    small box in one batch, with a non-integer zeta (the clamped power of Sec. I)."""
+    from paper_1905_02142_gb300.api import SoapGap
+    batch = synth.concat([synth.random_box(0, side=9.0, seed=1), synth.random_box(1, side=20.0, seed=2),
+                          synth.random_box(12, side=5.0, dmin=1.2, seed=3)])
+    w = synth.get_workload("box64_n6l6")
+    P = Params.from_dict(w.params())
+    W = oracle_W(P.n_max, P.r_cut, P.sigma_r0)
+    P_, qs, al, _ = sparse_model("box64_n6l6", 8)
+    zeta = 2.5
+    model = SoapGap.from_dict(params_dict(P), precision=precision)
+    model.set_model(qs, al, zeta)
+    out = model.design(structures(batch), k_atom=True, k_struct=True, dk=True)
+    q = soap.descriptors(batch, P, W=W)["q"]
+    k_ref = gap.kernel_matrix(q, qs, zeta).numpy()
+    ks_ref = gap.structure_rows(k_ref, batch.atom_offs).numpy()
+    dk_ref = gap.kernel_gradients(batch, P, qs, zeta, W=W)
+    k = out["k_atom"].double().cpu().numpy()
+    ks = out["k_struct"].cpu().numpy()
+    dk = out["dk"].double().cpu().numpy()
+    tol = TOL[precision]
+    assert np.all(ks[0] == 0.0)                      # the empty structure
+    assert np.all(dk[0] == 0.0)                      # the isolated atom does not move anything
+    assert np.abs(k - k_ref).max() < tol["k"]
+    assert np.max(np.abs(ks[1:] - ks_ref[1:]) / np.abs(ks_ref[1:])) < tol["ks"]
+    assert rel_all(dk, dk_ref) < tol["dk"]
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_sparse_block(precision):
     model, P, qs, al, zeta = make("box64_n6l6", 32, precision)
     kmm = model.kernel_rows(torch.as_tensor(qs, device="cuda")).double().cpu().numpy()
