@@ -627,7 +627,7 @@ cudaError_t sg_gap_tc_backward(const GapTcModel& md, const __half* kp, const flo
   e.qbar = md.qbar;
   e.r_part = r_part;
   e.g = g;
-  return launch_gemm<128, 6, 4>(kp, n, md.BT, md.dp, md.mp, e, err, st);
+  return launch_gemm<224, 5, 4>(kp, n, md.BT, md.dp, md.mp, e, err, st);
 }
 
 cudaError_t sg_tc_gemm_store(const __half* A, int m, const __half* B, int nn, int k, float* C, int* err,
