@@ -116,6 +116,25 @@ class ClockSampler:
                 "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
 
 
+# --------------------------------------------------------------------------- ranks
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest value of x over all ranks (the job's time is its slowest rank's)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t)
+
+
+def whole_job_rate(units_per_rank: float, seconds: float, world: int, device):
+    """Units per second of the whole job: every rank processes its own units (replicas, weak
+    scaling), the job ends with its slowest rank.  Returns (rate, slowest seconds)."""
+    t = max_over_ranks(seconds, world, device)
+    return world * units_per_rank / t, t
+
+
 # --------------------------------------------------------------------------- model set-up
 def sparse_set_from_library(model_cls, w, params, device):
     """Sparse-set descriptors of the workload's separate box, computed by the library."""
@@ -494,10 +513,7 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     clocks = clk.summary()
     t_sum = sum(times) / 1e3
-    t_local = torch.tensor([t_sum], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    t_max = float(t_local)
+    t_max = max_over_ranks(t_sum, world, dev)
     n_pairs = model.pair_count()
     stages = {k: v / args.steps for k, v in stage_acc.items()}
 
@@ -511,13 +527,14 @@ def run_ours(args, rank, world, local_rank):
                            forces=True, virial=True)
         if k >= args.warmup:
             e2e_times.append(time.perf_counter() - t0)
-    e2e_t = float(np.mean(e2e_times))
+    e2e_t = max_over_ranks(float(np.mean(e2e_times)), world, dev)
     n = batch.n_atoms
     h2d = n * (3 * 8 + 4)
     d2h = n * 4 + batch.n_struct * 8 + n * 24 + batch.n_struct * 72
 
     # the same step replayed from a captured CUDA graph (asynchronous library calls)
     graph = timed_graph(model, s, flush, stream, args.warmup, args.steps)
+    graph["ms_per_step"] = max_over_ranks(graph["ms_per_step"], world, dev)
     graph["value"] = world * n / (graph["ms_per_step"] / 1e3)
 
     # FP64 path on the same workload
@@ -588,7 +605,7 @@ def run_ours(args, rank, world, local_rank):
         "fp64_path": fp64,
         "roofline": roofline,
         "cpu_baseline": cpu,
-        "e2e": {"value": n / e2e_t, "unit": "atoms/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": world * n / e2e_t, "unit": "atoms/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clocks,
