@@ -621,7 +621,7 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     // the list is built from the positions mapped into their cells (identical for atoms
     // already inside)
     CK(h, sg_nbr_wrap(b->pos, N, nb, (double*)h->pos_w.p, (int4*)h->img.p, st));
-    CK(h, sg_nbr_bin((const double*)h->pos_w.p, N, h->n_bins, nb, st));
+    CK(h, sg_nbr_bin((const double*)h->pos_w.p, b->species, N, h->n_bins, nb, st));
     for (int attempt = 0; attempt < 2; ++attempt) {
       ENS(h, h->key_tmp, 8 * N1n * (size_t)maxn);
       nb.key_tmp = (unsigned long long*)h->key_tmp.p;
@@ -836,7 +836,8 @@ static int check_batch(soapgap_handle* h, const soapgap_batch* b) {
   for (int s = 0; s < b->n_struct; ++s)
     if (b->atom_offs_host[s + 1] < b->atom_offs_host[s]) return fail(h, SOAPGAP_E_INVALID_ARG, "atom_offs_host must be nondecreasing");
   if (b->n_atoms > 0 && (!b->pos || !b->species)) return fail(h, SOAPGAP_E_INVALID_ARG, "pos and species are required");
-  if ((long long)b->n_atoms * h->prm.n_species >= (1LL << 30)) return fail(h, SOAPGAP_E_UNSUPPORTED, "too many atoms");
+  if ((long long)b->n_atoms * h->prm.n_species >= (1LL << 30) || b->n_atoms >= (1 << 28))
+    return fail(h, SOAPGAP_E_UNSUPPORTED, "too many atoms");
   return SOAPGAP_OK;
 }
 

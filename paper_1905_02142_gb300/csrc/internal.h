@@ -87,7 +87,7 @@ cudaError_t sg_exclusive_scan(const int* in, int* out, int n, int* tmp, cudaStre
 // fractional coordinates (n = 0, pos_w = x exactly, for atoms inside up to 1e-9), img = n
 cudaError_t sg_nbr_wrap(const double* pos, int n_atoms, const NbrBuffers& b, double* pos_w,
                         int4* img, cudaStream_t st);
-cudaError_t sg_nbr_bin(const double* pos, int n_atoms, int n_bins, const NbrBuffers& b,
+cudaError_t sg_nbr_bin(const double* pos, const int* species, int n_atoms, int n_bins, const NbrBuffers& b,
                        cudaStream_t st);
 // one sweep over the candidates: per-atom slot arrays of keys (capacity maxn), counts per
 // (atom, species) segment, their exclusive scan into seg_offs, and the largest count

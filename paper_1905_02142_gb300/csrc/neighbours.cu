@@ -130,7 +130,10 @@ __global__ void bin_assign(const double* __restrict__ pos, int n, NbrBuffers b) 
   b.atom_slot[i] = atomicAdd(&b.bin_count[id], 1);
 }
 
-__global__ void bin_fill(const double* __restrict__ pos, int n, NbrBuffers b, float4* binpos) {
+// binpos[.].w packs the atom index (bits 0..27) and its species (bits 28..30), so the
+// candidate sweep needs no second dependent load for the species of a kept neighbour
+__global__ void bin_fill(const double* __restrict__ pos, const int* __restrict__ species, int n, NbrBuffers b,
+                         float4* binpos) {
   if (b.run && *b.run == 0) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -139,7 +142,7 @@ __global__ void bin_fill(const double* __restrict__ pos, int n, NbrBuffers b, fl
   const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
   const float xh = (float)x, yh = (float)y, zh = (float)z;
   const float4 lo = make_float4((float)(x - (double)xh), (float)(y - (double)yh), (float)(z - (double)zh), 0.f);
-  binpos[at] = make_float4(xh, yh, zh, __int_as_float(i));
+  binpos[at] = make_float4(xh, yh, zh, __int_as_float(i | (species[i] << 28)));
   b.atom_hi[i] = make_float4(xh, yh, zh, 0.f);
   b.atom_lo[i] = lo;
 }
@@ -187,7 +190,7 @@ cudaError_t sg_nbr_wrap(const double* pos, int n_atoms, const NbrBuffers& b, dou
   return cudaGetLastError();
 }
 
-cudaError_t sg_nbr_bin(const double* pos, int n_atoms, int n_bins, const NbrBuffers& b,
+cudaError_t sg_nbr_bin(const double* pos, const int* species, int n_atoms, int n_bins, const NbrBuffers& b,
                        cudaStream_t st) {
   cudaMemsetAsync(b.bin_count, 0, sizeof(int) * (size_t)n_bins, st);
   if (n_atoms > 0) {
@@ -197,7 +200,7 @@ cudaError_t sg_nbr_bin(const double* pos, int n_atoms, int n_bins, const NbrBuff
   cudaError_t e = sg_exclusive_scan(b.bin_count, b.bin_start, n_bins, b.scan_tmp, st, b.run);
   if (e != cudaSuccess) return e;
   if (n_atoms > 0) {
-    bin_fill<<<(n_atoms + 255) / 256, 256, 0, st>>>(pos, n_atoms, b, b.binpos);
+    bin_fill<<<(n_atoms + 255) / 256, 256, 0, st>>>(pos, species, n_atoms, b, b.binpos);
     ++sg_kernel_launches;
   }
   return cudaGetLastError();
@@ -303,11 +306,13 @@ __device__ __forceinline__ void visit_pairs(const double* __restrict__ pos, cons
         bool have_s = false;
         for (int base = beg; base < end; base += 32) {
           const int k = base + lane;
-          int j = -1;
+          int j = -1, sj = 0;
           bool cand = false, exact = false;
           if (k < end) {
             const float4 pj = binpos[k];
-            j = __float_as_int(pj.w);
+            const int w = __float_as_int(pj.w);
+            j = w & 0x0FFFFFFF;
+            sj = w >> 28;
             if (!(j == i && zero_shift)) {
               // explicit round-to-nearest ops: the count and fill kernels decide alike
               const float dx = __fsub_rn(__fadd_rn(pj.x, sx), xi);
@@ -341,7 +346,7 @@ __device__ __forceinline__ void visit_pairs(const double* __restrict__ pos, cons
               keep = true;  // exact value computed on demand by the caller
             }
           }
-          fn(keep, j, k, S1, S2, S3, f1, f2, f3, s, r, d2);
+          fn(keep, j, sj, S1, S2, S3, f1, f2, f3, s, r, d2);
         }
       }
     }
@@ -360,14 +365,12 @@ struct FillSlots {
   int lane, maxn;
   int* cnt;                      // running slot count (warp-uniform)
   int* percnt;                   // per-lane counts by species [SG_MAX_SPECIES]
-  const int* species;
   unsigned long long* slots;     // this atom's maxn slots
   int* err;
-  __device__ void operator()(bool keep, int j, int, int S1, int S2, int S3, float, float, float,
+  __device__ void operator()(bool keep, int j, int sj, int S1, int S2, int S3, float, float, float,
                              const double*, const double*, double) const {
     const unsigned mask = __ballot_sync(0xffffffffu, keep);
     if (keep) {
-      const int sj = species[j];
 #pragma unroll
       for (int s = 0; s < SG_MAX_SPECIES; ++s) percnt[s] += (s == sj);
       const int at = *cnt + __popc(mask & ((1u << lane) - 1u));
@@ -391,7 +394,7 @@ __global__ void fill_slots_kernel(const double* __restrict__ pos, const int* __r
 #pragma unroll
   for (int s = 0; s < SG_MAX_SPECIES; ++s) percnt[s] = 0;
   visit_pairs(pos, binpos, i, rc, b,
-              FillSlots{lane, maxn, &cnt, percnt, species, b.key_tmp + (size_t)i * maxn, b.err});
+              FillSlots{lane, maxn, &cnt, percnt, b.key_tmp + (size_t)i * maxn, b.err});
   for (int s = 0; s < nsp; ++s) {
     const int v = warp_sum(percnt[s]);
     if (lane == 0) b.seg_count[i * nsp + s] = v;
