@@ -304,10 +304,11 @@ __device__ __forceinline__ void visit_pairs(const double* __restrict__ pos, cons
         const bool lexpos = lex_positive(S1, S2, S3);
         double s[3] = {0.0, 0.0, 0.0};
         bool have_s = false;
-        for (int base = beg; base < end; base += 32) {
-          const int k = base + lane;
-          int j = -1, sj = 0;
-          bool cand = false, exact = false;
+        // two candidates per lane and step: both position loads are in flight together
+        auto test = [&](int k, int& j, int& sj, bool& cand, bool& exact) {
+          j = -1;
+          sj = 0;
+          cand = exact = false;
           if (k < end) {
             const float4 pj = binpos[k];
             const int w = __float_as_int(pj.w);
@@ -323,17 +324,8 @@ __device__ __forceinline__ void visit_pairs(const double* __restrict__ pos, cons
               cand = exact || d2f < rc2f;
             }
           }
-          if (!have_s && __any_sync(0xffffffffu, exact || (cand && Fn::kNeedsShift))) {
-            if (lane == 0) {
-#pragma unroll
-              for (int c = 0; c < 3; ++c)
-                s[c] = __dadd_rn(__dadd_rn(__dmul_rn((double)S1, g.h[c]), __dmul_rn((double)S2, g.h[3 + c])),
-                                 __dmul_rn((double)S3, g.h[6 + c]));
-            }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) s[c] = __shfl_sync(0xffffffffu, s[c], 0);
-            have_s = true;
-          }
+        };
+        auto decide = [&](int j, int sj, bool cand, bool exact) {
           bool keep = false;
           double r[3] = {0, 0, 0}, d2 = -1.0;
           if (cand) {
@@ -347,6 +339,25 @@ __device__ __forceinline__ void visit_pairs(const double* __restrict__ pos, cons
             }
           }
           fn(keep, j, sj, S1, S2, S3, f1, f2, f3, s, r, d2);
+        };
+        for (int base = beg; base < end; base += 64) {
+          int ja, sja, jb, sjb;
+          bool ca, ea, cb, eb;
+          test(base + lane, ja, sja, ca, ea);
+          test(base + 32 + lane, jb, sjb, cb, eb);
+          if (!have_s && __any_sync(0xffffffffu, ea || eb || ((ca || cb) && Fn::kNeedsShift))) {
+            if (lane == 0) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c)
+                s[c] = __dadd_rn(__dadd_rn(__dmul_rn((double)S1, g.h[c]), __dmul_rn((double)S2, g.h[3 + c])),
+                                 __dmul_rn((double)S3, g.h[6 + c]));
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) s[c] = __shfl_sync(0xffffffffu, s[c], 0);
+            have_s = true;
+          }
+          decide(ja, sja, ca, ea);
+          if (base + 32 < end) decide(jb, sjb, cb, eb);
         }
       }
     }
