@@ -57,8 +57,10 @@ template <int NC, int LC>
 int jac_per_warp(int nsp, int nmax, int lmax, int dim) {
   constexpr int NP = (NC + 3) / 4 * 4, LP = (LC + 1 + 3) / 4 * 4;
   const int L = (lmax + 1) * (lmax + 1), nch = nsp * nmax, lp1 = lmax + 1;
-  const int jt = std::max(4 * L, 3 * dim);
-  const int n = 4 * nch * lp1 + 4 * JB + nch * L + dim + (jt + 3) / 4 * 4 + 3 * dim + JB * (2 * NP + 2 * LP) + 2 * JB;
+  const int dpad = (dim + 7) / 8 * 8;  // row stride of the [3][D] arrays (16-byte aligned rows)
+  const int jt = std::max(4 * L, 3 * dpad);
+  const int n = 4 * nch * lp1 + 4 * JB + (jt + 3) / 4 * 4 + (nch * L + 3) / 4 * 4 + dpad + 3 * dpad +
+                JB * (2 * NP + 2 * LP) + 2 * JB;
   return (n + 3) / 4 * 4;
 }
 
@@ -84,15 +86,16 @@ design_jacobian_kernel(const JacArgs<T> a, int per_warp) {
   off += al32(sizeof(float) * (TABLE ? D : 1));
   T* wbase = reinterpret_cast<T*>(smem_raw + off) + (size_t)warp * per_warp;
   constexpr int RW = 2 * NP + 2 * LP;                // radial record of one pair
-  const int jt = (max(4 * L, 3 * D) + 3) / 4 * 4;
+  const int Dp = (D + 7) / 8 * 8;  // row stride of the [3][D] arrays (16-byte aligned rows)
+  const int jt = (max(4 * L, 3 * Dp) + 3) / 4 * 4;
   Vec4<T>* XZ = reinterpret_cast<Vec4<T>*>(wbase);  // [nch][lp1]  X, Z
   Vec4<T>* geo = XZ + nch * lp1;                     // [JB]  rhat, 1/r (< 0: masked pair)
-  T* Jt = reinterpret_cast<T*>(geo + JB);            // [3][D]  J of the current pair, and before
+  T* Jt = reinterpret_cast<T*>(geo + JB);            // [3][Dp] J of the current pair, and before
   Vec4<T>* Aw = reinterpret_cast<Vec4<T>*>(Jt);      //   it [L] A_lm, grad A_lm (used up by X, Z)
   T* cs = Jt + jt;                                   // [nch][L]  c of the owner
-  T* qi = cs + nch * L;                              // [D]     q of the owner
-  T* Jacc = qi + D;                                  // [3][D]  -sum of J (self columns)
-  T* rad = Jacc + 3 * D;                             // [JB][RW] b_n, b_n', A_l, A_l' per pair
+  T* qi = cs + (nch * L + 3) / 4 * 4;                // [D]     q of the owner
+  T* Jacc = qi + Dp;                                 // [3][Dp] -sum of J (self columns)
+  T* rad = Jacc + 3 * Dp;                            // [JB][RW] b_n, b_n', A_l, A_l' per pair
   int* pinfo = reinterpret_cast<int*>(rad + JB * RW);  // [JB][2] first column, neighbour
   const T SQRT2 = (T)1.4142135623730951;
 
@@ -122,7 +125,7 @@ design_jacobian_kernel(const JacArgs<T> a, int per_warp) {
       const T qb = TABLE ? (T)qbar_s[d] : T(0);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const T v = src[c * D + d];
+        const T v = src[c * Dp + d];
         mx[c] = max(mx[c], abs(v));
         tq[c] = fma(qv, v, tq[c]);
         tb[c] = fma(qb, v, tb[c]);
@@ -155,37 +158,46 @@ design_jacobian_kernel(const JacArgs<T> a, int per_warp) {
         sc = ldexpf(1.f, e);
         inv_scale[0] = inv_scale[1] = inv_scale[2] = (T)ldexpf(1.f, -e);
       }
-      // consecutive lanes write consecutive half2 (shared-memory reads without bank conflicts)
-      const int h2 = a.ld / 2;
-      __half2* rows = reinterpret_cast<__half2*>(reinterpret_cast<__half*>(a.J) + (size_t)col0 * a.ld);
-      for (int q = lane; q < 3 * h2; q += 32) {
-        const int c = (q >= h2) + (q >= 2 * h2);
-        const int d = (q - c * h2) * 2;
+      // 8 halves per lane and step: rows of src and q_o read as 16-byte vectors, one 16-byte
+      // store; the piece that holds D (and the two carried terms) takes the scalar path
+      const int c8 = a.ld / 8, full8 = D / 8;
+      __half* rows = reinterpret_cast<__half*>(a.J) + (size_t)col0 * a.ld;
+      for (int q = lane; q < 3 * c8; q += 32) {
+        const int c = (q >= c8) + (q >= 2 * c8);
+        const int k8 = q - c * c8;
         const float tcs = (float)(c == 0 ? tq[0] : (c == 1 ? tq[1] : tq[2])) * sc;
-        const T* sp = src + c * D;
-        __half hv[2];
-        if (d + 1 < D) {
-          hv[0] = __float2half_rn(fmaf(-(float)qi[d], tcs, (float)sp[d] * sc));
-          hv[1] = __float2half_rn(fmaf(-(float)qi[d + 1], tcs, (float)sp[d + 1] * sc));
+        const T* sp = src + c * Dp + 8 * k8;
+        const T* qp = qi + 8 * k8;
+        __align__(16) __half2 h4[4];
+        if (k8 < full8) {
+          const float4 s0 = *reinterpret_cast<const float4*>(sp), s1 = *reinterpret_cast<const float4*>(sp + 4);
+          const float4 q0 = *reinterpret_cast<const float4*>(qp), q1 = *reinterpret_cast<const float4*>(qp + 4);
+          h4[0] = __floats2half2_rn(fmaf(-q0.x, tcs, s0.x * sc), fmaf(-q0.y, tcs, s0.y * sc));
+          h4[1] = __floats2half2_rn(fmaf(-q0.z, tcs, s0.z * sc), fmaf(-q0.w, tcs, s0.w * sc));
+          h4[2] = __floats2half2_rn(fmaf(-q1.x, tcs, s1.x * sc), fmaf(-q1.y, tcs, s1.y * sc));
+          h4[3] = __floats2half2_rn(fmaf(-q1.z, tcs, s1.z * sc), fmaf(-q1.w, tcs, s1.w * sc));
         } else {
           const float xb = (c == 0 ? tbp[0] : (c == 1 ? tbp[1] : tbp[2])) * sc;
           const __half xh = __float2half_rn(xb);
           const __half xl = __float2half_rn(xb - __half2float(xh));
+          __half hv[8];
 #pragma unroll
-          for (int t = 0; t < 2; ++t) {
-            const int dd = d + t;
-            hv[t] = dd < D ? __float2half_rn(fmaf(-(float)qi[dd], tcs, (float)sp[dd] * sc))
-                           : (dd == D ? xh : (dd == D + 1 ? xl : __float2half_rn(0.f)));
+          for (int t = 0; t < 8; ++t) {
+            const int d = 8 * k8 + t;
+            hv[t] = d < D ? __float2half_rn(fmaf(-(float)qp[t], tcs, (float)sp[t] * sc))
+                          : (d == D ? xh : (d == D + 1 ? xl : __float2half_rn(0.f)));
           }
+#pragma unroll
+          for (int t = 0; t < 4; ++t) h4[t] = __halves2half2(hv[2 * t], hv[2 * t + 1]);
         }
-        rows[q] = __halves2half2(hv[0], hv[1]);
+        *reinterpret_cast<uint4*>(rows + (size_t)q * 8) = *reinterpret_cast<const uint4*>(h4);
       }
     } else {
       double* rows = reinterpret_cast<double*>(a.J) + (size_t)col0 * a.ld;
       for (int q = lane; q < 3 * a.ld; q += 32) {
         const int c = (q >= a.ld) + (q >= 2 * a.ld);
         const int d = q - c * a.ld;
-        rows[q] = d < D ? (double)src[c * D + d] : 0.0;
+        rows[q] = d < D ? (double)src[c * Dp + d] : 0.0;
       }
     }
     if (lane < 3) {
@@ -211,7 +223,7 @@ design_jacobian_kernel(const JacArgs<T> a, int per_warp) {
       qi[d] = qv;
       qmx = max(qmx, abs(qv));
       if (TABLE) qbq = fma((T)qbar_s[d], qv, qbq);
-      Jacc[d] = Jacc[D + d] = Jacc[2 * D + d] = T(0);
+      Jacc[d] = Jacc[Dp + d] = Jacc[2 * Dp + d] = T(0);
     }
     qmx = warp_max(qmx);
     qbq = warp_sum(qbq);
@@ -381,15 +393,15 @@ design_jacobian_kernel(const JacArgs<T> a, int per_warp) {
               const T qb = TABLE ? (T)qbar_s[d] : T(0);
 #pragma unroll
               for (int c = 0; c < 3; ++c) {
-                Jt[c * D + d] = jv[c];
-                Jacc[c * D + d] -= jv[c];
+                Jt[c * Dp + d] = jv[c];
+                Jacc[c * Dp + d] -= jv[c];
                 mx[c] = max(mx[c], abs(jv[c]));
                 tq[c] = fma(qv, jv[c], tq[c]);
                 tb[c] = fma(qb, jv[c], tb[c]);
               }
             }
           } else {
-            for (int d = lane; d < 3 * D; d += 32) Jt[d] = T(0);
+            for (int d = lane; d < 3 * Dp; d += 32) Jt[d] = T(0);
           }
           __syncwarp();
           emit3(Jt, (long long)pinfo[2 * k], atom, pinfo[2 * k + 1], mx, tq, tb);
