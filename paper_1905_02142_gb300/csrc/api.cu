@@ -1174,7 +1174,13 @@ static int design(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, voi
     if (ncols > 0x7fffffffLL - 256)
       return fail(h, SOAPGAP_E_UNSUPPORTED, "too many Jacobian columns (3 (pairs + atoms) >= 2^31): split the batch");
     const int ld = h->mixed ? h->tcm.dpd : D;
-    ENS(h, h->dk_J, (size_t)ncols * ld * (h->mixed ? sizeof(__half) : sizeof(double)));
+    {
+      // the table path writes only the first D + 2 entries of each column: the padding up to
+      // ld stays as zeroed at allocation (the sparse operand is zero there too)
+      const size_t cap_before = h->dk_J.cap;
+      ENS(h, h->dk_J, (size_t)ncols * ld * (h->mixed ? sizeof(__half) : sizeof(double)));
+      if (h->dk_J.cap != cap_before) CK(h, cudaMemsetAsync(h->dk_J.p, 0, h->dk_J.cap, st));
+    }
     ENS(h, h->dk_at, sizeof(int2) * (size_t)ncols);
     ENS(h, h->dk_v, sizeof(Vec4<T>) * (size_t)ncols);
     JacArgs<T> ja{};

@@ -158,39 +158,38 @@ design_jacobian_kernel(const JacArgs<T> a, int per_warp) {
         sc = ldexpf(1.f, e);
         inv_scale[0] = inv_scale[1] = inv_scale[2] = (T)ldexpf(1.f, -e);
       }
-      // 8 halves per lane and step: rows of src and q_o read as 16-byte vectors, one 16-byte
-      // store; the piece that holds D (and the two carried terms) takes the scalar path
-      const int c8 = a.ld / 8, full8 = D / 8;
+      // 8 halves per lane and step over the pieces inside [0, D): rows of src and q_o read as
+      // 16-byte vectors, one 16-byte store.  The piece holding D and the two carried terms is
+      // written by lane c of the three; the padding after it stays zero from allocation.
+      const int full8 = D / 8;
       __half* rows = reinterpret_cast<__half*>(a.J) + (size_t)col0 * a.ld;
-      for (int q = lane; q < 3 * c8; q += 32) {
-        const int c = (q >= c8) + (q >= 2 * c8);
-        const int k8 = q - c * c8;
+      for (int q = lane; q < 3 * full8; q += 32) {
+        const int c = (q >= full8) + (q >= 2 * full8);
+        const int k8 = q - c * full8;
         const float tcs = (float)(c == 0 ? tq[0] : (c == 1 ? tq[1] : tq[2])) * sc;
         const T* sp = src + c * Dp + 8 * k8;
         const T* qp = qi + 8 * k8;
+        const float4 s0 = *reinterpret_cast<const float4*>(sp), s1 = *reinterpret_cast<const float4*>(sp + 4);
+        const float4 q0 = *reinterpret_cast<const float4*>(qp), q1 = *reinterpret_cast<const float4*>(qp + 4);
         __align__(16) __half2 h4[4];
-        if (k8 < full8) {
-          const float4 s0 = *reinterpret_cast<const float4*>(sp), s1 = *reinterpret_cast<const float4*>(sp + 4);
-          const float4 q0 = *reinterpret_cast<const float4*>(qp), q1 = *reinterpret_cast<const float4*>(qp + 4);
-          h4[0] = __floats2half2_rn(fmaf(-q0.x, tcs, s0.x * sc), fmaf(-q0.y, tcs, s0.y * sc));
-          h4[1] = __floats2half2_rn(fmaf(-q0.z, tcs, s0.z * sc), fmaf(-q0.w, tcs, s0.w * sc));
-          h4[2] = __floats2half2_rn(fmaf(-q1.x, tcs, s1.x * sc), fmaf(-q1.y, tcs, s1.y * sc));
-          h4[3] = __floats2half2_rn(fmaf(-q1.z, tcs, s1.z * sc), fmaf(-q1.w, tcs, s1.w * sc));
-        } else {
-          const float xb = (c == 0 ? tbp[0] : (c == 1 ? tbp[1] : tbp[2])) * sc;
-          const __half xh = __float2half_rn(xb);
-          const __half xl = __float2half_rn(xb - __half2float(xh));
-          __half hv[8];
-#pragma unroll
-          for (int t = 0; t < 8; ++t) {
-            const int d = 8 * k8 + t;
-            hv[t] = d < D ? __float2half_rn(fmaf(-(float)qp[t], tcs, (float)sp[t] * sc))
-                          : (d == D ? xh : (d == D + 1 ? xl : __float2half_rn(0.f)));
-          }
-#pragma unroll
-          for (int t = 0; t < 4; ++t) h4[t] = __halves2half2(hv[2 * t], hv[2 * t + 1]);
-        }
-        *reinterpret_cast<uint4*>(rows + (size_t)q * 8) = *reinterpret_cast<const uint4*>(h4);
+        h4[0] = __floats2half2_rn(fmaf(-q0.x, tcs, s0.x * sc), fmaf(-q0.y, tcs, s0.y * sc));
+        h4[1] = __floats2half2_rn(fmaf(-q0.z, tcs, s0.z * sc), fmaf(-q0.w, tcs, s0.w * sc));
+        h4[2] = __floats2half2_rn(fmaf(-q1.x, tcs, s1.x * sc), fmaf(-q1.y, tcs, s1.y * sc));
+        h4[3] = __floats2half2_rn(fmaf(-q1.z, tcs, s1.z * sc), fmaf(-q1.w, tcs, s1.w * sc));
+        *reinterpret_cast<uint4*>(rows + (size_t)c * a.ld + 8 * k8) = *reinterpret_cast<const uint4*>(h4);
+      }
+      if (lane < 3) {
+        // entries 8 full8 .. D + 1 of column c (at most 9: D mod 8 + 2), within the row since
+        // ld >= D + 2
+        const int c = lane;
+        const float tcs = (float)(c == 0 ? tq[0] : (c == 1 ? tq[1] : tq[2])) * sc;
+        const float xb = (c == 0 ? tbp[0] : (c == 1 ? tbp[1] : tbp[2])) * sc;
+        const __half xh = __float2half_rn(xb);
+        __half* row = rows + (size_t)c * a.ld;
+        for (int d = 8 * full8; d < D; ++d)
+          row[d] = __float2half_rn(fmaf(-(float)qi[d], tcs, (float)src[c * Dp + d] * sc));
+        row[D] = xh;
+        row[D + 1] = __float2half_rn(xb - __half2float(xh));
       }
     } else {
       double* rows = reinterpret_cast<double*>(a.J) + (size_t)col0 * a.ld;
