@@ -152,7 +152,8 @@ def flush_l2(buf):
 
 
 def algorithmic_flops(stage, n_pairs, n_atoms, w):
-    """Algorithmic FLOPs per launch of a stage (definitions stated in the design doc)."""
+    """Algorithmic FLOPs per launch of a stage: the multiply-adds the method needs (the
+    contraction of each pair kernel; the GAP products at K = D, not the 3 D of the split)."""
     L = (w.l_max + 1) ** 2
     n = w.n_max
     if stage == "pair_forward":
@@ -166,7 +167,8 @@ def algorithmic_flops(stage, n_pairs, n_atoms, w):
 
 
 def algorithmic_bytes(stage, n_pairs, n_atoms, w):
-    """Minimum DRAM bytes per launch of the memory-bound stages (definitions in the design doc)."""
+    """Minimum DRAM bytes per launch of the memory-bound stages: what each must read and write
+    once (listed per stage below)."""
     L = (w.l_max + 1) ** 2
     nch = w.n_max * w.n_species
     d = nch * (nch + 1) // 2 * (w.l_max + 1)
