@@ -252,11 +252,11 @@ extern "C" int soapgap_create(const soapgap_params* params, soapgap_handle** out
       e = ensure(h->table, (size_t)(h->ti.K + 1) * 2 * h->ti.fp * sizeof(float));
       if (e == cudaSuccess) e = sg_build_table(h->dp, h->bc64, h->cls, h->ti, (float*)h->table.p, 0);
       // The adjoint only feeds forces and virial (bar 1e-3 RMS), and reads the table of every
-      // pair together with its derivative: it takes nodes twice as far apart (half the
-      // table, so more of it stays in L1), with interpolation errors of about 4e-6 on the
-      // values and 7e-6 RMS (1.1e-4 at most) on the derivatives, relative to each function's
-      // scale, against 2.4e-7 and 9e-7 for the descriptor table.
-      double ha = std::min(0.04, smin / 12.5);
+      // pair together with its derivative: it takes nodes four times as far apart (a quarter
+      // of the table, which then stays in L1), with interpolation errors of about 6e-5 on the
+      // values and 6e-5 RMS (9e-4 at most) on the derivatives, relative to each function's
+      // scale, against 2.4e-7 and 9e-7 RMS for the descriptor table.
+      double ha = std::min(0.08, smin / 6.25);
       h->ti_adj = h->ti;
       h->ti_adj.K = (int)std::ceil(p.r_cut / ha);
       h->ti_adj.h = p.r_cut / h->ti_adj.K;
