@@ -9,7 +9,10 @@
  *             08, 15; the density smoothing of Sec. III.B; the radial recursion Eq. 04),
  *   p_nn'l(i) = sum_m c_nlm c_n'lm   (Eq. 09),   q(i) = p(i) / |p(i)|   (Sec. I),
  *   eps_i     = sum_s alpha_s (q_i . q_s)^zeta  over a sparse set (Sec. IV.A),
- * the energy of each structure, the forces -dE/dx and the virial -dE/dstrain.
+ * the energy of each structure, the forces -dE/dx and the virial -dE/dstrain; and, for
+ * fitting the alpha_s (Sec. IV.A), the kernel rows k(i, s) = (q_i . q_s)^zeta, their sums
+ * over each structure and their derivatives with respect to every position
+ * (soapgap_design, soapgap_kernel_rows).
  *
  * Conventions
  *   - Lengths in Angstrom.  cell rows are the lattice vectors.  Positions may lie anywhere:
@@ -30,8 +33,9 @@
  *   SOAPGAP_FP64  every step in FP64: the radial recursion per pair in the primitive basis,
  *                 the orthonormalisation W = S^-1/2 per atom, FP64 GEMM for the GAP kernel.
  *   SOAPGAP_MIXED pair and power-spectrum kernels in FP32 with radial functions taken from
- *                 an FP64-built table of the orthonormal-basis coefficients; GAP products
- *                 on the tensor cores with FP32 accumulation; FP64 per-structure sums.
+ *                 FP64-built tables of the orthonormal-basis coefficients (the adjoint's
+ *                 with coarser nodes: it only feeds forces and virial); GAP products on the
+ *                 tensor cores with FP32 accumulation; FP64 per-structure sums.
  *   Float outputs typed "real" below are float for MIXED and double for FP64.
  *
  * Errors: every call returns 0 (SOAPGAP_OK) or a negative code; soapgap_last_error()
