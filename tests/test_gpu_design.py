@@ -177,6 +177,21 @@ def test_design_needs_model_and_valid_flags():
                                     None) == L.E_INVALID_ARG          # unknown flag bit
 
 
+def test_design_with_a_verlet_skin():
+    """With a skin the list holds pairs up to r_cut + skin; pairs beyond r_cut give zero
+    columns, so the rows equal those of a list without skin (up to summation order)."""
+    batch, name, m = CASES["batch"]()
+    model, *_ = make(name, m, "mixed")
+    s = structures(batch)
+    plain = model.design(s, k_atom=True, k_struct=True, dk=True)
+    model.set_skin(0.6)
+    skinned = model.design(s, k_atom=True, k_struct=True, dk=True)
+    assert model.pair_count() > 0
+    assert torch.allclose(skinned["k_atom"], plain["k_atom"], rtol=0, atol=1e-6)
+    assert torch.allclose(skinned["k_struct"], plain["k_struct"], rtol=1e-6, atol=0)
+    assert rel_all(skinned["dk"].cpu().numpy(), plain["dk"].cpu().numpy()) < 1e-5
+
+
 # ------------------------------------------------------------------ full training batch
 @pytest.fixture(scope="module")
 def full_batch():
