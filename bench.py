@@ -235,20 +235,11 @@ def profiled_traffic(w, stage, n_atoms):
         return None
 
 
-def oracle_sample_rate(w, n_sample_atoms: int, seed: int = 11, threads: int | None = None):
+def oracle_sample_rate(w, n_sample_atoms: int, seed: int = 11):
     """FP64 oracle on a bounded sample: a box of n_sample_atoms with the workload's recipe
     (density, minimum distance, hyperparameters, sparse-set size, zeta); energies, forces
-    and virial through the oracle as it stands, on `threads` host threads (default: as set).
-    Returns (atoms/s, seconds, threads)."""
+    and virial through the oracle as it stands.  Returns (atoms/s, seconds, threads)."""
     import torch
-
-    if threads is not None:
-        before = torch.get_num_threads()
-        torch.set_num_threads(threads)
-        try:
-            return oracle_sample_rate(w, n_sample_atoms, seed)
-        finally:
-            torch.set_num_threads(before)
 
     from oracle import Params, gap
     P = Params.from_dict(w.params())
@@ -595,12 +586,8 @@ def run_ours(args, rank, world, local_rank):
     if world == 1 and not args.no_cpu_baseline:
         n_cpu = 3072
         rate, dt, threads = oracle_sample_rate(w, n_cpu)
-        n_one = 128
-        rate1, dt1, _ = oracle_sample_rate(w, n_one, threads=1)
         cpu = {"value": rate, "unit": "atoms/s", "cores": threads, "kind": "oracle",
-               "sample": f"{n_cpu}-atom box of the workload recipe, energies+forces+virial, {dt:.1f} s",
-               "single_core": {"value": rate1, "unit": "atoms/s", "cores": 1,
-                               "sample": f"{n_one}-atom box of the same recipe, {dt1:.1f} s"}}
+               "sample": f"{n_cpu}-atom box of the workload recipe, energies+forces+virial, {dt:.1f} s"}
     line = {
         "metric": METRIC, "value": world * n / t_max * args.steps, "unit": "atoms/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
