@@ -149,7 +149,11 @@ int soapgap_descriptor_dim(const soapgap_handle* h, int32_t* dim);
 
 /* Set the GAP model (Sec. IV.A): q_sparse [M][D] host double, packed layout, each row a
  * normalised descriptor; alpha [M] host double; zeta > 0.  Copies to the device and
- * synchronises.  M >= 1. */
+ * synchronises.  M >= 1.  SOAPGAP_E_INVALID_ARG for a NULL pointer, M < 1, zeta <= 0 or a
+ * non-finite entry; the handle keeps its previous model then.  Past those checks the
+ * previous model is dropped first, so after any later failure (SOAPGAP_E_CUDA) the handle
+ * has none and calls that need one return SOAPGAP_E_STATE.  A new model requires a new
+ * ENERGY evaluation before soapgap_backward. */
 int soapgap_set_model(soapgap_handle* h, const double* q_sparse, const double* alpha,
                       int32_t m, double zeta);
 
@@ -177,6 +181,8 @@ int soapgap_compute(soapgap_handle* h, const soapgap_batch* batch, uint32_t flag
  *     replay); the cell and atom_offs are taken at call (capture) time through the
  *     handle's pinned staging, so the handle must not be used for another batch shape
  *     between replays of a captured graph;
+ *   - a captured graph holds the device buffers of the model it was captured with:
+ *     capture again after soapgap_set_model (a larger sparse set reallocates them);
  *   - device-detected errors (non-finite position, coincident atoms, pair capacity) are
  *     reported by soapgap_sync_status, not by the return value. */
 
@@ -226,7 +232,8 @@ int soapgap_verlet(soapgap_handle* h, const soapgap_batch* batch, double* pos, d
  * dE_dEstruct [n_struct] DEVICE double (weights of each structure's energy);
  * grad_pos [n_atoms][3] DEVICE double receives d(sum_s w_s E_s)/dx (i.e. minus the
  * force when w = 1); virial [n_struct][3][3] DEVICE double or NULL.
- * Returns SOAPGAP_E_STATE without a preceding ENERGY evaluation. */
+ * Returns SOAPGAP_E_STATE without a model, or without a preceding ENERGY evaluation
+ * under the current model. */
 int soapgap_backward(soapgap_handle* h, const soapgap_batch* batch, const double* dE_dEstruct,
                      double* grad_pos, double* virial, void* stream);
 

@@ -111,8 +111,13 @@ class SoapGap:
         al = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64))
         if qs.ndim != 2 or qs.shape[1] != self.dim or al.shape != (qs.shape[0],):
             raise ValueError(f"q_sparse must be [M, {self.dim}] and alpha [M]")
-        self._check(self.lib.soapgap_set_model(self.h, qs.ctypes.data, al.ctypes.data,
-                                               qs.shape[0], float(zeta)))
+        try:
+            self._check(self.lib.soapgap_set_model(self.h, qs.ctypes.data, al.ctypes.data,
+                                                   qs.shape[0], float(zeta)))
+        except SoapGapError as e:
+            if e.code != L.E_INVALID_ARG:
+                self.m = 0          # the library dropped its previous model
+            raise
         self.m = qs.shape[0]
 
     def compute(self, s: Structures, *, desc=False, energy=False, forces=False, virial=False,
@@ -322,7 +327,8 @@ class CapturedEvaluation:
     The constructor makes one synchronous call (sizing the workspace), then captures an
     asynchronous call; replay() re-runs the whole evaluation (neighbour list included) on
     the current contents of s.pos / s.species and returns the same output tensors, updated
-    in place.  Call model.sync_status() after replays to surface device-side errors."""
+    in place.  Call model.sync_status() after replays to surface device-side errors.
+    Capture again after model.set_model: the graph holds the buffers of the model it saw."""
 
     def __init__(self, model: SoapGap, s: Structures, **outputs):
         self.model, self.s = model, s

@@ -299,6 +299,16 @@ extern "C" int soapgap_set_model(soapgap_handle* h, const double* q_sparse, cons
   if (!q_sparse || !alpha || m < 1) return fail(h, SOAPGAP_E_INVALID_ARG, "set_model: need q_sparse, alpha and m >= 1");
   if (!(zeta > 0) || !std::isfinite(zeta)) return fail(h, SOAPGAP_E_INVALID_ARG, "set_model: zeta must be > 0");
   const size_t nq = (size_t)m * h->D;
+  for (size_t i = 0; i < nq; ++i)
+    if (!std::isfinite(q_sparse[i])) return fail(h, SOAPGAP_E_INVALID_ARG, "set_model: q_sparse is not finite");
+  for (int i = 0; i < m; ++i)
+    if (!std::isfinite(alpha[i])) return fail(h, SOAPGAP_E_INVALID_ARG, "set_model: alpha is not finite");
+  // The buffers below may be reallocated: until they all hold the new model the handle has
+  // none, so a failure part-way leaves no stale device pointer in use.
+  h->has_model = false;
+  h->have_forward = false;
+  h->M = 0;
+  h->tcm = GapTcModel{};
   const size_t es = h->mixed ? sizeof(float) : sizeof(double);
   CK(h, ensure(h->qs, nq * es));
   CK(h, ensure(h->alpha, (size_t)m * es));
@@ -889,6 +899,7 @@ extern "C" int soapgap_backward(soapgap_handle* h, const soapgap_batch* batch, c
   if (!h) return SOAPGAP_E_INVALID_ARG;
   int rc = check_batch(h, batch);
   if (rc != SOAPGAP_OK) return rc;
+  if (!h->has_model) return fail(h, SOAPGAP_E_STATE, "no GAP model: call soapgap_set_model first");
   if (!h->have_forward || h->fw_atoms != batch->n_atoms || h->fw_struct != batch->n_struct)
     return fail(h, SOAPGAP_E_STATE, "backward needs a preceding ENERGY evaluation of the same batch");
   if (!dE_dEstruct || !grad_pos) return fail(h, SOAPGAP_E_INVALID_ARG, "backward needs dE_dEstruct and grad_pos");

@@ -309,6 +309,32 @@ def test_invalid_inputs_are_reported():
     assert torch.isfinite(ok["e_struct"]).all()
 
 
+def test_model_replacement_and_invalid_models():
+    """An invalid model is refused and leaves the previous one in place; a replaced model
+    needs a new energy evaluation before the adjoint."""
+    from paper_1905_02142_gb300 import _lib as L
+    from paper_1905_02142_gb300.api import SoapGapError
+    P, qs, al, zeta = sparse_model("box64_n6l6")
+    model = model_for(params_dict(P), "mixed", qs, al, zeta)
+    s = structures(SMALL_BATCH)
+    e0 = model.compute(s, energy=True)["e_struct"].clone()
+    bad = np.array(al, dtype=np.float64)
+    bad[3] = np.nan
+    with pytest.raises(SoapGapError) as e:
+        model.set_model(qs, bad, zeta)
+    assert e.value.code == L.E_INVALID_ARG
+    assert torch.equal(model.compute(s, energy=True)["e_struct"], e0)
+    model.set_model(qs, 2 * np.asarray(al), zeta)
+    w = torch.ones(s.n_struct, dtype=torch.float64, device=e0.device)
+    with pytest.raises(SoapGapError) as e:
+        model.backward(s, w)
+    assert e.value.code == L.E_STATE
+    e1 = model.compute(s, energy=True)["e_struct"]
+    scale = float(e0.abs().max())
+    assert torch.allclose(e1, 2 * e0, rtol=1e-5, atol=1e-5 * scale)
+    assert torch.isfinite(model.backward(s, w)).all()
+
+
 def test_pair_list_dense_corner_cluster():
     """Atoms squeezed into one corner of a large cell: far more neighbours per atom than the
     cell's mean density predicts, so the library's first neighbour sweep overflows its
