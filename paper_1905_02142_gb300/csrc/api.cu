@@ -548,6 +548,9 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
   const long long launches0 = sg_kernel_launches;
   const size_t N1n = (size_t)std::max(N, 1);
   if (!backward) {
+    // the workspace is about to change: until this call succeeds there is no forward pass
+    // for soapgap_backward to use
+    h->have_forward = false;
     int rc = setup_geometry(h, b);
     if (rc != SOAPGAP_OK) return rc;
     const int nseg = N * nsp;
@@ -632,6 +635,8 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     // one sweep over the candidates into per-atom slot arrays; a synchronous call retries
     // once with the measured largest count if the density estimate was too small
     int maxn = h->async_call ? h->slot_maxn : h->slot_maxn_est;
+    // a synchronous rebuild overwrites the list: it may be reused only once it completes
+    if (!device_decides) h->ref_valid = false;
     if (h->async_call && maxn <= 0)
       return fail(h, SOAPGAP_E_STATE, "no neighbour slots for an asynchronous call: make one synchronous call with the same batch first");
     ENS(h, h->slot_count, sizeof(int) * N1n);

@@ -335,6 +335,31 @@ def test_model_replacement_and_invalid_models():
     assert torch.isfinite(model.backward(s, w)).all()
 
 
+def test_failed_evaluation_leaves_no_forward_for_the_adjoint():
+    """A call that fails part-way has rewritten the workspace: the adjoint of the last
+    successful evaluation of the same batch shape is refused until a new one succeeds."""
+    from paper_1905_02142_gb300 import _lib as L
+    from paper_1905_02142_gb300.api import SoapGapError
+    P, qs, al, zeta = sparse_model("box64_n6l6")
+    model = model_for(params_dict(P), "mixed", qs, al, zeta)
+    good = synth.random_box(20, side=8.0, dmin=1.2, seed=12)
+    pos = good.pos.copy()
+    pos[1] = pos[0]                                   # same shape, two atoms coincide
+    bad = synth.Structure(pos=pos, cell=good.cell, species=good.species)
+    s_good = structures(synth.concat([good]))
+    w = torch.ones(1, dtype=torch.float64, device=s_good.pos.device)
+    model.compute(s_good, energy=True)
+    g0 = model.backward(s_good, w)
+    with pytest.raises(SoapGapError) as e:
+        model.compute(structures(synth.concat([bad])), energy=True)
+    assert "coincide" in str(e.value)
+    with pytest.raises(SoapGapError) as e:
+        model.backward(s_good, w)
+    assert e.value.code == L.E_STATE
+    model.compute(s_good, energy=True)
+    assert torch.equal(model.backward(s_good, w), g0)
+
+
 def test_pair_list_dense_corner_cluster():
     """Atoms squeezed into one corner of a large cell: far more neighbours per atom than the
     cell's mean density predicts, so the library's first neighbour sweep overflows its
