@@ -296,10 +296,13 @@ int soapgap_last_launch_count(const soapgap_handle* h, int64_t* n);
 /* Number of neighbour pairs found by the last compute call (diagnostics). */
 int soapgap_last_pair_count(const soapgap_handle* h, int64_t* n_pairs);
 
-/* Copy the pair list of the last soapgap_compute call to HOST arrays, in canonical order
+/* Copy the pair list of the last synchronous list build to HOST arrays, in canonical order
  * (centre, neighbour species, neighbour, then shift S lexicographically):
  *   centre[P], neighbour[P] int32 atom indices; shift[P][3] int32 image S (x_j + S.h).
- * `capacity` is the length of the arrays; SOAPGAP_E_CAPACITY if it is below P. */
+ * With a Verlet skin the list holds the pairs within r_cut + skin of its build.
+ * `capacity` is the length of the arrays; SOAPGAP_E_CAPACITY if it is below P.
+ * SOAPGAP_E_STATE if no synchronous call has completed a list since the last failed or
+ * asynchronous rebuild. */
 int soapgap_export_pairs(soapgap_handle* h, int64_t capacity, int32_t* centre,
                          int32_t* neighbour, int32_t* shift);
 

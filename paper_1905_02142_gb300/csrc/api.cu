@@ -107,6 +107,8 @@ struct soapgap_handle {
   int ref_atoms = -1, ref_struct = -1;
   std::vector<double> ref_cell;
   int last_rebuild = -1;    // 1 / 0 for synchronous calls, -1 when decided on the device
+  bool list_ok = false;     // the pair list (seg_offs, key) is complete, with last_pairs pairs
+  int list_atoms = 0;       // ... over this many atoms
   int slot_maxn = 0;        // slot capacity per atom of the last synchronous neighbour search
   int cur_maxn = 0;         // slot capacity used by the current call
   int slot_maxn_est = 0;    // estimate for the current batch (from its densities)
@@ -635,8 +637,10 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     // one sweep over the candidates into per-atom slot arrays; a synchronous call retries
     // once with the measured largest count if the density estimate was too small
     int maxn = h->async_call ? h->slot_maxn : h->slot_maxn_est;
-    // a synchronous rebuild overwrites the list: it may be reused only once it completes
+    // a rebuild overwrites the list: it may be reused or exported only once it completes
+    // (an asynchronous rebuild never reads its pair count back, so it does not count)
     if (!device_decides) h->ref_valid = false;
+    h->list_ok = false;
     if (h->async_call && maxn <= 0)
       return fail(h, SOAPGAP_E_STATE, "no neighbour slots for an asynchronous call: make one synchronous call with the same batch first");
     ENS(h, h->slot_count, sizeof(int) * N1n);
@@ -720,6 +724,10 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
       if (e == cudaErrorInvalidConfiguration)
         return fail(h, SOAPGAP_E_UNSUPPORTED, "too many neighbours per atom for the pair sort");
       CK(h, e);
+      if (!h->async_call) {
+        h->list_ok = true;
+        h->list_atoms = N;
+      }
     }
     if (h->skin > 0.0) {
       // every call: current separations of the whole list and the list of live pairs
@@ -998,14 +1006,20 @@ extern "C" int soapgap_last_pair_count(const soapgap_handle* h, int64_t* n) {
 extern "C" int soapgap_export_pairs(soapgap_handle* h, int64_t capacity, int32_t* centre,
                                     int32_t* neighbour, int32_t* shift) {
   if (!h || !centre || !neighbour || !shift) return SOAPGAP_E_INVALID_ARG;
+  if (!h->list_ok)
+    return fail(h, SOAPGAP_E_STATE, "export_pairs: no complete pair list (the last list build failed or was asynchronous)");
   const long long P = h->last_pairs;
   if (capacity < P) return fail(h, SOAPGAP_E_CAPACITY, "export_pairs: arrays shorter than the pair count");
   if (P == 0) return SOAPGAP_OK;
-  const int N = h->fw_atoms, nsp = h->prm.n_species;
+  const int N = h->list_atoms, nsp = h->prm.n_species;
   std::vector<int> offs((size_t)N * nsp + 1);
   std::vector<unsigned long long> keys((size_t)P);
   CK(h, cudaMemcpy(offs.data(), h->seg_offs.p, sizeof(int) * offs.size(), cudaMemcpyDeviceToHost));
   CK(h, cudaMemcpy(keys.data(), h->key.p, 8 * (size_t)P, cudaMemcpyDeviceToHost));
+  // the offsets must span exactly [0, P) in order before they index the caller's arrays
+  if (offs[0] != 0 || offs.back() != P) return fail(h, SOAPGAP_E_STATE, "export_pairs: pair offsets inconsistent");
+  for (size_t k = 1; k < offs.size(); ++k)
+    if (offs[k] < offs[k - 1]) return fail(h, SOAPGAP_E_STATE, "export_pairs: pair offsets inconsistent");
   for (int i = 0; i < N; ++i)
     for (int p = offs[(size_t)i * nsp]; p < offs[(size_t)(i + 1) * nsp]; ++p) centre[p] = i;
   for (long long p = 0; p < P; ++p) {
