@@ -45,6 +45,12 @@ class Structures:
         else:
             self.species = torch.as_tensor(np.asarray(species, dtype=np.int32), device=device).contiguous()
         self.n_atoms = int(self.pos.shape[0])
+        if self.pos.dim() != 2 or self.pos.shape[1] != 3:
+            raise ValueError("pos must be [n_atoms, 3]")
+        if tuple(self.species.shape) != (self.n_atoms,):
+            raise ValueError("species must be [n_atoms]")
+        if self.atom_offs.shape != (self.n_struct + 1,):
+            raise ValueError("atom_offs must be [n_struct + 1] for n_struct cells")
 
     @staticmethod
     def from_batch(b, device="cuda") -> "Structures":
@@ -52,9 +58,16 @@ class Structures:
         return Structures(b.pos, b.cell, b.species, b.atom_offs, device=device)
 
     def c_batch(self, pos=None, species=None) -> L.Batch:
+        """The library's batch record.  Positions and species must still be contiguous CUDA
+        tensors of their original shape and dtype: the library reads them as device arrays."""
+        pos = self.pos if pos is None else pos
+        species = self.species if species is None else species
+        for name, t, dt, shape in (("pos", pos, torch.float64, (self.n_atoms, 3)),
+                                   ("species", species, torch.int32, (self.n_atoms,))):
+            if not (t.is_cuda and t.dtype == dt and tuple(t.shape) == shape and t.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous CUDA {dt} tensor of shape {shape}")
         return L.Batch(self.n_struct, self.n_atoms, self.atom_offs.ctypes.data, self.cell.ctypes.data,
-                       _ptr(self.pos if pos is None else pos),
-                       _ptr(self.species if species is None else species))
+                       _ptr(pos), _ptr(species))
 
 
 class SoapGap:
@@ -233,6 +246,8 @@ class SoapGap:
         """Gradient of sum_s w_s E_s with respect to positions (after an energy evaluation)."""
         dev = s.pos.device
         w = dE_dEstruct.to(device=dev, dtype=torch.float64).contiguous()
+        if tuple(w.shape) != (s.n_struct,):
+            raise ValueError(f"dE_dEstruct must be [n_struct] = [{s.n_struct}]")
         grad = torch.empty((s.n_atoms, 3), dtype=torch.float64, device=dev)
         vir = torch.empty((s.n_struct, 3, 3), dtype=torch.float64, device=dev) if virial else None
         st = (stream or torch.cuda.current_stream(dev)).cuda_stream
