@@ -29,6 +29,15 @@ def _ptr(t) -> int | None:
     raise TypeError(type(t))
 
 
+def _device_array(t, dtype, shape, name):
+    """t itself if it is a contiguous CUDA tensor of this dtype and shape (the library reads
+    it as a device array), else ValueError."""
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype
+            and tuple(t.shape) == tuple(shape) and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor of shape {tuple(shape)}")
+    return t
+
+
 class Structures:
     """A batch of periodic structures: host metadata plus device positions/species."""
 
@@ -62,10 +71,8 @@ class Structures:
         tensors of their original shape and dtype: the library reads them as device arrays."""
         pos = self.pos if pos is None else pos
         species = self.species if species is None else species
-        for name, t, dt, shape in (("pos", pos, torch.float64, (self.n_atoms, 3)),
-                                   ("species", species, torch.int32, (self.n_atoms,))):
-            if not (t.is_cuda and t.dtype == dt and tuple(t.shape) == shape and t.is_contiguous()):
-                raise ValueError(f"{name} must be a contiguous CUDA {dt} tensor of shape {shape}")
+        _device_array(pos, torch.float64, (self.n_atoms, 3), "pos")
+        _device_array(species, torch.int32, (self.n_atoms,), "species")
         return L.Batch(self.n_struct, self.n_atoms, self.atom_offs.ctypes.data, self.cell.ctypes.data,
                        _ptr(pos), _ptr(species))
 
@@ -203,6 +210,7 @@ class SoapGap:
         q = q.to(self.dtype).contiguous()
         if q.ndim != 2 or q.shape[1] != self.dim:
             raise ValueError(f"q must be [n, {self.dim}]")
+        _device_array(q, self.dtype, q.shape, "q")
         k = torch.empty((q.shape[0], self.m), dtype=self.dtype, device=q.device)
         st = (stream or torch.cuda.current_stream(q.device)).cuda_stream
         self._check(self.lib.soapgap_kernel_rows(self.h, _ptr(q), q.shape[0], _ptr(k), st))
@@ -221,6 +229,10 @@ class SoapGap:
 
     def verlet(self, s: "Structures", vel, forces, inv_mass, dt, drift: bool, stream=None):
         """Velocity-Verlet half step in place on s.pos and vel (see soapgap_verlet)."""
+        n = s.n_atoms
+        _device_array(vel, torch.float64, (n, 3), "vel")
+        _device_array(forces, torch.float64, (n, 3), "forces")
+        _device_array(inv_mass, torch.float64, (n,), "inv_mass")
         st = (stream or torch.cuda.current_stream(s.pos.device)).cuda_stream
         b = s.c_batch()
         self._check(self.lib.soapgap_verlet(self.h, ctypes.byref(b), _ptr(s.pos), _ptr(vel),
