@@ -58,8 +58,11 @@ extern "C" {
 /* return codes */
 #define SOAPGAP_OK 0
 #define SOAPGAP_E_INVALID_ARG (-1) /* bad pointer, size, parameter, non-finite position */
-#define SOAPGAP_E_UNSUPPORTED (-2) /* n_max or l_max outside the supported range, or a
-                                      batch of 2^28 atoms or more (n_atoms n_species < 2^30) */
+#define SOAPGAP_E_UNSUPPORTED (-2) /* n_max or l_max outside the supported range, a
+                                      batch of 2^28 atoms or more (n_atoms n_species < 2^30),
+                                      or one whose pair list may reach 2^31 pairs (atoms x
+                                      per-atom neighbour slots, about 1.3 x the densest
+                                      structure's neighbours + 32) */
 #define SOAPGAP_E_CAPACITY (-3)    /* a fixed-size buffer is too small (see message)    */
 #define SOAPGAP_E_CUDA (-4)        /* a CUDA runtime call or kernel failed              */
 #define SOAPGAP_E_STATE (-5)       /* call order violated (no model / no forward pass)  */

@@ -654,6 +654,11 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     CK(h, sg_nbr_wrap(b->pos, N, nb, (double*)h->pos_w.p, (int4*)h->img.p, st));
     CK(h, sg_nbr_bin((const double*)h->pos_w.p, b->species, N, h->n_bins, nb, st));
     for (int attempt = 0; attempt < 2; ++attempt) {
+      // pair offsets are 32-bit: a sweep that raises no capacity flag has at most maxn pairs
+      // per atom, so N maxn below 2^31 keeps every offset and the total in range
+      if ((long long)N * maxn > 0x7fffffffLL)
+        return fail(h, SOAPGAP_E_UNSUPPORTED,
+                    "too many neighbour pairs for 32-bit pair offsets (atoms x per-atom slots >= 2^31): split the batch");
       ENS(h, h->key_tmp, 8 * N1n * (size_t)maxn);
       nb.key_tmp = (unsigned long long*)h->key_tmp.p;
       CK(h, sg_nbr_slots((const double*)h->pos_w.p, b->species, N, nsp, h->prm.r_cut + h->skin, maxn, nb, st));
