@@ -34,6 +34,27 @@ def test_every_declared_symbol_is_exported(lib):
         assert n in _lib.SIGNATURES, n
 
 
+def test_header_is_plain_c(tmp_path):
+    """The boundary header compiles as strict C99 (no C++ in the ABI), and a C program can
+    take the address of every declared function."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    import subprocess
+    names = declared_functions()
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "soapgap.h"\n'
+                   "void* table[] = {\n" + ",\n".join(f"  (void*){n}" for n in names) + "\n};\n")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-Wno-pedantic", "-I", os.path.join(ROOT, "include"), "-c", str(src),
+                        "-o", str(tmp_path / "use_header.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                        "-x", "c", os.path.join(ROOT, "include", "soapgap.h")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_parameter_validation_happens_on_host(lib):
     from paper_1905_02142_gb300 import _lib as L
 
