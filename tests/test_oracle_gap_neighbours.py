@@ -46,6 +46,38 @@ def test_zeta_one_is_linear(model):
     assert torch.allclose(e, q @ (torch.as_tensor(qs).T @ torch.as_tensor(al)), rtol=1e-13)
 
 
+@pytest.mark.parametrize("s,zeta,expected", [
+    (0.5, 4.0, 0.0625),                 # 2^-4
+    (0.5, 2.0, 0.25),                   # 2^-2
+    (0.5, 2.5, 2.0 ** -2.5),            # 0.17677669529663687
+    (0.25, 0.5, 0.5),                   # square root
+    (0.9, 3.0, 0.729),                  # 0.9 * 0.9 * 0.9
+    (1.0, 7.0, 1.0),                    # a unit self-similarity stays 1
+    (0.0, 4.0, 0.0),
+    (-1e-17, 2.5, 0.0),                 # a rounding-negative dot product is clamped (non-integer zeta)
+    (-0.5, 3.0, -0.125),                # integer zeta: plain repeated product, sign kept
+])
+def test_kernel_power_hand_values(s, zeta, expected):
+    """(q_i . q_s)^zeta of the SOAP kernel (Sec. I) at values fixed by arithmetic alone:
+    a wrong exponent (zeta - 1, zeta + 1) or a wrong branch fails at least one case."""
+    got = float(gap.kernel_power(torch.tensor([s], dtype=DT), zeta)[0])
+    assert got == pytest.approx(expected, rel=1e-15, abs=0.0)
+
+
+def test_local_energies_by_hand():
+    """eps_i = sum_s alpha_s (q_i . q_s)^zeta (Sec. IV.A) on two 2-dimensional unit
+    descriptors and two sparse rows, summed by hand: q_0 . q_s = (1, 0.6), q_1 . q_s = (0, 0.8)."""
+    q = torch.tensor([[1.0, 0.0], [0.0, 1.0]], dtype=DT)
+    qs = torch.tensor([[1.0, 0.0], [0.6, 0.8]], dtype=DT)
+    al = torch.tensor([0.5, -2.0], dtype=DT)
+    e2 = gap.local_energies(q, qs, al, 2.0)
+    assert e2.tolist() == pytest.approx([0.5 - 2.0 * 0.36, -2.0 * 0.64], rel=1e-15)
+    e4 = gap.local_energies(q, qs, al, 4.0)
+    assert e4.tolist() == pytest.approx([0.5 - 2.0 * 0.1296, -2.0 * 0.4096], rel=1e-15)
+    e15 = gap.local_energies(q, qs, al, 1.5)
+    assert e15.tolist() == pytest.approx([0.5 - 2.0 * 0.6 ** 1.5, -2.0 * 0.8 ** 1.5], rel=1e-15)
+
+
 @pytest.mark.parametrize("zeta", [4.0, 2.5])
 def test_forces_by_central_differences(model, zeta):
     P, qs, al, b = model
