@@ -11,6 +11,9 @@ timed on the same workload beside it.
 Under torchrun each rank evaluates its own copy of the workload (independent problems,
 no collective on the data path: weak scaling); rank 0 prints one JSON line.
 The reference arm (--impl reference) times the FP64 CPU oracle on bounded samples.
+The oracle leg of the default run (cpu_baseline, 1 GPU only) times the oracle on sample
+boxes and also evaluates it on sampled atoms of the benchmark workload itself, so that the
+line states the measured error of both GPU paths (measured_err) beside the bars.
 """
 from __future__ import annotations
 
@@ -33,8 +36,11 @@ import synth  # noqa: E402
 
 METRIC = "atoms/s for SOAP+GAP energy+forces, mixed vs FP64 GPU path at stated err"
 STATED_ERR = {"p_rel": 1e-5, "energy_rel": 1e-4, "forces_rms_rel": 1e-3,
-              "fp64_p_rel": "1e-11 at n_max<=6; 50 eps sqrt(cond S) above"}
-FP32_PEAK_NOTE = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x SM clock"
+              "fp64_p_rel": "max(1e-11, 4 eps sqrt(cond S))",
+              "fp64_energy_rel": "max(1e-10, 0.1 eps sqrt(cond S))",
+              "fp64_forces_rms_rel": "max(1e-9, 2 eps sqrt(cond S))"}
+FP32_PEAK_NOTE = "FP32 FMA measured (soapgap_measure_alu_peak: independent FMA chains on every SM)"
+FP64_PEAK_NOTE = "FP64 FMA measured (soapgap_measure_alu_peak: independent FMA chains on every SM)"
 
 
 def parse():
@@ -151,15 +157,23 @@ def flush_l2(buf):
     buf.add_(1.0)  # writes (and reads) a buffer larger than the 129 MB L2
 
 
-def algorithmic_flops(stage, n_pairs, n_atoms, w):
-    """Algorithmic FLOPs per launch of a stage: the multiply-adds the method needs (the
-    contraction of each pair kernel; the GAP products at K = D, not the 3 D of the split)."""
+def algorithmic_flops(stage, n_pairs, n_atoms, w, contraction_only=False):
+    """Algorithmic FLOPs per launch of a stage: the arithmetic the method needs.
+
+    Per pair (each pair feeds the n_max channels of its neighbour's species):
+      pair_forward  2 n_max L (c[n][lm] += b_n a_lm) + 4 L (the Y_lm recursion)
+                    + 12 (n_max + 2) (the radial terms)
+      pair_adjoint  4 n_max L (u = G b, u' = G b') + 12 L (Y_lm and grad Y_lm, dotted)
+    contraction_only keeps the first term of each.  The GAP products count 2 N M D
+    (K = D, not the padded or split K the tensor cores execute)."""
     L = (w.l_max + 1) ** 2
     n = w.n_max
     if stage == "pair_forward":
-        return 2.0 * n * L * n_pairs            # c[n][lm] += b_n a_lm
+        extra = 0.0 if contraction_only else 4.0 * L + 12.0 * (n + 2)
+        return (2.0 * n * L + extra) * n_pairs
     if stage == "pair_adjoint":
-        return 4.0 * n * L * n_pairs            # u_lm = G b, u'_lm = G b'
+        extra = 0.0 if contraction_only else 12.0 * L
+        return (4.0 * n * L + extra) * n_pairs
     if stage in ("gap_forward", "gap_backward"):
         d = (n * w.n_species) * (n * w.n_species + 1) // 2 * (w.l_max + 1)
         return 2.0 * n_atoms * w.n_sparse * d
@@ -190,10 +204,10 @@ def load_peaks():
         return 6800.0, 1900.0, "fallback"
 
 
-def stage_rooflines(stages, n_pairs, n_atoms, w, sm_mhz):
-    """Per-stage roofline: achieved algorithmic rate over the stage's own bound."""
+def stage_rooflines(stages, n_pairs, n_atoms, w, alu):
+    """Per-stage roofline: achieved algorithmic rate over the stage's own bound (alu: the
+    measured FP32 FMA peak in TFLOP/s)."""
     hbm, tc, src = load_peaks()
-    alu = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     out = {}
     for k, ms in stages.items():
         if ms <= 0:
@@ -205,8 +219,10 @@ def stage_rooflines(stages, n_pairs, n_atoms, w, sm_mhz):
                       "frac": a / tc, "peak_source": "FP16 dense = BF16 " + src}
         elif k in ("pair_forward", "pair_adjoint"):
             a = algorithmic_flops(k, n_pairs, n_atoms, w) / t / 1e12
+            ac = algorithmic_flops(k, n_pairs, n_atoms, w, contraction_only=True) / t / 1e12
             out[k] = {"bound": "alu", "achieved": a, "peak": alu, "unit": "TFLOP/s",
-                      "frac": a / alu, "peak_source": FP32_PEAK_NOTE}
+                      "frac": a / alu, "contraction_only_frac": ac / alu,
+                      "peak_source": FP32_PEAK_NOTE}
         else:
             a = algorithmic_bytes(k, n_pairs, n_atoms, w) / t / 1e9
             out[k] = {"bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
@@ -374,6 +390,50 @@ def cpu_baseline(w, n_atoms: int = 512):
                       f"{wall:.1f} s wall",
             "single_core": {"value": n_atoms / solo, "unit": "atoms/s", "cores": 1,
                             "sample": f"one {n_atoms}-atom box on one thread, {solo:.1f} s"}}
+
+
+def measured_errors(w, batch, s, dev, n_centres=16, n_force_atoms=2, seed=2024):
+    """Errors of the mixed and FP64 GPU paths against the oracle on the benchmark workload
+    itself (part of the oracle leg: the oracle is run, not timed, on sampled atoms).
+
+    Both sides take the oracle's own sparse set of the workload (its separate box and
+    selection), so no oracle input comes from the GPU.  p = q |p| of n_centres sampled
+    centres (max over centres of |dp|/|p|), their local energies (|d eps|_2/|eps|_2) and the
+    forces on n_force_atoms of them (|dF|_2/|F|_2)."""
+    import torch
+
+    from oracle import Params, basis, gap, soap
+    from paper_1905_02142_gb300.api import SoapGap
+    t0 = time.monotonic()
+    P = Params.from_dict(w.params())
+    W = basis.orthonormaliser(P.n_max, P.r_cut, P.sigma_r0)
+    sb = w.sparse_box()
+    qs = gap.sparse_set(sb, P, synth.sparse_indices(sb.n_atoms, w.n_sparse, w.sparse_seed), W=W)
+    al = synth.gap_weights(w.n_sparse, w.alpha_seed)
+    centres = np.sort(np.random.default_rng(seed).choice(batch.n_atoms, n_centres, replace=False))
+    ref = soap.descriptors(batch, P, centers=centres, W=W)
+    c = ref["centers"]
+    p_ref = (ref["q"] * ref["pnorm"][:, None]).numpy()
+    eps_ref = gap.local_energies(ref["q"], torch.as_tensor(qs), torch.as_tensor(al), w.zeta).numpy()
+    f_ref, f_atoms = gap.forces_at(batch, P, qs, al, w.zeta, c[:n_force_atoms], W=W)
+    oracle_s = time.monotonic() - t0
+    out = {}
+    for precision in ("mixed", "fp64"):
+        m = SoapGap.from_dict(w.params(), precision=precision)
+        m.set_model(qs, al, w.zeta)
+        r = m.compute(s, desc=True, energy=True, forces=True)
+        q = r["q"].double().cpu().numpy()[c]
+        pn = r["pnorm"].double().cpu().numpy()[c]
+        p_err = np.max(np.linalg.norm(q * pn[:, None] - p_ref, axis=1) / np.linalg.norm(p_ref, axis=1))
+        e = r["e_atom"].double().cpu().numpy()[c]
+        f = r["forces"].cpu().numpy()[f_atoms]
+        out[precision] = {"p_rel_max": float(p_err),
+                          "energy_rel": float(np.linalg.norm(e - eps_ref) / np.linalg.norm(eps_ref)),
+                          "forces_rms_rel": float(np.linalg.norm(f - f_ref) / np.linalg.norm(f_ref))}
+        m.close()
+    out["sample"] = (f"{len(c)} sampled centres (p, local energies) and forces on {len(f_atoms)} "
+                     f"of them, oracle sparse set of {w.n_sparse}, oracle {oracle_s:.0f} s")
+    return out
 
 
 def run_reference(args, rank, world):
@@ -586,7 +646,7 @@ def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
 
-    from paper_1905_02142_gb300.api import SoapGap, Structures
+    from paper_1905_02142_gb300.api import SoapGap, Structures, measure_alu_peak
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     w = synth.get_workload(args.workload)
@@ -599,6 +659,9 @@ def run_ours(args, rank, world, local_rank):
     model = SoapGap.from_dict(params, precision="mixed")
     model.set_model(qs, al, w.zeta)
     tuned_warps = model.autotune(s)
+    gap_terms = model.gap_terms()
+    fp32_peak, sm_count = measure_alu_peak("fp32")
+    fp64_peak, _ = measure_alu_peak("fp64")
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     stream = torch.cuda.current_stream(dev)
 
@@ -673,9 +736,17 @@ def run_ours(args, rank, world, local_rank):
             e1.record(stream)
             e1.synchronize()
             t64.append(e0.elapsed_time(e1))
+        st64 = m64.stage_times()
         fp64 = {"value": n * len(t64) / (sum(t64) / 1e3), "unit": "atoms/s",
                 "ms_per_step": float(np.mean(t64)), "steps": len(t64),
-                "stages_ms": {k: round(v, 4) for k, v in m64.stage_times().items()}}
+                "stages_ms": {k: round(v, 4) for k, v in st64.items()}}
+        dom64 = max(st64, key=lambda k: st64[k])
+        fl64 = algorithmic_flops(dom64, model.pair_count(), n, w)
+        if fl64 is not None and st64[dom64] > 0:
+            a64 = fl64 / (st64[dom64] / 1e3) / 1e12
+            fp64["roofline"] = {"bound": "alu", "kernel": dom64, "achieved": a64, "peak": fp64_peak,
+                                "unit": "TFLOP/s", "frac": a64 / fp64_peak,
+                                "peak_source": FP64_PEAK_NOTE, "flops_per_launch": fl64}
         m64.close()
 
     if rank != 0:
@@ -684,14 +755,20 @@ def run_ours(args, rank, world, local_rank):
     dom = max((k for k in stages if algorithmic_flops(k, n_pairs, n, w) is not None),
               key=lambda k: stages[k])
     flops = algorithmic_flops(dom, n_pairs, n, w)
-    sm_mhz = clocks.get("sm_max_mhz") or 2070.0
-    peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     achieved = flops / (stages[dom] / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": profiled_traffic(w, dom, n),
-                "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
-                "peak_source": FP32_PEAK_NOTE + f" ({sm_mhz:.0f} MHz)",
-                "flops_per_launch": flops}
+    hbm, tc, src = load_peaks()
+    if dom in ("gap_forward", "gap_backward"):
+        roofline = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": tc,
+                    "unit": "TFLOP/s", "frac": achieved / tc, "peak_source": "FP16 dense = BF16 " + src}
+    else:
+        cflops = algorithmic_flops(dom, n_pairs, n, w, contraction_only=True)
+        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak,
+                    "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                    "contraction_only_frac": cflops / (stages[dom] / 1e3) / 1e12 / fp32_peak,
+                    "peak_source": FP32_PEAK_NOTE}
+    roofline.update({"traffic": profiled_traffic(w, dom, n),
+                     "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
+                     "flops_per_launch": flops})
     md = run_md(model, s, stream, max(args.steps, 20)) if not args.no_md else None
     batched = None
     if world == 1 and not args.no_batched:
@@ -700,8 +777,10 @@ def run_ours(args, rank, world, local_rank):
     if world == 1 and not args.no_design:
         design = run_design(args, dev, flush, stream)
     cpu = None
+    measured = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
+        measured = measured_errors(w, batch, s, dev)
     line = {
         "metric": METRIC, "value": world * n / t_max * args.steps, "unit": "atoms/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -710,10 +789,14 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": w.name, "description": w.description, "atoms": n,
                    "pairs": n_pairs, "sparse": w.n_sparse, "l2": "flushed between steps (256 MB write)",
                    "autotuned_adjoint_warps": tuned_warps,
+                   "gap_fp16_products": gap_terms[0], "gap_one_product_probe_err": gap_terms[1],
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "stated_err": STATED_ERR,
+        "measured_err": measured,
+        "peaks_measured": {"fp32_fma_tflops": fp32_peak, "fp64_fma_tflops": fp64_peak,
+                           "sm_count": sm_count},
         "stages_ms": {k: round(v, 4) for k, v in stages.items()},
-        "stages_roofline": stage_rooflines(stages, n_pairs, n, w, sm_mhz),
+        "stages_roofline": stage_rooflines(stages, n_pairs, n, w, fp32_peak),
         "graph": graph,
         "md": md,
         "batched": batched,

@@ -319,15 +319,45 @@ int soapgap_export_pairs(soapgap_handle* h, int64_t capacity, int32_t* centre,
  * that loads the library keeps until the process exits.
  *   q [n][d], q_sparse [m][d], alpha [m], e_atom [n]: DEVICE float (MIXED layout of q);
  *   zeta > 0; work is enqueued on `stream` (a cudaStream_t, NULL = default stream).
- * Returns SOAPGAP_E_CAPACITY, before any device work, when n * ceil(m/64) > 4194304.
+ * Returns SOAPGAP_E_CAPACITY, before any device work, when n * ceil(m/64) > 4194304 or
+ * n > 4194240 (65535 rows of 64 atoms, the launch grid's limit).
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.
+ * with that device current; make that first call before any stream capture.  A device
+ * reset destroys the array with its context: the next call on that device, in the new
+ * context, looks the address up again (it must then also come before any capture).
  * All calls share the one array and it keeps the last call's contents (each call writes
  * every entry it reads, so nothing needs clearing); calls that overlap on the GPU, on
  * different streams of the same device, race on it. */
 int soapgap_gap_energy_noalloc(const float* q, const float* q_sparse, const float* alpha,
                                int32_t n, int32_t m, int32_t d, double zeta, float* e_atom,
                                void* stream);
+
+/* Number of FP16 products of the mixed path's GAP energy (Sec. IV.A, eps_i = sum_s alpha_s
+ * (q_i . q_s)^zeta on the tensor cores; the paper has no GPU design to follow here).  The
+ * products are taken about the sparse-set mean, q = qbar + n u, as u_i . u_s on FP16
+ * operands: one product hi.hi, or three, hi.hi + hi.lo + lo.hi, with u = hi + lo.  At
+ * soapgap_set_model the library evaluates the local energies of the sparse rows themselves
+ * with one product and with three, and uses one product when their relative difference
+ * (|d eps|_2 / |eps|_2) is at most 1e-5, ten times below the 1e-4 energy bar; otherwise three.
+ * soapgap_set_gap_terms(h, terms): 0 = that automatic choice (default), 1 or 3 = forced; it
+ * applies to the current model and to later ones; SOAPGAP_E_INVALID_ARG for other values.
+ * soapgap_gap_terms(h, &terms, &probe_err): the number in use (0 without a mixed-precision
+ * model) and the measured one-product error (-1 without one; probe_err may be NULL).
+ * The kernel rows of the fitting matrices always take three products; the FP64 path has none. */
+int soapgap_set_gap_terms(soapgap_handle* h, int32_t terms);
+int soapgap_gap_terms(const soapgap_handle* h, int32_t* terms, double* probe_err);
+
+/* Arithmetic peak of the current device, measured (the paper has no counterpart: this is
+ * the denominator of the roofline reported for the pair kernels and the FP64 path).
+ * kind SOAPGAP_PEAK_FP32_FMA or SOAPGAP_PEAK_FP64_FMA: a kernel of independent fused
+ * multiply-add chains on every SM (8 blocks of 256 threads per SM), timed with CUDA events
+ * on `stream` (a cudaStream_t, NULL = default stream), best of three launches after one
+ * warm-up.  Writes *tflops (TFLOP/s, one FMA = 2 flop) and, if sm_count is not NULL, the
+ * device's SM count.  Synchronises `stream`; runs for a few tens of milliseconds.
+ * SOAPGAP_E_INVALID_ARG for an unknown kind or a NULL tflops. */
+#define SOAPGAP_PEAK_FP32_FMA 0
+#define SOAPGAP_PEAK_FP64_FMA 1
+int soapgap_measure_alu_peak(int32_t kind, double* tflops, int32_t* sm_count, void* stream);
 
 /* Message describing the last error on h ("" if none); valid until the next call. */
 const char* soapgap_last_error(const soapgap_handle* h);

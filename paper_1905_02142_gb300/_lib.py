@@ -29,6 +29,8 @@ DESIGN_DK = 256
 N_DESIGN_STAGES = 4
 DESIGN_STAGES = ("descriptors", "kernel_rows", "jacobian", "force_rows")
 N_STAGES = 7
+PEAK_FP32_FMA = 0
+PEAK_FP64_FMA = 1
 STAGES = ("neighbours", "pair_forward", "power_spectrum", "gap_forward", "gap_backward",
           "pair_adjoint", "finish")
 
@@ -70,6 +72,10 @@ SIGNATURES = {
     "soapgap_export_pairs": (ctypes.c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
     "soapgap_gap_energy_noalloc": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int32,
                                                   c_int32, c_double, c_void_p, c_void_p]),
+    "soapgap_set_gap_terms": (ctypes.c_int, [c_void_p, c_int32]),
+    "soapgap_gap_terms": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_int32), ctypes.POINTER(c_double)]),
+    "soapgap_measure_alu_peak": (ctypes.c_int, [c_int32, ctypes.POINTER(c_double),
+                                                ctypes.POINTER(c_int32), c_void_p]),
     "soapgap_sync_status": (ctypes.c_int, [c_void_p, c_void_p]),
     "soapgap_autotune": (ctypes.c_int, [c_void_p, ctypes.POINTER(Batch), ctypes.POINTER(c_int32),
                                         c_void_p]),

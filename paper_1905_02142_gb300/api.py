@@ -216,6 +216,18 @@ class SoapGap:
         self._check(self.lib.soapgap_kernel_rows(self.h, _ptr(q), q.shape[0], _ptr(k), st))
         return k
 
+    def set_gap_terms(self, terms: int):
+        """FP16 products of the GAP energy on the tensor cores: 0 = chosen per model from
+        the measured one-product error on the sparse rows (default), 1 or 3 = forced."""
+        self._check(L.load().soapgap_set_gap_terms(self.h, int(terms)))
+
+    def gap_terms(self) -> tuple[int, float]:
+        """(products in use, measured one-product relative error of the sparse rows' energies)."""
+        t = ctypes.c_int32(0)
+        e = ctypes.c_double(0.0)
+        self._check(L.load().soapgap_gap_terms(self.h, ctypes.byref(t), ctypes.byref(e)))
+        return int(t.value), float(e.value)
+
     def set_skin(self, skin: float):
         """Verlet skin in A (0 disables neighbour-list reuse); see soapgap_set_skin."""
         self._check(self.lib.soapgap_set_skin(self.h, float(skin)))
@@ -325,6 +337,20 @@ class SoapGap:
         self._check(self.lib.soapgap_export_pairs(self.h, p, i.ctypes.data, j.ctypes.data,
                                                   s.ctypes.data))
         return i[:p], j[:p], s[:p]
+
+
+def measure_alu_peak(kind: str = "fp32", stream=None) -> tuple[float, int]:
+    """Measured FMA throughput of the current device in TFLOP/s and its SM count
+    (soapgap_measure_alu_peak; kind "fp32" or "fp64")."""
+    lib = L.load()
+    k = {"fp32": L.PEAK_FP32_FMA, "fp64": L.PEAK_FP64_FMA}[kind]
+    tf = ctypes.c_double(0.0)
+    sms = ctypes.c_int32(0)
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    rc = lib.soapgap_measure_alu_peak(k, ctypes.byref(tf), ctypes.byref(sms), st)
+    if rc != L.OK:
+        raise SoapGapError(rc, f"soapgap_measure_alu_peak({kind}) failed")
+    return float(tf.value), int(sms.value)
 
 
 class SoapGapEnergy(torch.autograd.Function):

@@ -16,7 +16,7 @@
 #include "soapmath.cuh"
 
 // --------------------------------------------------------------------- helpers
-long long sg_kernel_launches = 0;
+std::atomic<long long> sg_kernel_launches{0};
 
 int sg_cap_class(int nmax, int lmax) {
   int m = nmax > lmax ? nmax : lmax;
@@ -94,6 +94,8 @@ struct soapgap_handle {
   Buf tc_B, tc_BT, tc_cols, tc_qbar, tc_Ad;
   GapTcModel tcm{};
   Buf A16, nrm, uq, r_part, kp16;
+  int gap_terms_forced = 0;      // 0: chosen per model from the probe below; 1 or 3: forced
+  double gap_probe_err = -1.0;   // one-product error of the energy on the sparse rows
   // workspace
   Buf geom, atom_offs, atom_struct, atom_bin, atom_bin4, atom_slot, bin_count, bin_start, bin_atoms, binpos,
       atom_hi, atom_lo;
@@ -295,6 +297,8 @@ extern "C" int soapgap_descriptor_dim(const soapgap_handle* h, int32_t* dim) {
   return SOAPGAP_OK;
 }
 
+static std::string device_error_text(int code);
+
 extern "C" int soapgap_set_model(soapgap_handle* h, const double* q_sparse, const double* alpha,
                                  int32_t m, double zeta) {
   if (!h) return SOAPGAP_E_INVALID_ARG;
@@ -311,6 +315,7 @@ extern "C" int soapgap_set_model(soapgap_handle* h, const double* q_sparse, cons
   h->have_forward = false;
   h->M = 0;
   h->tcm = GapTcModel{};
+  h->gap_probe_err = -1.0;
   const size_t es = h->mixed ? sizeof(float) : sizeof(double);
   CK(h, ensure(h->qs, nq * es));
   CK(h, ensure(h->alpha, (size_t)m * es));
@@ -398,6 +403,42 @@ extern "C" int soapgap_set_model(soapgap_handle* h, const double* q_sparse, cons
     t.dpd = dpd;
     t.kd = (float)kd;
     t.Ad = (const __half*)h->tc_Ad.p;
+    t.terms = 3;
+    // How much does one FP16 product lose on this model?  The sparse rows, taken as atoms,
+    // are environments of the model's own kind: their local energies with one product and
+    // with three (~1e-7) give its relative error.  One product is used when that error is
+    // at most 1e-5, ten times below the 1e-4 energy bar of the mixed path.
+    const int tiles = sg_gap_tc_tiles(mp);
+    CK(h, ensure(h->A16, sizeof(__half) * (size_t)m * 3 * dp));
+    CK(h, ensure(h->nrm, sizeof(float) * (size_t)m));
+    CK(h, ensure(h->uq, sizeof(float) * (size_t)m));
+    CK(h, ensure(h->eps_part, sizeof(float) * (size_t)m * tiles));
+    CK(h, ensure(h->r_part, sizeof(float) * (size_t)m * tiles));
+    CK(h, ensure(h->err, sizeof(int)));
+    CK(h, cudaMemset(h->err.p, 0, sizeof(int)));
+    std::vector<double> e_terms[2];
+    for (int k = 0; k < 2; ++k) {
+      const int terms = k == 0 ? 1 : 3;
+      CK(h, sg_gap_tc_prepare((const float*)h->qs.p, m, D, dp, t.qbar, (__half*)h->A16.p, (float*)h->nrm.p,
+                              (float*)h->uq.p, terms, 0));
+      CK(h, sg_gap_tc_forward(t, terms, (const __half*)h->A16.p, (const float*)h->nrm.p, (const float*)h->uq.p,
+                              m, (float*)h->eps_part.p, (float*)h->r_part.p, nullptr, (int*)h->err.p, 0));
+      std::vector<float> part((size_t)m * tiles);
+      CK(h, cudaMemcpy(part.data(), h->eps_part.p, part.size() * sizeof(float), cudaMemcpyDeviceToHost));
+      e_terms[k].assign(m, 0.0);
+      for (int s = 0; s < m; ++s)
+        for (int j = 0; j < tiles; ++j) e_terms[k][s] += (double)part[(size_t)s * tiles + j];
+    }
+    int derr = 0;
+    CK(h, cudaMemcpy(&derr, h->err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (derr) return fail(h, SOAPGAP_E_CUDA, device_error_text(derr));
+    double num = 0.0, den = 0.0;
+    for (int s = 0; s < m; ++s) {
+      num += (e_terms[0][s] - e_terms[1][s]) * (e_terms[0][s] - e_terms[1][s]);
+      den += e_terms[1][s] * e_terms[1][s];
+    }
+    h->gap_probe_err = den > 0 ? std::sqrt(num / den) : (num > 0 ? 1.0 : 0.0);
+    t.terms = h->gap_terms_forced ? h->gap_terms_forced : (h->gap_probe_err <= 1e-5 ? 1 : 3);
   } else {
     CK(h, cudaMemcpy(h->qs.p, q_sparse, nq * es, cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->alpha.p, alpha, (size_t)m * es, cudaMemcpyHostToDevice));
@@ -791,14 +832,14 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     if constexpr (sizeof(T) == 4) {
       // tensor cores: centred, norm-scaled FP16 split operands (see gap_tc.cu)
       const GapTcModel& tm = h->tcm;
-      ENS(h, h->A16, sizeof(__half) * N1 * 3 * tm.dp);
+      ENS(h, h->A16, sizeof(__half) * N1 * tm.terms * tm.dp);
       ENS(h, h->nrm, sizeof(float) * N1);
       ENS(h, h->uq, sizeof(float) * N1);
       ENS(h, h->r_part, sizeof(float) * N1 * tiles);
       if (want_grad) ENS(h, h->kp16, sizeof(__half) * N1 * tm.mp);
       CK(h, sg_gap_tc_prepare((const float*)h->q.p, N, D, tm.dp, tm.qbar, (__half*)h->A16.p,
-                              (float*)h->nrm.p, (float*)h->uq.p, st));
-      CK(h, sg_gap_tc_forward(tm, (const __half*)h->A16.p, (const float*)h->nrm.p, (const float*)h->uq.p, N,
+                              (float*)h->nrm.p, (float*)h->uq.p, tm.terms, st));
+      CK(h, sg_gap_tc_forward(tm, tm.terms, (const __half*)h->A16.p, (const float*)h->nrm.p, (const float*)h->uq.p, N,
                               (float*)h->eps_part.p, (float*)h->r_part.p,
                               want_grad ? (__half*)h->kp16.p : nullptr, (int*)h->err.p, st));
     } else {
@@ -1135,6 +1176,24 @@ extern "C" int soapgap_autotune(soapgap_handle* h, const soapgap_batch* batch, i
   return SOAPGAP_OK;
 }
 
+extern "C" int soapgap_set_gap_terms(soapgap_handle* h, int32_t terms) {
+  if (!h) return SOAPGAP_E_INVALID_ARG;
+  if (terms != 0 && terms != 1 && terms != 3)
+    return fail(h, SOAPGAP_E_INVALID_ARG, "set_gap_terms: terms must be 0 (automatic), 1 or 3");
+  h->gap_terms_forced = terms;
+  if (h->has_model && h->mixed)
+    h->tcm.terms = terms ? terms : (h->gap_probe_err >= 0 && h->gap_probe_err <= 1e-5 ? 1 : 3);
+  h->msg.clear();
+  return SOAPGAP_OK;
+}
+
+extern "C" int soapgap_gap_terms(const soapgap_handle* h, int32_t* terms, double* probe_err) {
+  if (!h || !terms) return SOAPGAP_E_INVALID_ARG;
+  *terms = (h->has_model && h->mixed) ? h->tcm.terms : 0;
+  if (probe_err) *probe_err = (h->has_model && h->mixed) ? h->gap_probe_err : -1.0;
+  return SOAPGAP_OK;
+}
+
 extern "C" int soapgap_set_skin(soapgap_handle* h, double skin) {
   if (!h) return SOAPGAP_E_INVALID_ARG;
   if (!(skin >= 0.0) || !std::isfinite(skin)) return fail(h, SOAPGAP_E_INVALID_ARG, "skin must be >= 0");
@@ -1204,7 +1263,7 @@ static int design(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, voi
       ENS(h, h->nrm, sizeof(float) * N1);
       ENS(h, h->uq, sizeof(float) * N1);
       CK(h, sg_gap_tc_prepare((const float*)h->q.p, N, D, tm.dp, tm.qbar, (__half*)h->A16.p, (float*)h->nrm.p,
-                              (float*)h->uq.p, st));
+                              (float*)h->uq.p, 3, st));
       CK(h, sg_tc_kernel_rows(tm, (const __half*)h->A16.p, (const float*)h->nrm.p, (const float*)h->uq.p, N, M,
                               (const float*)h->pnorm.p, kbuf, wv, (int*)h->err.p, st));
     } else {
@@ -1330,7 +1389,7 @@ extern "C" int soapgap_kernel_rows(soapgap_handle* h, const void* q, int32_t n, 
     CK(h, ensure(h->nrm, sizeof(float) * (size_t)n));
     CK(h, ensure(h->uq, sizeof(float) * (size_t)n));
     CK(h, sg_gap_tc_prepare((const float*)q, n, h->D, tm.dp, tm.qbar, (__half*)h->A16.p, (float*)h->nrm.p,
-                            (float*)h->uq.p, st));
+                            (float*)h->uq.p, 3, st));
     CK(h, sg_tc_kernel_rows(tm, (const __half*)h->A16.p, (const float*)h->nrm.p, (const float*)h->uq.p, n, h->M,
                             nullptr, (float*)k, nullptr, (int*)h->err.p, st));
   } else {

@@ -9,9 +9,12 @@
 // ~6e-2 of it and plain FP16 ~5e-3.  The products are therefore split as
 //   q = qbar + n u,  qbar = mean of the sparse rows, n = |q - qbar|, |u| = 1,
 //   q_i.q_s = qbar.qbar + qbar.(q_i - qbar) + qbar.(q_s - qbar) + n_i n_s (u_i . u_s),
-// with the rank-one terms in FP32 and u_i.u_s on the tensor cores as hi*hi + hi*lo + lo*hi
-// of an FP16 hi/lo split (one GEMM over K = 3 D: A = [hi|hi|lo], B = [hi|lo|hi]); relative
-// error ~2e-7 on eps.  The backward product needs less: g_i = r_i qbar + kappa kp'_i U with
+// with the rank-one terms in FP32 and only u_i.u_s on the tensor cores, either as one FP16
+// product hi*hi (K = D) or as the split hi*hi + hi*lo + lo*hi (one GEMM over K = 3 D:
+// A = [hi|hi|lo], B = [hi|lo|hi]; relative error ~1e-7 on eps).  How much one product loses
+// depends on the model (a few 1e-6 on carbon-like boxes with thousands of sparse rows, above
+// 1e-4 with a dozen): the library measures it per model and picks the number of products.
+// The backward product needs less: g_i = r_i qbar + kappa kp'_i U with
 // r_i = sum_s zeta alpha_s S^(zeta-1) in FP32, kp'_is = zeta alpha_s n_s S^(zeta-1) / kappa in
 // FP16 and U the unit sparse rows in FP16 (single pass).
 #include <cuda.h>
@@ -162,7 +165,7 @@ struct EpiGapFwd {
   }
   // S^(zeta-1) for one output, zeta fixed at compile time (Z > 0) or general (Z = 0)
   template <int Z>
-  __device__ __forceinline__ void run(int col0, const uint32_t* v, __half2* out) {
+  __device__ __forceinline__ void run(int col0, const uint32_t* v, uint32_t* out) {
 #pragma unroll
     for (int j = 0; j < 32; j += 2) {
       float kv[2];
@@ -175,12 +178,13 @@ struct EpiGapFwd {
         r = fmaf(zeta * c.z, sz1, r);
         kv[h] = c.w * sz1;
       }
-      out[j / 2] = __floats2half2_rn(kv[0], kv[1]);
+      const __half2 h2 = __floats2half2_rn(kv[0], kv[1]);
+      out[j / 2] = *reinterpret_cast<const uint32_t*>(&h2);
     }
   }
   __device__ void apply(int row, int col0, const uint32_t* v) {
     if (row >= rows) return;
-    __align__(16) __half2 out[16];
+    uint32_t out[16];   // 32 FP16 kernel derivatives, packed in pairs (registers)
     switch (izeta) {
       case 1: run<1>(col0, v, out); break;
       case 2: run<2>(col0, v, out); break;
@@ -190,9 +194,8 @@ struct EpiGapFwd {
     }
     if (kp) {
       uint4* dst = reinterpret_cast<uint4*>(kp + (size_t)row * ld_kp + col0);
-      const uint4* src = reinterpret_cast<const uint4*>(out);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) dst[k] = src[k];
+      for (int k = 0; k < 4; ++k) dst[k] = make_uint4(out[4 * k], out[4 * k + 1], out[4 * k + 2], out[4 * k + 3]);
     }
   }
   __device__ void end(int row, int slot) {
@@ -530,13 +533,15 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int box_rows
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// C = A B^T over K = k; lda: row stride of A in elements (k when 0)
+// C = A B^T over K = k; lda, ldb: row strides of A and B in elements (k when 0)
 template <int BN, int STAGES, int EPI_WARPS, bool MFAST = false, class Epi>
 cudaError_t launch_gemm(const void* A, int a_rows, const void* B, int b_rows, int k, Epi epi, int* err,
-                        cudaStream_t st, int lda = 0) {
+                        cudaStream_t st, int lda = 0, int ldb = 0) {
   if (k % BK != 0 || a_rows <= 0 || b_rows <= 0) return cudaErrorInvalidValue;
+  if ((lda > 0 && lda < k) || (ldb > 0 && ldb < k)) return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
-  if (!make_map(&ma, A, a_rows, k, BM, lda) || !make_map(&mb, B, b_rows, k, BN)) return cudaErrorInvalidValue;
+  if (!make_map(&ma, A, a_rows, k, BM, lda) || !make_map(&mb, B, b_rows, k, BN, ldb))
+    return cudaErrorInvalidValue;
   auto kern = tc_gemm_kernel<BN, STAGES, EPI_WARPS, Epi, MFAST>;
   constexpr size_t smem = smem_bytes<BN, STAGES>();
   cudaError_t e = sg_set_smem<tc_gemm_kernel<BN, STAGES, EPI_WARPS, Epi, MFAST>>(smem);
@@ -553,7 +558,9 @@ cudaError_t launch_gemm(const void* A, int a_rows, const void* B, int b_rows, in
 }
 
 // ------------------------------------------------------------------ operand preparation
-// one warp per atom: u = (q - qbar)/|q - qbar| as FP16 hi/lo, A row = [hi | hi | lo]
+// one warp per atom: u = (q - qbar)/|q - qbar| in FP16, A row = [hi] (TERMS = 1, row
+// stride dp) or the split [hi | hi | lo] (TERMS = 3, row stride 3 dp)
+template <int TERMS>
 __global__ void prep_atoms_kernel(const float* __restrict__ q, int n, int d, int dp,
                                   const float* __restrict__ qbar, __half* A, float* nrm, float* uq) {
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -570,14 +577,15 @@ __global__ void prep_atoms_kernel(const float* __restrict__ q, int n, int d, int
   dq = warp_sum(dq);
   const float nn = sqrtf(ss);
   const float inv = nn > 0.f ? 1.f / nn : 0.f;
-  __half* row = A + (size_t)i * 3 * dp;
+  __half* row = A + (size_t)i * TERMS * dp;
   for (int k = lane; k < dp; k += 32) {
     const float uk = k < d ? (qi[k] - qbar[k]) * inv : 0.f;
     const __half hi = __float2half_rn(uk);
-    const __half lo = __float2half_rn(uk - __half2float(hi));
     row[k] = hi;
-    row[dp + k] = hi;
-    row[2 * dp + k] = lo;
+    if (TERMS == 3) {
+      row[dp + k] = hi;
+      row[2 * dp + k] = __float2half_rn(uk - __half2float(hi));
+    }
   }
   if (lane == 0) {
     nrm[i] = nn;
@@ -591,16 +599,23 @@ __global__ void prep_atoms_kernel(const float* __restrict__ q, int n, int d, int
 int sg_gap_tc_tiles(int mp) { return (mp + 255) / 256 * 2; }
 
 cudaError_t sg_gap_tc_prepare(const float* q, int n, int d, int dp, const float* qbar, __half* A, float* nrm,
-                              float* uq, cudaStream_t st) {
+                              float* uq, int terms, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  prep_atoms_kernel<<<(n * 32 + 127) / 128, 128, 0, st>>>(q, n, d, dp, qbar, A, nrm, uq);
+  if (terms == 1)
+    prep_atoms_kernel<1><<<(n * 32 + 127) / 128, 128, 0, st>>>(q, n, d, dp, qbar, A, nrm, uq);
+  else if (terms == 3)
+    prep_atoms_kernel<3><<<(n * 32 + 127) / 128, 128, 0, st>>>(q, n, d, dp, qbar, A, nrm, uq);
+  else
+    return cudaErrorInvalidValue;
   ++sg_kernel_launches;
   return cudaGetLastError();
 }
 
-cudaError_t sg_gap_tc_forward(const GapTcModel& md, const __half* A, const float* nrm, const float* uq, int n,
-                              float* eps_part, float* r_part, __half* kp, int* err, cudaStream_t st) {
+cudaError_t sg_gap_tc_forward(const GapTcModel& md, int terms, const __half* A, const float* nrm,
+                              const float* uq, int n, float* eps_part, float* r_part, __half* kp, int* err,
+                              cudaStream_t st) {
   if (n == 0) return cudaSuccess;
+  if (terms != 1 && terms != 3) return cudaErrorInvalidValue;
   EpiGapFwd e{};
   e.rows = n;
   e.ld_kp = md.mp;
@@ -613,6 +628,9 @@ cudaError_t sg_gap_tc_forward(const GapTcModel& md, const __half* A, const float
   e.eps_part = eps_part;
   e.r_part = r_part;
   e.kp = kp;
+  // one FP16 product hi.hi: A rows [hi] against the first dp columns of the sparse rows
+  // [hi | lo | hi]; three: A rows [hi | hi | lo] against the whole rows
+  if (terms == 1) return launch_gemm<256, 4, 8>(A, n, md.B, md.mp, md.dp, e, err, st, md.dp, 3 * md.dp);
   return launch_gemm<256, 4, 8>(A, n, md.B, md.mp, 3 * md.dp, e, err, st);
 }
 

@@ -4,6 +4,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <atomic>
 #include "common.cuh"
 
 // Raise kernel Kern's dynamic shared-memory limit, once per device and size: the attribute
@@ -22,7 +24,7 @@ inline cudaError_t sg_set_smem(size_t bytes) {
 }
 
 // Kernels launched by this library since load (read around a call to count its launches).
-extern long long sg_kernel_launches;
+extern std::atomic<long long> sg_kernel_launches;
 
 // Compile-time capacity class of the pair kernels: (n_max, l_max) <= (NC, LC).
 int sg_cap_class(int nmax, int lmax);            // 0..3 -> (6,6) (8,8) (10,10) (12,12)
@@ -162,12 +164,17 @@ struct GapTcModel {
   int dpd;                // D + 2 padded to 64
   float kd;               // power of two: max |kd (q_s - qbar)| in [1, 2)
   const __half* Ad;       // [mp][dpd]
+  int terms;              // FP16 products of the energy: 1 (hi.hi) or 3 (hi.hi + hi.lo + lo.hi)
 };
 int sg_gap_tc_tiles(int m);
+// A rows of the atoms: terms = 1 gives [hi] (row stride dp; the energy and its gradient),
+// terms = 3 the split [hi | hi | lo] (row stride 3 dp; kernel rows of the fitting matrices)
 cudaError_t sg_gap_tc_prepare(const float* q, int n, int d, int dp, const float* qbar, __half* A,
-                              float* nrm, float* uq, cudaStream_t st);
-cudaError_t sg_gap_tc_forward(const GapTcModel& md, const __half* A, const float* nrm, const float* uq,
-                              int n, float* eps_part, float* r_part, __half* kp, int* err, cudaStream_t st);
+                              float* nrm, float* uq, int terms, cudaStream_t st);
+// energy epilogue over `terms` FP16 products (1 or 3): A from sg_gap_tc_prepare with the same terms
+cudaError_t sg_gap_tc_forward(const GapTcModel& md, int terms, const __half* A, const float* nrm,
+                              const float* uq, int n, float* eps_part, float* r_part, __half* kp, int* err,
+                              cudaStream_t st);
 cudaError_t sg_gap_tc_backward(const GapTcModel& md, const __half* kp, const float* r_part, int n,
                                float* g, int* err, cudaStream_t st);
 cudaError_t sg_tc_gemm_store(const __half* A, int m, const __half* B, int n, int k, float* C, int* err,

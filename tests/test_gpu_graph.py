@@ -138,3 +138,36 @@ def test_autotune_keeps_results(batched):
     assert torch.equal(after["forces"], before["forces"])
     assert torch.equal(after["e_struct"], before["e_struct"])
     assert torch.allclose(after["virial"], before["virial"], rtol=1e-6, atol=1e-9)
+
+
+def test_batched_graph_against_oracle(batched):
+    """The 256-structure batch with the oracle's own sparse set (1000 environments, zeta 2),
+    replayed from a captured graph: four structures of different sizes (the smallest, full of
+    self-images, and three up to ~200 atoms) against the oracle's energies, forces and virial."""
+    from oracle import Params, gap
+    from paper_1905_02142_gb300.api import CapturedEvaluation, SoapGap, Structures
+    from parity_helpers import oracle_W, rel_all, sparse_model
+    w, batch = batched
+    P, qs, al, zeta = sparse_model("batch256_n8l8")
+    model = SoapGap.from_dict(w.params(), precision="mixed")
+    model.set_model(qs, al, zeta)
+    s = Structures.from_batch(batch)
+    cap = CapturedEvaluation(model, s, **OUT)
+    for _ in range(2):
+        out = cap.replay()
+    model.sync_status()
+    sizes = np.diff(batch.atom_offs)
+    order = np.argsort(sizes, kind="stable")
+    small = [t for t in order if sizes[t] <= 200]
+    picks = [small[0], small[len(small) // 3], small[2 * len(small) // 3], small[-1]]
+    W = oracle_W(P.n_max, P.r_cut, P.sigma_r0)
+    for t in picks:
+        a, b = batch.atom_offs[t], batch.atom_offs[t + 1]
+        one = synth.concat([batch.structure(t)])
+        ref = gap.evaluate(one, P, qs, al, zeta, W=W)
+        e_err = abs(float(out["e_struct"][t]) - ref["e_struct"][0]) / abs(ref["e_struct"][0])
+        f_err = rel_all(out["forces"][a:b].cpu().numpy(), ref["forces"])
+        v_err = rel_all(out["virial"][t].cpu().numpy().reshape(1, 9), ref["virial"].reshape(1, 9))
+        print(f"PARITY batched graph structure {t} ({b - a} atoms): E {e_err:.2e} F {f_err:.2e} "
+              f"W {v_err:.2e}")
+        assert e_err < 1e-4 and f_err < 1e-3 and v_err < 1e-3

@@ -38,19 +38,28 @@ def test_noalloc_energies_match_regular_entry_point_twice(lib):
     qs_d = torch.as_tensor(qs, dtype=torch.float32, device="cuda").contiguous()
     al_d = torch.as_tensor(al, dtype=torch.float32, device="cuda").contiguous()
     st = torch.cuda.current_stream().cuda_stream
+    # descriptors and regular energies of two boxes first, so that no torch or handle
+    # allocation falls between the two allocation-free calls below
+    cases = []
     for seed, n_atoms in ((61, 48), (62, 20)):   # two calls in a row, different sizes
         batch = synth.concat([synth.random_box(n_atoms, side=7.0, dmin=1.2, seed=seed)])
         out = model.compute(Structures.from_batch(batch), desc=True, energy=True)
-        q = out["q"]
         e = torch.full((n_atoms,), float("nan"), dtype=torch.float32, device="cuda")
+        cases.append((n_atoms, out["q"], out["e_atom"].double().cpu().numpy(), e))
+    torch.cuda.synchronize()
+    free = []
+    for n_atoms, q, ref, e in cases:
         rc = lib.soapgap_gap_energy_noalloc(q.data_ptr(), qs_d.data_ptr(), al_d.data_ptr(),
                                             n_atoms, len(qs), model.dim, zeta, e.data_ptr(), st)
         assert rc == L.OK
         torch.cuda.synchronize()
-        ref = out["e_atom"].double().cpu().numpy()
+        free.append(torch.cuda.mem_get_info()[0])
         got = e.double().cpu().numpy()
         assert np.all(np.isfinite(got))
         assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-4
+    # the first call may load the library's module; the second one must leave the
+    # device's free memory exactly as it was
+    assert free[1] == free[0]
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
@@ -59,6 +68,10 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
     p = dummy.data_ptr()
     # 4194304 floats of scratch: 65537 atoms x 64 tiles (m = 4096) is one row too many
     rc = lib.soapgap_gap_energy_noalloc(p, p, p, 65537, 4096, 8, 2.0, p, None)
+    assert rc == L.E_CAPACITY
+    # one sparse tile (m <= 64) keeps the scratch small, but 4194304 atoms need 65536
+    # block rows of 64, one more than a launch grid holds
+    rc = lib.soapgap_gap_energy_noalloc(p, p, p, 4194304, 64, 8, 2.0, p, None)
     assert rc == L.E_CAPACITY
     rc = lib.soapgap_gap_energy_noalloc(p, p, p, 4, 0, 8, 2.0, p, None)
     assert rc == L.E_INVALID_ARG
