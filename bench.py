@@ -39,6 +39,9 @@ STATED_ERR = {"p_rel": 1e-5, "energy_rel": 1e-4, "forces_rms_rel": 1e-3,
               "fp64_p_rel": "max(1e-11, 4 eps sqrt(cond S))",
               "fp64_energy_rel": "max(1e-10, 0.1 eps sqrt(cond S))",
               "fp64_forces_rms_rel": "max(1e-9, 2 eps sqrt(cond S))"}
+# tile plans of earlier autotuner runs on this machine (soapgap_autotune / soapgap_set_plan)
+PLAN_CACHE = os.environ.get("SOAPGAP_PLAN_CACHE",
+                            os.path.join(os.path.expanduser("~"), ".cache", "soapgap", "plans.json"))
 FP32_PEAK_NOTE = "FP32 FMA measured (soapgap_measure_alu_peak: independent FMA chains on every SM)"
 FP64_PEAK_NOTE = "FP64 FMA measured (soapgap_measure_alu_peak: independent FMA chains on every SM)"
 
@@ -528,11 +531,11 @@ def run_batched(args, dev, flush, stream):
     qs, al = sparse_set_from_library(SoapGap, wb, pb, dev)
     mb = SoapGap.from_dict(pb, precision="mixed")
     mb.set_model(qs, al, wb.zeta)
-    warps = mb.autotune(sb)
+    plan_b = mb.autotune(sb, cache=PLAN_CACHE)
     g = timed_graph(mb, sb, flush, stream, args.warmup, args.steps)
     g["value"] = bb.n_atoms / (g["ms_per_step"] / 1e3)
     g.update({"workload": wb.name, "description": wb.description, "atoms": bb.n_atoms,
-              "structures": bb.n_struct, "pairs": mb.pair_count(), "autotuned_adjoint_warps": warps})
+              "structures": bb.n_struct, "pairs": mb.pair_count(), "tile_plan": plan_b})
     mb.close()
     return g
 
@@ -658,7 +661,7 @@ def run_ours(args, rank, world, local_rank):
     qs, al = sparse_set_from_library(SoapGap, w, params, dev)
     model = SoapGap.from_dict(params, precision="mixed")
     model.set_model(qs, al, w.zeta)
-    tuned_warps = model.autotune(s)
+    tuned = model.autotune(s, cache=PLAN_CACHE)
     gap_terms = model.gap_terms()
     fp32_peak, sm_count = measure_alu_peak("fp32")
     fp64_peak, _ = measure_alu_peak("fp64")
@@ -788,7 +791,7 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "description": w.description, "atoms": n,
                    "pairs": n_pairs, "sparse": w.n_sparse, "l2": "flushed between steps (256 MB write)",
-                   "autotuned_adjoint_warps": tuned_warps,
+                   "tile_plan": tuned,
                    "gap_fp16_products": gap_terms[0], "gap_one_product_probe_err": gap_terms[1],
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "stated_err": STATED_ERR,

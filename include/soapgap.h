@@ -194,13 +194,31 @@ int soapgap_compute(soapgap_handle* h, const soapgap_batch* batch, uint32_t flag
  * non-finite position, coincident atoms) or SOAPGAP_E_CUDA; soapgap_last_error has the text. */
 int soapgap_sync_status(soapgap_handle* h, void* stream);
 
-/* Autotuner: runs one synchronous ENERGY|FORCES|VIRIAL evaluation of `batch` (device
- * pos/species, as for soapgap_compute; it also sizes the workspace for asynchronous calls),
- * then times the tensor-core adjoint kernel with 2, 3 and 4 warps (pair batches) per block
- * on it and keeps the fastest for this basis class, species count and pairs per atom.
- * Later calls on the handle with matching problems use it.  *choice (may be NULL) receives
- * the warps chosen (0 on the FP64 path, which has nothing to tune).  Synchronises. */
-int soapgap_autotune(soapgap_handle* h, const soapgap_batch* batch, int32_t* choice, void* stream);
+/* Autotuner (the paper has no counterpart: it picks launch shapes of this library's kernels).
+ * Runs one synchronous ENERGY|FORCES|VIRIAL evaluation of `batch` (device pos/species, as
+ * for soapgap_compute; it also sizes the workspace for asynchronous calls), then times on
+ * it, stage by stage, the candidates of a tile plan of SOAPGAP_PLAN_LEN entries:
+ *   plan[0]  warps (32-pair batches) per block of the tensor-core adjoint: 2, 3 or 4
+ *   plan[1]  tile configuration of the GAP forward product (columns per tile, pipeline
+ *            stages, epilogue warps): 0 = (256, 4, 8), 1 = (128, 6, 4), 2 = (128, 6, 8)
+ *   plan[2]  the same for the GAP backward product: 0 = (224, 5, 4), 1 = (128, 6, 4),
+ *            2 = (192, 5, 4), 3 = (256, 4, 4)
+ * and keeps the fastest of each for the batch's problem class (basis class, species count,
+ * 32-pair batches per atom, power of two of the atom count).  Later calls on the handle
+ * in that class use the plan; classes without one use {0 (by pairs per atom), 0, 0}.  The
+ * results do not depend on the plan beyond the order of floating-point sums.  `plan` (may
+ * be NULL) receives the choice ({0, 0, 0} on the FP64 path, which has nothing to tune).
+ * Synchronises; afterwards soapgap_backward needs a new evaluation. */
+#define SOAPGAP_PLAN_LEN 3
+int soapgap_autotune(soapgap_handle* h, const soapgap_batch* batch, int32_t* plan, void* stream);
+
+/* Tile plan of the batch's problem class: soapgap_get_plan writes it to plan[SOAPGAP_PLAN_LEN]
+ * (the defaults {0, 0, 0} if none was tuned or set); soapgap_set_plan installs one (e.g. read
+ * back from a cache of earlier tuning runs).  Both need a synchronous evaluation of this
+ * batch on the handle first (its pair count fixes the class): SOAPGAP_E_STATE otherwise;
+ * SOAPGAP_E_INVALID_ARG for an entry out of range (plan[0] may also be 0). */
+int soapgap_get_plan(soapgap_handle* h, const soapgap_batch* batch, int32_t* plan);
+int soapgap_set_plan(soapgap_handle* h, const soapgap_batch* batch, const int32_t* plan);
 
 /* Verlet skin (neighbour-list reuse).  skin >= 0 (A); 0 (the default) builds the list at
  * every call.  With skin > 0 the list holds all pairs within r_cut + skin and is rebuilt only

@@ -29,6 +29,7 @@ DESIGN_DK = 256
 N_DESIGN_STAGES = 4
 DESIGN_STAGES = ("descriptors", "kernel_rows", "jacobian", "force_rows")
 N_STAGES = 7
+PLAN_LEN = 3
 PEAK_FP32_FMA = 0
 PEAK_FP64_FMA = 1
 STAGES = ("neighbours", "pair_forward", "power_spectrum", "gap_forward", "gap_backward",
@@ -77,8 +78,9 @@ SIGNATURES = {
     "soapgap_measure_alu_peak": (ctypes.c_int, [c_int32, ctypes.POINTER(c_double),
                                                 ctypes.POINTER(c_int32), c_void_p]),
     "soapgap_sync_status": (ctypes.c_int, [c_void_p, c_void_p]),
-    "soapgap_autotune": (ctypes.c_int, [c_void_p, ctypes.POINTER(Batch), ctypes.POINTER(c_int32),
-                                        c_void_p]),
+    "soapgap_autotune": (ctypes.c_int, [c_void_p, ctypes.POINTER(Batch), c_void_p, c_void_p]),
+    "soapgap_get_plan": (ctypes.c_int, [c_void_p, ctypes.POINTER(Batch), c_void_p]),
+    "soapgap_set_plan": (ctypes.c_int, [c_void_p, ctypes.POINTER(Batch), c_void_p]),
     "soapgap_set_skin": (ctypes.c_int, [c_void_p, c_double]),
     "soapgap_last_rebuild": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_int32)]),
     "soapgap_verlet": (ctypes.c_int, [c_void_p, ctypes.POINTER(Batch), c_void_p, c_void_p, c_void_p,

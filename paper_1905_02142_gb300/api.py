@@ -6,6 +6,9 @@ passes pointers (PyTorch CUDA tensors provide device memory and the stream).
 from __future__ import annotations
 
 import ctypes
+import json
+import os
+import tempfile
 
 import numpy as np
 import torch
@@ -257,14 +260,76 @@ class SoapGap:
         st = (stream or torch.cuda.current_stream()).cuda_stream
         self._check(self.lib.soapgap_sync_status(self.h, st))
 
-    def autotune(self, s: Structures, stream=None) -> int:
-        """Time the adjoint's block shapes on this batch and keep the fastest (see
-        soapgap_autotune); returns the warps per block chosen (0 on the FP64 path)."""
+    PLAN_KEYS = ("adjoint_warps", "gap_forward", "gap_backward")
+
+    def _plan_cache_key(self, s: Structures) -> str:
+        """Problem class of a batch as the library tunes it (after an evaluation of it), with
+        the device and the model sizes that set the GAP products' shapes."""
+        p = self.params
+        n, nsp = s.n_atoms, p.n_species
+        per_seg = self.pair_count() / max(1, n * nsp)
+        batches = nsp * int(np.ceil(per_seg / 32.0))
+        lg = int(np.ceil(np.log2(max(n, 1))))
+        terms = self.gap_terms()[0] if self.precision == "mixed" else 0
+        dev = torch.cuda.get_device_name(s.pos.device)
+        return (f"{dev}|{self.precision}|n{p.n_max}l{p.l_max}sp{nsp}|M{self.m}|terms{terms}"
+                f"|batches{batches}|lgN{lg}")
+
+    def autotune(self, s: Structures, stream=None, cache: str | None = None) -> dict:
+        """Pick the tile plan of this batch's problem class (soapgap_autotune): warps per
+        block of the adjoint and the tile configurations of the two GAP products.
+
+        cache: path of a JSON file of earlier choices, keyed by device, precision, basis,
+        species, model size, FP16 products and problem class.  A plan found there is
+        installed without timing (soapgap_set_plan); a new one is timed and added.
+        Returns {"adjoint_warps", "gap_forward", "gap_backward", "cached"}."""
         st = (stream or torch.cuda.current_stream(s.pos.device)).cuda_stream
         b = s.c_batch()
-        w = ctypes.c_int32()
-        self._check(self.lib.soapgap_autotune(self.h, ctypes.byref(b), ctypes.byref(w), st))
-        return int(w.value)
+        key = None
+        if cache:
+            self.compute(s, energy=True, forces=True, stream=stream)
+            key = self._plan_cache_key(s)
+            try:
+                with open(cache) as f:
+                    known = json.load(f)
+            except (OSError, ValueError):
+                known = {}
+            if key in known:
+                vals = [int(known[key][k]) for k in self.PLAN_KEYS]
+                arr = (ctypes.c_int32 * L.PLAN_LEN)(*vals)
+                self._check(self.lib.soapgap_set_plan(self.h, ctypes.byref(b), arr))
+                return dict(zip(self.PLAN_KEYS, vals), cached=True)
+        arr = (ctypes.c_int32 * L.PLAN_LEN)()
+        self._check(self.lib.soapgap_autotune(self.h, ctypes.byref(b), arr, st))
+        plan = dict(zip(self.PLAN_KEYS, [int(x) for x in arr]))
+        if cache and self.precision == "mixed":
+            try:
+                with open(cache) as f:
+                    known = json.load(f)
+            except (OSError, ValueError):
+                known = {}
+            known[key] = plan
+            d = os.path.dirname(os.path.abspath(cache))
+            os.makedirs(d, exist_ok=True)
+            fd, tmp = tempfile.mkstemp(dir=d, suffix=".json")
+            with os.fdopen(fd, "w") as f:
+                json.dump(known, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return dict(plan, cached=False)
+
+    def set_plan(self, s: Structures, plan: dict):
+        """Install a tile plan for this batch's problem class (soapgap_set_plan; the batch
+        must have been evaluated on this handle)."""
+        b = s.c_batch()
+        arr = (ctypes.c_int32 * L.PLAN_LEN)(*[int(plan[k]) for k in self.PLAN_KEYS])
+        self._check(self.lib.soapgap_set_plan(self.h, ctypes.byref(b), arr))
+
+    def plan(self, s: Structures) -> dict:
+        """The tile plan in use for this batch's problem class (soapgap_get_plan)."""
+        b = s.c_batch()
+        arr = (ctypes.c_int32 * L.PLAN_LEN)()
+        self._check(self.lib.soapgap_get_plan(self.h, ctypes.byref(b), arr))
+        return dict(zip(self.PLAN_KEYS, [int(x) for x in arr]))
 
     def backward(self, s: Structures, dE_dEstruct: torch.Tensor, virial=False, stream=None):
         """Gradient of sum_s w_s E_s with respect to positions (after an energy evaluation)."""

@@ -124,7 +124,10 @@ struct soapgap_handle {
   int64_t* h_offs = nullptr;      // pinned staging of atom_offs (read by captured copies)
   size_t h_offs_cap = 0;
   bool async_call = false;        // current call must not allocate or synchronise
-  std::map<long long, int> adj_warps;  // autotuned adjoint block shape per problem class
+  // tile plan per problem class (soapgap_autotune / soapgap_set_plan): adjoint warps per
+  // block (0: by pairs per atom) and the configurations of the two GAP products
+  struct TilePlan { int adj_warps = 0, gap_fwd = 0, gap_bwd = 0; };
+  std::map<long long, TilePlan> plans;
   StructGeom* h_geom = nullptr;   // pinned staging
   size_t h_geom_cap = 0;
   double* h_w = nullptr;
@@ -408,7 +411,7 @@ extern "C" int soapgap_set_model(soapgap_handle* h, const double* q_sparse, cons
     // are environments of the model's own kind: their local energies with one product and
     // with three (~1e-7) give its relative error.  One product is used when that error is
     // at most 1e-5, ten times below the 1e-4 energy bar of the mixed path.
-    const int tiles = sg_gap_tc_tiles(mp);
+    const int tiles = sg_gap_tc_tiles(mp, t.fwd_cfg);
     CK(h, ensure(h->A16, sizeof(__half) * (size_t)m * 3 * dp));
     CK(h, ensure(h->nrm, sizeof(float) * (size_t)m));
     CK(h, ensure(h->uq, sizeof(float) * (size_t)m));
@@ -548,11 +551,19 @@ static std::string device_error_text(int code) {
   return m;
 }
 
-// tuning-table key of the adjoint: basis class, species, 32-pair batches per atom
-static long long adj_key(const soapgap_handle* h, int n_atoms, long long n_pairs) {
+// tuning-table key of a problem class: basis class, species, 32-pair batches per atom (the
+// adjoint's shape) and the power of two of the atom count (the GAP products' row tiles)
+static long long plan_key(const soapgap_handle* h, int n_atoms, long long n_pairs) {
   const int nsp = h->prm.n_species;
   const int batches = std::min(63, sg_adj_batches_per_atom(n_pairs, n_atoms, nsp));
-  return ((long long)h->cls * 16 + nsp) * 64 + batches;
+  int lg = 0;
+  while (lg < 31 && (1LL << lg) < (long long)n_atoms) ++lg;
+  return (((long long)h->cls * 16 + nsp) * 64 + batches) * 32 + lg;
+}
+
+static soapgap_handle::TilePlan plan_for(const soapgap_handle* h, int n_atoms) {
+  auto it = h->plans.find(plan_key(h, n_atoms, h->last_pairs));
+  return it == h->plans.end() ? soapgap_handle::TilePlan{} : it->second;
 }
 
 // arguments of the adjoint pair kernel from the handle's workspace (after a forward pass)
@@ -562,8 +573,7 @@ static AdjArgs<T> adj_args(soapgap_handle* h, int N, const int* species) {
   aa.n_atoms = N; aa.nsp = h->prm.n_species; aa.nmax = h->prm.n_max; aa.lmax = h->prm.l_max;
   aa.dim = h->D;
   aa.n_pairs = h->last_pairs;
-  auto it = h->adj_warps.find(adj_key(h, N, h->last_pairs));
-  aa.warps = it == h->adj_warps.end() ? 0 : it->second;
+  aa.warps = plan_for(h, N).adj_warps;
   aa.species = species; aa.atom_struct = (const int*)h->atom_struct.p;
   aa.struct_w = (const double*)h->struct_w.p;
   aa.list_offs = (const int*)h->seg_offs.p;
@@ -817,8 +827,15 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
   }
   if (want_energy || backward) {
     const int M = h->M;
-    const int tiles = h->mixed ? sg_gap_tc_tiles(h->tcm.mp) : sg_gap_tiles(M);
-    ENS(h, h->eps_part, es * N1 * tiles);
+    GapTcModel tm = h->tcm;  // with the tile configurations of this problem class
+    if (h->mixed) {
+      const soapgap_handle::TilePlan pl = plan_for(h, N);
+      tm.fwd_cfg = pl.gap_fwd;
+      tm.bwd_cfg = pl.gap_bwd;
+    }
+    const int tiles = h->mixed ? sg_gap_tc_tiles(tm.mp, tm.fwd_cfg) : sg_gap_tiles(M);
+    const int tiles_alloc = h->mixed ? sg_gap_tc_tiles_max(tm.mp) : tiles;
+    ENS(h, h->eps_part, es * N1 * tiles_alloc);
     ENS(h, h->e_atom, es * N1);
     if (want_grad) {
       if (!h->mixed) ENS(h, h->kp, es * N1 * M);
@@ -831,11 +848,10 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     h->stage_ran[3] = true;
     if constexpr (sizeof(T) == 4) {
       // tensor cores: centred, norm-scaled FP16 split operands (see gap_tc.cu)
-      const GapTcModel& tm = h->tcm;
       ENS(h, h->A16, sizeof(__half) * N1 * tm.terms * tm.dp);
       ENS(h, h->nrm, sizeof(float) * N1);
       ENS(h, h->uq, sizeof(float) * N1);
-      ENS(h, h->r_part, sizeof(float) * N1 * tiles);
+      ENS(h, h->r_part, sizeof(float) * N1 * tiles_alloc);
       if (want_grad) ENS(h, h->kp16, sizeof(__half) * N1 * tm.mp);
       CK(h, sg_gap_tc_prepare((const float*)h->q.p, N, D, tm.dp, tm.qbar, (__half*)h->A16.p,
                               (float*)h->nrm.p, (float*)h->uq.p, tm.terms, st));
@@ -850,7 +866,7 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     if (want_grad) {
       h->stage_ran[4] = h->stage_ran[5] = true;
       if constexpr (sizeof(T) == 4)
-        CK(h, sg_gap_tc_backward(h->tcm, (const __half*)h->kp16.p, (const float*)h->r_part.p, N,
+        CK(h, sg_gap_tc_backward(tm, (const __half*)h->kp16.p, (const float*)h->r_part.p, N,
                                  (float*)h->g.p, (int*)h->err.p, st));
       else
         CK(h, sg_gap_backward_simt<T>((const T*)h->kp.p, (const T*)h->qs.p, N, M, D, (T*)h->g.p, st));
@@ -1122,7 +1138,38 @@ extern "C" int soapgap_sync_status(soapgap_handle* h, void* stream) {
   return fail(h, rc, device_error_text(code));
 }
 
-extern "C" int soapgap_autotune(soapgap_handle* h, const soapgap_batch* batch, int32_t* choice,
+#define TL(x)                          \
+  do {                                 \
+    const int rc_ = (x);               \
+    if (rc_ != SOAPGAP_OK) return rc_; \
+  } while (0)
+
+// CUDA-event time (ms) of `launch`, mean of `reps` launches after one untimed launch (which
+// also sets kernel attributes and warms the caches); a negative time if it cannot run.
+template <typename F>
+static int time_launches(soapgap_handle* h, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, int reps,
+                         F&& launch, float* ms) {
+  float total = 0.f;
+  for (int rep = 0; rep <= reps; ++rep) {
+    CK(h, cudaEventRecord(e0, st));
+    cudaError_t e = launch();
+    if (e == cudaErrorInvalidConfiguration) {
+      cudaGetLastError();
+      *ms = -1.f;
+      return SOAPGAP_OK;
+    }
+    CK(h, e);
+    CK(h, cudaEventRecord(e1, st));
+    CK(h, cudaEventSynchronize(e1));
+    float t = 0.f;
+    CK(h, cudaEventElapsedTime(&t, e0, e1));
+    if (rep > 0) total += t;
+  }
+  *ms = total / reps;
+  return SOAPGAP_OK;
+}
+
+extern "C" int soapgap_autotune(soapgap_handle* h, const soapgap_batch* batch, int32_t* plan,
                                 void* stream) {
   if (!h) return SOAPGAP_E_INVALID_ARG;
   int rc = check_batch(h, batch);
@@ -1131,7 +1178,7 @@ extern "C" int soapgap_autotune(soapgap_handle* h, const soapgap_batch* batch, i
   cudaStream_t st = (cudaStream_t)stream;
   const int N = batch->n_atoms, S = batch->n_struct;
   const size_t N1 = (size_t)std::max(N, 1);
-  // one synchronous evaluation sizes the workspace and leaves the adjoint's inputs
+  // one synchronous evaluation sizes the workspace and leaves every stage's inputs
   CK(h, ensure(h->host_e_struct, sizeof(double) * S));
   CK(h, ensure(h->host_forces, sizeof(double) * 3 * N1));
   CK(h, ensure(h->host_virial, sizeof(double) * 9 * S));
@@ -1139,39 +1186,114 @@ extern "C" int soapgap_autotune(soapgap_handle* h, const soapgap_batch* batch, i
                        nullptr, (double*)h->host_e_struct.p, (double*)h->host_forces.p,
                        (double*)h->host_virial.p, stream);
   if (rc != SOAPGAP_OK) return rc;
-  int best = 0;
+  soapgap_handle::TilePlan best{};
   if (h->mixed && N > 0) {
-    // the adjoint kernel is idempotent on the handle's state: time each block shape
+    // each stage is idempotent on the handle's state after that evaluation: time its
+    // candidates one after the other, keeping the others' choices fixed
     cudaEvent_t e0, e1;
     CK(h, cudaEventCreate(&e0));
     CK(h, cudaEventCreate(&e1));
-    float best_ms = 0.f;
+    float best_ms = -1.f;
     for (int w = 2; w <= 4; ++w) {
       AdjArgs<float> aa = adj_args<float>(h, N, batch->species);
       aa.warps = w;
       float ms = 0.f;
-      bool ok = true;
-      for (int rep = 0; rep < 3 && ok; ++rep) {
-        CK(h, cudaEventRecord(e0, st));
-        cudaError_t e = sg_pair_adjoint<float>(aa, h->cls, true, st);
-        if (e == cudaErrorInvalidConfiguration) { cudaGetLastError(); ok = false; break; }
-        CK(h, e);
-        CK(h, cudaEventRecord(e1, st));
-        CK(h, cudaEventSynchronize(e1));
-        float t = 0.f;
-        CK(h, cudaEventElapsedTime(&t, e0, e1));
-        if (rep > 0) ms += t;  // first launch warms caches and sets kernel attributes
+      TL(time_launches(h, st, e0, e1, 2, [&] { return sg_pair_adjoint<float>(aa, h->cls, true, st); }, &ms));
+      if (ms >= 0.f && (best_ms < 0.f || ms < best_ms)) {
+        best.adj_warps = w;
+        best_ms = ms;
       }
-      if (ok && (best == 0 || ms < best_ms)) {
-        best = w;
+    }
+    // the GAP forward (its partial sums and kernel derivatives), then the backward on them
+    GapTcModel tm = h->tcm;
+    best_ms = -1.f;
+    for (int c = 0; c < SG_GAP_FWD_CFGS; ++c) {
+      tm.fwd_cfg = c;
+      float ms = 0.f;
+      TL(time_launches(h, st, e0, e1, 2, [&] {
+        return sg_gap_tc_forward(tm, tm.terms, (const __half*)h->A16.p, (const float*)h->nrm.p,
+                                 (const float*)h->uq.p, N, (float*)h->eps_part.p, (float*)h->r_part.p,
+                                 (__half*)h->kp16.p, (int*)h->err.p, st);
+      }, &ms));
+      if (ms >= 0.f && (best_ms < 0.f || ms < best_ms)) {
+        best.gap_fwd = c;
+        best_ms = ms;
+      }
+    }
+    tm.fwd_cfg = best.gap_fwd;
+    CK(h, sg_gap_tc_forward(tm, tm.terms, (const __half*)h->A16.p, (const float*)h->nrm.p,
+                            (const float*)h->uq.p, N, (float*)h->eps_part.p, (float*)h->r_part.p,
+                            (__half*)h->kp16.p, (int*)h->err.p, st));
+    best_ms = -1.f;
+    for (int c = 0; c < SG_GAP_BWD_CFGS; ++c) {
+      tm.bwd_cfg = c;
+      float ms = 0.f;
+      TL(time_launches(h, st, e0, e1, 2, [&] {
+        return sg_gap_tc_backward(tm, (const __half*)h->kp16.p, (const float*)h->r_part.p, N, (float*)h->g.p,
+                                  (int*)h->err.p, st);
+      }, &ms));
+      if (ms >= 0.f && (best_ms < 0.f || ms < best_ms)) {
+        best.gap_bwd = c;
         best_ms = ms;
       }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (best) h->adj_warps[adj_key(h, N, h->last_pairs)] = best;
+    CK(h, cudaMemcpyAsync(h->h_err, h->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    if (*h->h_err) return fail(h, SOAPGAP_E_CUDA, device_error_text(*h->h_err));
+    h->plans[plan_key(h, N, h->last_pairs)] = best;
+    // the stages' outputs now come from the trial launches: a new evaluation is needed
+    // before the adjoint's inputs are consistent again
+    h->have_forward = false;
   }
-  if (choice) *choice = best;
+  if (plan) {
+    plan[0] = best.adj_warps;
+    plan[1] = best.gap_fwd;
+    plan[2] = best.gap_bwd;
+  }
+  h->msg.clear();
+  return SOAPGAP_OK;
+}
+
+// The batch's problem class as of its last evaluation on this handle.
+static int plan_batch_key(soapgap_handle* h, const soapgap_batch* batch, long long* key) {
+  int rc = check_batch(h, batch);
+  if (rc != SOAPGAP_OK) return rc;
+  if (!h->list_ok || h->list_atoms != batch->n_atoms)
+    return fail(h, SOAPGAP_E_STATE, "plan: evaluate the batch synchronously first (its pair count sets its class)");
+  *key = plan_key(h, batch->n_atoms, h->last_pairs);
+  return SOAPGAP_OK;
+}
+
+extern "C" int soapgap_get_plan(soapgap_handle* h, const soapgap_batch* batch, int32_t* plan) {
+  if (!h || !plan) return SOAPGAP_E_INVALID_ARG;
+  long long key = 0;
+  int rc = plan_batch_key(h, batch, &key);
+  if (rc != SOAPGAP_OK) return rc;
+  auto it = h->plans.find(key);
+  const soapgap_handle::TilePlan p = it == h->plans.end() ? soapgap_handle::TilePlan{} : it->second;
+  plan[0] = p.adj_warps;
+  plan[1] = p.gap_fwd;
+  plan[2] = p.gap_bwd;
+  h->msg.clear();
+  return SOAPGAP_OK;
+}
+
+extern "C" int soapgap_set_plan(soapgap_handle* h, const soapgap_batch* batch, const int32_t* plan) {
+  if (!h || !plan) return SOAPGAP_E_INVALID_ARG;
+  if (!(plan[0] == 0 || (plan[0] >= 2 && plan[0] <= 4)) || plan[1] < 0 || plan[1] >= SG_GAP_FWD_CFGS ||
+      plan[2] < 0 || plan[2] >= SG_GAP_BWD_CFGS)
+    return fail(h, SOAPGAP_E_INVALID_ARG, "set_plan: adjoint warps 0 or 2..4, GAP configurations in range");
+  long long key = 0;
+  int rc = plan_batch_key(h, batch, &key);
+  if (rc != SOAPGAP_OK) return rc;
+  soapgap_handle::TilePlan p;
+  p.adj_warps = plan[0];
+  p.gap_fwd = plan[1];
+  p.gap_bwd = plan[2];
+  h->plans[key] = p;
+  h->have_forward = false;  // a new forward pass must produce the layout of the new plan
   h->msg.clear();
   return SOAPGAP_OK;
 }

@@ -595,8 +595,18 @@ __global__ void prep_atoms_kernel(const float* __restrict__ q, int n, int d, int
 
 }  // namespace
 
-// partial-sum slots per row of the forward epilogue: two column halves per 256-wide tile
-int sg_gap_tc_tiles(int mp) { return (mp + 255) / 256 * 2; }
+// Tile configurations of the two GAP products, chosen by the autotuner.  Each is a
+// (columns per tile BN, pipeline stages, epilogue warps) instance of tc_gemm_kernel:
+//   forward  0: (256, 4, 8)   1: (128, 6, 4)   2: (128, 6, 8)
+//   backward 0: (224, 5, 4)   1: (128, 6, 4)   2: (192, 5, 4)   3: (256, 4, 4)
+// The forward's columns are the sparse set padded to 256 (every BN above divides it); the
+// backward's, the descriptor padded to 64 (ragged last tiles read TMA's zero fill).
+static int fwd_bn(int cfg) { return cfg == 0 ? 256 : 128; }
+static int fwd_halves(int cfg) { return cfg == 1 ? 1 : 2; }
+
+// partial-sum slots per row of the forward epilogue: one per column group of every tile
+int sg_gap_tc_tiles(int mp, int fwd_cfg) { return mp / fwd_bn(fwd_cfg) * fwd_halves(fwd_cfg); }
+int sg_gap_tc_tiles_max(int mp) { return mp / 64; }
 
 cudaError_t sg_gap_tc_prepare(const float* q, int n, int d, int dp, const float* qbar, __half* A, float* nrm,
                               float* uq, int terms, cudaStream_t st) {
@@ -619,7 +629,7 @@ cudaError_t sg_gap_tc_forward(const GapTcModel& md, int terms, const __half* A, 
   EpiGapFwd e{};
   e.rows = n;
   e.ld_kp = md.mp;
-  e.n_tiles = sg_gap_tc_tiles(md.mp);
+  e.n_tiles = sg_gap_tc_tiles(md.mp, md.fwd_cfg);
   e.izeta = md.izeta;
   e.zeta = md.zeta;
   e.u = uq;
@@ -630,8 +640,13 @@ cudaError_t sg_gap_tc_forward(const GapTcModel& md, int terms, const __half* A, 
   e.kp = kp;
   // one FP16 product hi.hi: A rows [hi] against the first dp columns of the sparse rows
   // [hi | lo | hi]; three: A rows [hi | hi | lo] against the whole rows
-  if (terms == 1) return launch_gemm<256, 4, 8>(A, n, md.B, md.mp, md.dp, e, err, st, md.dp, 3 * md.dp);
-  return launch_gemm<256, 4, 8>(A, n, md.B, md.mp, 3 * md.dp, e, err, st);
+  const int k = terms * md.dp, lda = terms * md.dp, ldb = 3 * md.dp;
+  switch (md.fwd_cfg) {
+    case 0: return launch_gemm<256, 4, 8>(A, n, md.B, md.mp, k, e, err, st, lda, ldb);
+    case 1: return launch_gemm<128, 6, 4>(A, n, md.B, md.mp, k, e, err, st, lda, ldb);
+    case 2: return launch_gemm<128, 6, 8>(A, n, md.B, md.mp, k, e, err, st, lda, ldb);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t sg_gap_tc_backward(const GapTcModel& md, const __half* kp, const float* r_part, int n, float* g,
@@ -640,12 +655,18 @@ cudaError_t sg_gap_tc_backward(const GapTcModel& md, const __half* kp, const flo
   EpiGapBwd e{};
   e.rows = n;
   e.d = md.d;
-  e.n_tiles = sg_gap_tc_tiles(md.mp);
+  e.n_tiles = sg_gap_tc_tiles(md.mp, md.fwd_cfg);  // the forward's partial-sum layout
   e.kappa = md.kappa;
   e.qbar = md.qbar;
   e.r_part = r_part;
   e.g = g;
-  return launch_gemm<224, 5, 4>(kp, n, md.BT, md.dp, md.mp, e, err, st);
+  switch (md.bwd_cfg) {
+    case 0: return launch_gemm<224, 5, 4>(kp, n, md.BT, md.dp, md.mp, e, err, st);
+    case 1: return launch_gemm<128, 6, 4>(kp, n, md.BT, md.dp, md.mp, e, err, st);
+    case 2: return launch_gemm<192, 5, 4>(kp, n, md.BT, md.dp, md.mp, e, err, st);
+    case 3: return launch_gemm<256, 4, 4>(kp, n, md.BT, md.dp, md.mp, e, err, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t sg_tc_gemm_store(const __half* A, int m, const __half* B, int nn, int k, float* C, int* err,

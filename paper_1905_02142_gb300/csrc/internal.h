@@ -165,8 +165,14 @@ struct GapTcModel {
   float kd;               // power of two: max |kd (q_s - qbar)| in [1, 2)
   const __half* Ad;       // [mp][dpd]
   int terms;              // FP16 products of the energy: 1 (hi.hi) or 3 (hi.hi + hi.lo + lo.hi)
+  int fwd_cfg, bwd_cfg;   // tile configurations of the forward and backward products
 };
-int sg_gap_tc_tiles(int m);
+#define SG_GAP_FWD_CFGS 3
+#define SG_GAP_BWD_CFGS 4
+// partial-sum slots per atom row of the forward product with configuration fwd_cfg, and
+// the most any configuration needs
+int sg_gap_tc_tiles(int mp, int fwd_cfg);
+int sg_gap_tc_tiles_max(int mp);
 // A rows of the atoms: terms = 1 gives [hi] (row stride dp; the energy and its gradient),
 // terms = 3 the split [hi | hi | lo] (row stride 3 dp; kernel rows of the fitting matrices)
 cudaError_t sg_gap_tc_prepare(const float* q, int n, int d, int dp, const float* qbar, __half* A,
