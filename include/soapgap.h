@@ -198,7 +198,10 @@ int soapgap_sync_status(soapgap_handle* h, void* stream);
  * Runs one synchronous ENERGY|FORCES|VIRIAL evaluation of `batch` (device pos/species, as
  * for soapgap_compute; it also sizes the workspace for asynchronous calls), then times on
  * it, stage by stage, the candidates of a tile plan of SOAPGAP_PLAN_LEN entries:
- *   plan[0]  warps (32-pair batches) per block of the tensor-core adjoint: 2, 3 or 4
+ *   plan[0]  the tensor-core adjoint: 2, 3 or 4 = mma.sync with that many warps (32-pair
+ *            batches) per block; 5 = tcgen05 with the per-atom contraction accumulated in
+ *            tensor memory (exact class sizes n_max = l_max = 6, 8, 10, 12 only; other sizes
+ *            run the mma.sync kernel with 4 warps)
  *   plan[1]  tile configuration of the GAP forward product (columns per tile, pipeline
  *            stages, epilogue warps): 0 = (256, 4, 8), 1 = (128, 6, 4), 2 = (128, 6, 8)
  *   plan[2]  the same for the GAP backward product: 0 = (224, 5, 4), 1 = (128, 6, 4),
@@ -216,7 +219,8 @@ int soapgap_autotune(soapgap_handle* h, const soapgap_batch* batch, int32_t* pla
  * (the defaults {0, 0, 0} if none was tuned or set); soapgap_set_plan installs one (e.g. read
  * back from a cache of earlier tuning runs).  Both need a synchronous evaluation of this
  * batch on the handle first (its pair count fixes the class): SOAPGAP_E_STATE otherwise;
- * SOAPGAP_E_INVALID_ARG for an entry out of range (plan[0] may also be 0). */
+ * SOAPGAP_E_INVALID_ARG for an entry out of range (plan[0] may also be 0: chosen by the
+ * pairs per atom). */
 int soapgap_get_plan(soapgap_handle* h, const soapgap_batch* batch, int32_t* plan);
 int soapgap_set_plan(soapgap_handle* h, const soapgap_batch* batch, const int32_t* plan);
 

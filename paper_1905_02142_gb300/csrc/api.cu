@@ -585,6 +585,7 @@ static AdjArgs<T> adj_args(soapgap_handle* h, int N, const int* species) {
   else { aa.yc = h->yc64; aa.bc = h->bc64; }
   aa.c = (const T*)h->c.p; aa.q = (const T*)h->q.p; aa.pnorm = (const T*)h->pnorm.p;
   aa.g = (const T*)h->g.p; aa.dedr = (Vec4<T>*)h->dedr.p; aa.vir_atom = (T*)h->vir_atom.p;
+  aa.err = (int*)h->err.p;
   return aa;
 }
 
@@ -1194,8 +1195,9 @@ extern "C" int soapgap_autotune(soapgap_handle* h, const soapgap_batch* batch, i
     CK(h, cudaEventCreate(&e0));
     CK(h, cudaEventCreate(&e1));
     float best_ms = -1.f;
-    for (int w = 2; w <= 4; ++w) {
+    for (int w = 2; w <= SG_ADJ_TCGEN05; ++w) {
       AdjArgs<float> aa = adj_args<float>(h, N, batch->species);
+      if (w == SG_ADJ_TCGEN05 && !sg_pair_adjoint_tc_supported(aa, h->cls)) continue;
       aa.warps = w;
       float ms = 0.f;
       TL(time_launches(h, st, e0, e1, 2, [&] { return sg_pair_adjoint<float>(aa, h->cls, true, st); }, &ms));
@@ -1282,9 +1284,9 @@ extern "C" int soapgap_get_plan(soapgap_handle* h, const soapgap_batch* batch, i
 
 extern "C" int soapgap_set_plan(soapgap_handle* h, const soapgap_batch* batch, const int32_t* plan) {
   if (!h || !plan) return SOAPGAP_E_INVALID_ARG;
-  if (!(plan[0] == 0 || (plan[0] >= 2 && plan[0] <= 4)) || plan[1] < 0 || plan[1] >= SG_GAP_FWD_CFGS ||
+  if (!(plan[0] == 0 || (plan[0] >= 2 && plan[0] <= SG_ADJ_TCGEN05)) || plan[1] < 0 || plan[1] >= SG_GAP_FWD_CFGS ||
       plan[2] < 0 || plan[2] >= SG_GAP_BWD_CFGS)
-    return fail(h, SOAPGAP_E_INVALID_ARG, "set_plan: adjoint warps 0 or 2..4, GAP configurations in range");
+    return fail(h, SOAPGAP_E_INVALID_ARG, "set_plan: adjoint variant 0 or 2..5, GAP configurations in range");
   long long key = 0;
   int rc = plan_batch_key(h, batch, &key);
   if (rc != SOAPGAP_OK) return rc;

@@ -209,11 +209,17 @@ template <typename T> struct AdjArgs {
   const T* g;               // [N][D] dE/dq (before the structure weight)
   Vec4<T>* dedr;            // [P] dE/dr_ij
   T* vir_atom;              // [N][9]
+  int* err;                 // device error word (SG_ERR_*)
 };
 template <typename T> cudaError_t sg_pair_adjoint(const AdjArgs<T>& a, int cls, bool table,
                                                   cudaStream_t st);
 // mixed-precision (table) adjoint with the per-atom contraction on tensor cores
 cudaError_t sg_pair_adjoint_mma(const AdjArgs<float>& a, int cls, cudaStream_t st);
+// the tcgen05 variant (pair_adj_tc.cu), selected by a.warps == SG_ADJ_TCGEN05; only for
+// exact basis sizes of the class (n_max = l_max = 6 + 2 cls)
+#define SG_ADJ_TCGEN05 5
+bool sg_pair_adjoint_tc_supported(const AdjArgs<float>& a, int cls);
+cudaError_t sg_pair_adjoint_tc(const AdjArgs<float>& a, int cls, cudaStream_t st);
 // 32-pair batches of a typical atom (sum over its neighbour-species segments)
 int sg_adj_batches_per_atom(long long n_pairs, int n_atoms, int nsp);
 

@@ -22,24 +22,12 @@
 #include <cmath>
 #include <cstdint>
 
+#include "adj_common.cuh"
 #include "internal.h"
 #include "table.cuh"
 
 namespace {
 
-// Number of tau rows the recursion visits for a given l_max: the m = 0 column (l_max + 1
-// entries, padded to an even count) followed by (cos, sin) pairs for m >= 1.
-__host__ __device__ inline int tau_even(int lmax) { return (lmax + 2) & ~1; }
-__host__ __device__ inline int tau_count(int lmax) { return tau_even(lmax) + lmax * (lmax + 1); }
-__host__ __device__ inline int tau_rows16(int lmax) { return (tau_count(lmax) + 15) & ~15; }
-
-// tau of (l, m) (m < 0: the sin-type harmonic l^2 + l + m)
-__device__ __forceinline__ int tau_of(int l, int ms, int lmax) {
-  if (ms == 0) return l;
-  const int m = ms < 0 ? -ms : ms;
-  const int base = tau_even(lmax) + 2 * ((m - 1) * (lmax + 1) - m * (m - 1) / 2);
-  return base + 2 * (l - m) + (ms < 0 ? 1 : 0);
-}
 
 // FP16 operand rows of KP halfs.  KP = 32: 64-byte rows with the 16-byte chunk index XORed
 // by (row / 2) % 4, so that the 8 rows an ldmatrix reads hit 8 distinct bank groups.
@@ -52,26 +40,6 @@ template <int KP> struct RowLayout {
   }
 };
 
-// Packed recursion coefficients for the rolled (l, m) loops.  For column j and degree l:
-//   A(l, j) = s1[j] (l = j + 1), a[l][j] (l >= j + 2), 0 otherwise
-//   B(l, j) = b[l][j] (l >= j + 2), 0 otherwise
-//   C(l, j) = seed[j] (l = j), 0 otherwise
-// so that N~_l^j = A z N~_{l-1}^j - B N~_{l-2}^j + C for every l >= j, starting from zeros.
-template <int LC> struct CoefShared {
-  float4 p[LC + 1][LC + 1];  // (A(l,m), B(l,m), A(l,m+1), B(l,m+1))
-  float4 q[LC + 1][LC + 1];  // (C(l,m), C(l,m+1), d[l][m], 0)
-};
-
-__device__ __forceinline__ float coef_a(const YlmCoef<float>& y, int l, int j) {
-  if (l == j + 1) return y.s1[j];
-  return l >= j + 2 ? y.a[l][j] : 0.f;
-}
-__device__ __forceinline__ float coef_b(const YlmCoef<float>& y, int l, int j) {
-  return l >= j + 2 ? y.b[l][j] : 0.f;
-}
-__device__ __forceinline__ float coef_c(const YlmCoef<float>& y, int l, int j) {
-  return (l == j && j <= SG_MAX_LMAX) ? y.seed[j] : 0.f;
-}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -84,10 +52,6 @@ __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r
                : "r"(addr));
 }
 
-// 4-byte asynchronous global -> shared copy (completes at cp.async.wait_group)
-__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
 
 __device__ __forceinline__ void mma_f16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
                                         uint32_t b1) {
@@ -98,9 +62,6 @@ __device__ __forceinline__ void mma_f16(float (&d)[4], const uint32_t (&a)[4], u
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ uint32_t pack_half2(__half lo_k, __half hi_k) {
-  return (uint32_t)__half_as_ushort(lo_k) | ((uint32_t)__half_as_ushort(hi_k) << 16);
-}
 
 // Operand row for a value vector v[0..NC): k = [hi(v) | hi(v) | lo(v) | 0...] (A side) or
 // [hi(v) | lo(v) | hi(v) | 0...] (B side), so that the k-sum gives hi.hi + hi.lo + lo.hi.
@@ -148,7 +109,6 @@ template <int NC, int LC> struct Dims {
 
 // prologue scratch (floats, each part 16-byte aligned):
 //   h [D] | q [D] | g [D] | c [nch][L] | M [nsp][l_max+1][nch][NP] | G [nsp][t16][NP]
-__host__ __device__ inline int align4(int x) { return (x + 3) & ~3; }
 
 template <int NC, int LC>
 int prologue_floats(int nsp, int nmax, int lmax, int dim, int t16) {
@@ -175,28 +135,6 @@ MmaLayout make_layout(int nsp, int nmax, int lmax, int dim) {
   return m;
 }
 
-template <int W> __device__ __forceinline__ float block_sum(float v, float* red) {
-  v = warp_sum(v);
-  __syncthreads();  // red free
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  float t = 0.f;
-#pragma unroll
-  for (int w = 0; w < W; ++w) t += red[w];
-  return t;
-}
-
-template <int W> __device__ __forceinline__ float block_max(float v, float* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  float t = 0.f;
-#pragma unroll
-  for (int w = 0; w < W; ++w) t = fmaxf(t, red[w]);
-  return t;
-}
 
 // The (l, m) sweep of one pair with l_max = LC known at compile time: fully unrolled, so the
 // recursion coefficients are constant-bank operands of the kernel's parameters, every
@@ -704,6 +642,12 @@ int sg_adj_batches_per_atom(long long n_pairs, int n_atoms, int nsp) {
 
 cudaError_t sg_pair_adjoint_mma(const AdjArgs<float>& a, int cls, cudaStream_t st) {
   if (a.n_atoms == 0) return cudaSuccess;
+  if (a.warps == SG_ADJ_TCGEN05) {
+    if (sg_pair_adjoint_tc_supported(a, cls)) return sg_pair_adjoint_tc(a, cls, st);
+    AdjArgs<float> b = a;  // other basis sizes: the mma.sync kernel with four warps
+    b.warps = 4;
+    return sg_pair_adjoint_mma(b, cls, st);
+  }
   switch (cls) {
     case 0: return launch_mma_v<6, 6>(a, st);
     case 1: return launch_mma_v<8, 8>(a, st);

@@ -136,7 +136,7 @@ def test_autotune_keeps_results(batched):
     s = Structures.from_batch(batch)
     before = {k: v.clone() for k, v in model.compute(s, **OUT).items()}
     plan = model.autotune(s)
-    assert plan["adjoint_warps"] in (2, 3, 4)
+    assert plan["adjoint_warps"] in (2, 3, 4, 5)
     assert 0 <= plan["gap_forward"] < 3 and 0 <= plan["gap_backward"] < 4
     assert model.plan(s) == {k: plan[k] for k in model.PLAN_KEYS}
     after = model.compute(s, **OUT)
@@ -157,15 +157,15 @@ def test_every_tile_plan_gives_the_same_results(batched):
     s = Structures.from_batch(batch)
     ref = {k: v.clone() for k, v in model.compute(s, **OUT).items()}
     assert model.plan(s) == {"adjoint_warps": 0, "gap_forward": 0, "gap_backward": 0}
-    for warps, fwd, bwd in itertools.product((2, 4), range(3), range(4)):
+    for warps, fwd, bwd in itertools.product((2, 4, 5), range(3), range(4)):
         model.set_plan(s, {"adjoint_warps": warps, "gap_forward": fwd, "gap_backward": bwd})
         out = model.compute(s, **OUT)
         # norm-wise: the local energies are sums of terms far larger than themselves, so
         # their last bits follow the partial-sum layout of the forward tile shape
-        for k in ("forces", "e_struct", "e_atom"):
-            assert rel(out[k], ref[k]) < 1e-5, (k, warps, fwd, bwd, rel(out[k], ref[k]))
+        for k, bar in (("forces", 1e-5), ("e_struct", 1e-5), ("e_atom", 5e-5)):
+            assert rel(out[k], ref[k]) < bar, (k, warps, fwd, bwd, rel(out[k], ref[k]))
     with pytest.raises(SoapGapError) as err:
-        model.set_plan(s, {"adjoint_warps": 5, "gap_forward": 0, "gap_backward": 0})
+        model.set_plan(s, {"adjoint_warps": 6, "gap_forward": 0, "gap_backward": 0})
     assert err.value.code == L.E_INVALID_ARG
 
 

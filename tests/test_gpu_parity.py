@@ -483,3 +483,36 @@ def test_gap_terms_forced_one_and_three_against_oracle():
           f"automatic {auto})")
     assert errs[3] < 2e-6 and errs[1] < MIXED["e"]
     assert errs[3] < errs[1]
+
+
+# ------------------------------------------------------------------ adjoint variants
+@pytest.mark.parametrize("name,m_sparse,sampled", [("box64_n6l6", None, False), ("box1000_n8l8", 100, False),
+                                                   ("twospecies4096_n8l8", 300, True),
+                                                   ("box100k_n10l10", None, True)])
+def test_adjoint_variants_against_oracle(name, m_sparse, sampled):
+    """The adjoint on tcgen05 (TMEM accumulators) and on mma.sync with 2 and 4 warps per
+    block, forced through the tile plan: forces against the oracle (all atoms, or 4 sampled
+    atoms of the large boxes) within the mixed bar, and against each other."""
+    w = synth.get_workload(name)
+    batch = w.structures()
+    P, qs, al, zeta = sparse_model(name, m_sparse)
+    model = model_for(params_dict(P), "mixed", qs, al, zeta)
+    s = structures(batch)
+    model.compute(s, energy=True)
+    W = oracle_W(P.n_max, P.r_cut, P.sigma_r0)
+    if sampled:
+        atoms = np.random.default_rng(7).choice(batch.n_atoms, 4, replace=False)
+        f_ref, atoms = gap.forces_at(batch, P, qs, al, zeta, atoms, W=W)
+    else:
+        atoms = np.arange(batch.n_atoms)
+        f_ref = gap.evaluate(batch, P, qs, al, zeta, W=W, virial=False)["forces"]
+    forces = {}
+    for variant in (5, 4, 2):
+        model.set_plan(s, {"adjoint_warps": variant, "gap_forward": 0, "gap_backward": 0})
+        f = model.compute(s, energy=True, forces=True)["forces"].cpu().numpy()
+        forces[variant] = f
+        err = rel_all(f[atoms], f_ref)
+        print(f"PARITY {name} adjoint variant {variant}: F {err:.2e}")
+        assert err < MIXED["f"]
+    assert rel_all(forces[5], forces[4]) < 1e-5
+    assert rel_all(forces[2], forces[4]) < 1e-5
