@@ -260,7 +260,7 @@ class SoapGap:
         st = (stream or torch.cuda.current_stream()).cuda_stream
         self._check(self.lib.soapgap_sync_status(self.h, st))
 
-    PLAN_KEYS = ("adjoint_warps", "gap_forward", "gap_backward")
+    PLAN_KEYS = ("adjoint_warps", "gap_forward", "gap_backward", "neighbour_sweep")
 
     def _plan_cache_key(self, s: Structures) -> str:
         """Problem class of a batch as the library tunes it (after an evaluation of it), with
@@ -276,13 +276,14 @@ class SoapGap:
                 f"|batches{batches}|lgN{lg}")
 
     def autotune(self, s: Structures, stream=None, cache: str | None = None) -> dict:
-        """Pick the tile plan of this batch's problem class (soapgap_autotune): warps per
-        block of the adjoint and the tile configurations of the two GAP products.
+        """Pick the tile plan of this batch's problem class (soapgap_autotune): the adjoint
+        variant, the tile configurations of the two GAP products and the neighbour sweep.
 
         cache: path of a JSON file of earlier choices, keyed by device, precision, basis,
         species, model size, FP16 products and problem class.  A plan found there is
         installed without timing (soapgap_set_plan); a new one is timed and added.
-        Returns {"adjoint_warps", "gap_forward", "gap_backward", "cached"}."""
+        Returns {"adjoint_warps", "gap_forward", "gap_backward", "neighbour_sweep",
+        "cached"}."""
         st = (stream or torch.cuda.current_stream(s.pos.device)).cuda_stream
         b = s.c_batch()
         key = None
@@ -302,7 +303,7 @@ class SoapGap:
         arr = (ctypes.c_int32 * L.PLAN_LEN)()
         self._check(self.lib.soapgap_autotune(self.h, ctypes.byref(b), arr, st))
         plan = dict(zip(self.PLAN_KEYS, [int(x) for x in arr]))
-        if cache and self.precision == "mixed":
+        if cache:
             try:
                 with open(cache) as f:
                     known = json.load(f)

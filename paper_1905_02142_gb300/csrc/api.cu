@@ -126,7 +126,7 @@ struct soapgap_handle {
   bool async_call = false;        // current call must not allocate or synchronise
   // tile plan per problem class (soapgap_autotune / soapgap_set_plan): adjoint warps per
   // block (0: by pairs per atom) and the configurations of the two GAP products
-  struct TilePlan { int adj_warps = 0, gap_fwd = 0, gap_bwd = 0; };
+  struct TilePlan { int adj_warps = 0, gap_fwd = 0, gap_bwd = 0, nbr_sweep = 0; };
   std::map<long long, TilePlan> plans;
   StructGeom* h_geom = nullptr;   // pinned staging
   size_t h_geom_cap = 0;
@@ -301,6 +301,7 @@ extern "C" int soapgap_descriptor_dim(const soapgap_handle* h, int32_t* dim) {
 }
 
 static std::string device_error_text(int code);
+static soapgap_handle::TilePlan plan_for(const soapgap_handle* h, int n_atoms);
 
 extern "C" int soapgap_set_model(soapgap_handle* h, const double* q_sparse, const double* alpha,
                                  int32_t m, double zeta) {
@@ -661,6 +662,9 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
   nb.err = (int*)h->err.p;
   nb.run = nullptr;
   nb.rc2_mask = h->skin > 0.0 ? h->prm.r_cut * h->prm.r_cut : 0.0;
+  nb.n_struct = S;
+  nb.n_bins = h->n_bins;
+  nb.sweep = plan_for(h, N).nbr_sweep;
   // Verlet skin: reuse the list while no atom has moved by skin/2 since its build
   bool rebuild = true, device_decides = false;
   if (!backward && h->skin > 0.0) {
@@ -1188,6 +1192,35 @@ extern "C" int soapgap_autotune(soapgap_handle* h, const soapgap_batch* batch, i
                        (double*)h->host_virial.p, stream);
   if (rc != SOAPGAP_OK) return rc;
   soapgap_handle::TilePlan best{};
+  if (N > 0) {
+    // the neighbour sweep (both paths): per bin or per atom, timed over whole evaluations
+    // (the list is rebuilt at every call without a skin; with one, the sweep only runs on
+    // rebuilds and the default is kept)
+    const long long key = plan_key(h, N, h->last_pairs);
+    float best_nb = -1.f;
+    for (int v = 1; v <= 2 && h->skin == 0.0; ++v) {
+      h->plans[key].nbr_sweep = v;
+      double t = 0.0;
+      for (int rep = 0; rep < 3; ++rep) {
+        rc = soapgap_compute(h, batch, SOAPGAP_ENERGY | SOAPGAP_TIMING, nullptr, nullptr, nullptr,
+                             (double*)h->host_e_struct.p, nullptr, nullptr, stream);
+        if (rc != SOAPGAP_OK) return rc;
+        double ms[SOAPGAP_N_STAGES] = {};
+        rc = soapgap_stage_times(h, ms);
+        if (rc != SOAPGAP_OK) return rc;
+        if (rep > 0) t += ms[0];
+      }
+      if (best_nb < 0.f || t < best_nb) {
+        best_nb = (float)t;
+        best.nbr_sweep = v;
+      }
+    }
+    h->plans[key].nbr_sweep = best.nbr_sweep;
+    rc = soapgap_compute(h, batch, SOAPGAP_ENERGY | SOAPGAP_FORCES | SOAPGAP_VIRIAL, nullptr, nullptr,
+                         nullptr, (double*)h->host_e_struct.p, (double*)h->host_forces.p,
+                         (double*)h->host_virial.p, stream);
+    if (rc != SOAPGAP_OK) return rc;
+  }
   if (h->mixed && N > 0) {
     // each stage is idempotent on the handle's state after that evaluation: time its
     // candidates one after the other, keeping the others' choices fixed
@@ -1245,6 +1278,8 @@ extern "C" int soapgap_autotune(soapgap_handle* h, const soapgap_batch* batch, i
     CK(h, cudaStreamSynchronize(st));
     if (*h->h_err) return fail(h, SOAPGAP_E_CUDA, device_error_text(*h->h_err));
     h->plans[plan_key(h, N, h->last_pairs)] = best;
+  } else if (N > 0) {
+    h->plans[plan_key(h, N, h->last_pairs)] = best;
     // the stages' outputs now come from the trial launches: a new evaluation is needed
     // before the adjoint's inputs are consistent again
     h->have_forward = false;
@@ -1253,6 +1288,7 @@ extern "C" int soapgap_autotune(soapgap_handle* h, const soapgap_batch* batch, i
     plan[0] = best.adj_warps;
     plan[1] = best.gap_fwd;
     plan[2] = best.gap_bwd;
+    plan[3] = best.nbr_sweep;
   }
   h->msg.clear();
   return SOAPGAP_OK;
@@ -1278,6 +1314,7 @@ extern "C" int soapgap_get_plan(soapgap_handle* h, const soapgap_batch* batch, i
   plan[0] = p.adj_warps;
   plan[1] = p.gap_fwd;
   plan[2] = p.gap_bwd;
+  plan[3] = p.nbr_sweep;
   h->msg.clear();
   return SOAPGAP_OK;
 }
@@ -1285,8 +1322,8 @@ extern "C" int soapgap_get_plan(soapgap_handle* h, const soapgap_batch* batch, i
 extern "C" int soapgap_set_plan(soapgap_handle* h, const soapgap_batch* batch, const int32_t* plan) {
   if (!h || !plan) return SOAPGAP_E_INVALID_ARG;
   if (!(plan[0] == 0 || (plan[0] >= 2 && plan[0] <= SG_ADJ_TCGEN05)) || plan[1] < 0 || plan[1] >= SG_GAP_FWD_CFGS ||
-      plan[2] < 0 || plan[2] >= SG_GAP_BWD_CFGS)
-    return fail(h, SOAPGAP_E_INVALID_ARG, "set_plan: adjoint variant 0 or 2..5, GAP configurations in range");
+      plan[2] < 0 || plan[2] >= SG_GAP_BWD_CFGS || plan[3] < 0 || plan[3] > 2)
+    return fail(h, SOAPGAP_E_INVALID_ARG, "set_plan: adjoint variant 0 or 2..5, GAP configurations and neighbour sweep in range");
   long long key = 0;
   int rc = plan_batch_key(h, batch, &key);
   if (rc != SOAPGAP_OK) return rc;
@@ -1294,6 +1331,7 @@ extern "C" int soapgap_set_plan(soapgap_handle* h, const soapgap_batch* batch, c
   p.adj_warps = plan[0];
   p.gap_fwd = plan[1];
   p.gap_bwd = plan[2];
+  p.nbr_sweep = plan[3];
   h->plans[key] = p;
   h->have_forward = false;  // a new forward pass must produce the layout of the new plan
   h->msg.clear();

@@ -81,6 +81,9 @@ struct NbrBuffers {
                              // (neighbour-list reuse decided on the device)
   double rc2_mask;           // > 0: pairs with |r|^2 >= rc2_mask get |r| = -1 (beyond r_cut
                              // in a list built with a skin); 0: no masking
+  int n_struct, n_bins;      // structures and bins of the batch
+  int sweep;                 // candidate sweep: 1 one block per bin, 2 one warp per atom, 0 chosen
+                             // from the batch (per bin for one structure of many bins)
 };
 size_t sg_scan_tmp_ints(int n);
 cudaError_t sg_exclusive_scan(const int* in, int* out, int n, int* tmp, cudaStream_t st,

@@ -11,6 +11,8 @@
 // every candidate whose d2 is farther than a rigorous rounding margin from r_cut^2 (or
 // from 0), and the FP64 expression decides the rest, so the set equals the FP64 one.
 // Pairs of each (centre, neighbour species) segment are sorted by (j, S).
+#include <algorithm>
+
 #include "internal.h"
 
 // ---------------------------------------------------------------- scan
@@ -416,14 +418,227 @@ __global__ void fill_slots_kernel(const double* __restrict__ pos, const int* __r
   }
 }
 
+// ---- the same sweep organised by bin
+// One block per bin (persistent over bins): the candidates of the bin's neighbour bins, in
+// every periodic image, are staged once in shared memory with their FP32 image shift already
+// added (the same rounded sums as visit_pairs, so every decision is bit-identical), and each
+// centre atom of the bin, one warp each, tests them there.  The bin's atoms share the 27 (or
+// more) neighbour bins, so the candidates are read from memory once per bin instead of once
+// per atom.  A bin whose neighbourhood has more than NB_CAP candidates, more than NB_COLS
+// (x, y) bin columns or more than NB_RPC z-runs per column (small cells with many images)
+// takes the per-atom sweep instead.
+constexpr int NB_WARPS = 4;
+constexpr int NB_CAP = 1536;   // candidates staged per bin
+constexpr int NB_COLS = 32;    // (x, y) bin columns of a bin's neighbourhood
+constexpr int NB_RPC = 4;      // z-runs per column
+
+__device__ __forceinline__ int pack_shift(int s1, int s2, int s3) {
+  return ((s1 + 128) << 16) | ((s2 + 128) << 8) | (s3 + 128);
+}
+
+__global__ void __launch_bounds__(NB_WARPS * 32)
+fill_slots_bins_kernel(const double* __restrict__ pos, int nsp, double rc, int maxn, NbrBuffers b,
+                       const float4* __restrict__ binpos) {
+  if (b.run && *b.run == 0) return;
+  __shared__ float4 cpos[NB_CAP];      // candidate position + image shift, .w = j | species << 28
+  __shared__ int cshift[NB_CAP];       // candidate image S, packed
+  __shared__ int run_beg[NB_COLS * NB_RPC], run_len[NB_COLS * NB_RPC], run_S[NB_COLS * NB_RPC];
+  __shared__ float run_sx[NB_COLS * NB_RPC], run_sy[NB_COLS * NB_RPC], run_sz[NB_COLS * NB_RPC];
+  __shared__ int run_off[NB_COLS * NB_RPC + 1];
+  __shared__ int col_ok;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const double rc2 = rc * rc;
+  const float rc2f = (float)rc2;
+  for (int bin = blockIdx.x; bin < b.n_bins; bin += gridDim.x) {
+    const int a_beg = b.bin_start[bin], a_end = b.bin_start[bin + 1];
+    if (a_beg == a_end) continue;  // no centre atom (the same for the whole block)
+    // structure of this bin: the last s with bin_off <= bin (every structure has a bin)
+    int lo = 0, hi = b.n_struct - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (b.geom[mid].bin_off <= bin) lo = mid;
+      else hi = mid - 1;
+    }
+    const StructGeom& g = b.geom[lo];
+    const int local = bin - g.bin_off;
+    const int bx = local / (g.nb[1] * g.nb[2]), by = (local / g.nb[2]) % g.nb[1], bz = local % g.nb[2];
+    const int ncols = (2 * g.m[0] + 1) * (2 * g.m[1] + 1);
+    __syncthreads();  // the previous bin's candidates are no longer read
+    if (tid == 0) col_ok = ncols <= NB_COLS;
+    __syncthreads();
+    // ---- runs: thread t < ncols walks column t = (d0, d1) and its z-runs (as visit_pairs)
+    if (col_ok && tid < NB_COLS) {
+      int nr = 0;
+      if (tid < ncols) {
+        const int d0 = tid / (2 * g.m[1] + 1) - g.m[0], d1 = tid % (2 * g.m[1] + 1) - g.m[1];
+        int b0, S1, b1, S2;
+        float f1, f2;
+        wrap(bx + d0, g.nb[0], b0, S1, f1);
+        wrap(by + d1, g.nb[1], b1, S2, f2);
+        const int zlo = bz - g.m[2], zhi = bz + g.m[2];
+        int S3 = 0, t0 = zlo;
+        while (t0 < 0) { t0 += g.nb[2]; --S3; }
+        while (t0 >= g.nb[2]) { t0 -= g.nb[2]; ++S3; }
+        const int tb = g.bin_off + (b0 * g.nb[1] + b1) * g.nb[2];
+        for (int t = zlo; t <= zhi; ++S3, t0 = 0) {
+          const int t1 = min(g.nb[2] - 1, t0 + (zhi - t));
+          t += t1 - t0 + 1;
+          const int beg = b.bin_start[tb + t0], end = b.bin_start[tb + t1 + 1];
+          if (end > beg) {
+            if (nr == NB_RPC) {
+              nr = NB_RPC + 1;  // too many runs in this column
+              break;
+            }
+            const int k = tid * NB_RPC + nr;
+            const float f3 = (float)S3;
+            run_beg[k] = beg;
+            run_len[k] = end - beg;
+            run_S[k] = pack_shift(S1, S2, S3);
+            run_sx[k] = __fadd_rn(__fadd_rn(__fmul_rn(f1, g.h32[0]), __fmul_rn(f2, g.h32[3])), __fmul_rn(f3, g.h32[6]));
+            run_sy[k] = __fadd_rn(__fadd_rn(__fmul_rn(f1, g.h32[1]), __fmul_rn(f2, g.h32[4])), __fmul_rn(f3, g.h32[7]));
+            run_sz[k] = __fadd_rn(__fadd_rn(__fmul_rn(f1, g.h32[2]), __fmul_rn(f2, g.h32[5])), __fmul_rn(f3, g.h32[8]));
+            ++nr;
+          }
+        }
+      }
+      // empty run slots of the column, then candidate offsets of all runs (warp 0 scan)
+      for (int r = min(nr, NB_RPC); r < NB_RPC; ++r) run_len[tid * NB_RPC + r] = 0;
+      const bool bad = nr > NB_RPC;
+      int cnt = 0;
+      for (int r = 0; r < NB_RPC; ++r) cnt += run_len[tid * NB_RPC + r];
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      int off = incl - cnt;
+      for (int r = 0; r < NB_RPC; ++r) {
+        run_off[tid * NB_RPC + r] = off;
+        off += run_len[tid * NB_RPC + r];
+      }
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      if (tid == 31) run_off[NB_COLS * NB_RPC] = total;
+      if (__any_sync(0xffffffffu, bad) || total > NB_CAP) {
+        if (tid == 0) col_ok = 0;
+      }
+    }
+    __syncthreads();
+    const bool staged = col_ok != 0;
+    if (staged) {
+      const int total = run_off[NB_COLS * NB_RPC];
+      for (int c = tid; c < total; c += NB_WARPS * 32) {
+        int rlo = 0, rhi = NB_COLS * NB_RPC - 1;  // the last run with run_off <= c and run_len > 0
+        while (rlo < rhi) {
+          const int mid = (rlo + rhi + 1) >> 1;
+          if (run_off[mid] <= c) rlo = mid;
+          else rhi = mid - 1;
+        }
+        while (run_len[rlo] == 0 || run_off[rlo] + run_len[rlo] <= c) ++rlo;  // skip empty slots
+        const float4 pj = binpos[run_beg[rlo] + (c - run_off[rlo])];
+        cpos[c] = make_float4(__fadd_rn(pj.x, run_sx[rlo]), __fadd_rn(pj.y, run_sy[rlo]),
+                              __fadd_rn(pj.z, run_sz[rlo]), pj.w);
+        cshift[c] = run_S[rlo];
+      }
+    }
+    __syncthreads();
+    const int total = staged ? run_off[NB_COLS * NB_RPC] : 0;
+    // ---- centre atoms of the bin, one warp each
+    for (int ca = a_beg + warp; ca < a_end; ca += NB_WARPS) {
+      const int i = b.bin_atoms[ca];
+      int cnt = 0;
+      int percnt[SG_MAX_SPECIES];
+#pragma unroll
+      for (int s = 0; s < SG_MAX_SPECIES; ++s) percnt[s] = 0;
+      FillSlots fn{lane, maxn, &cnt, percnt, b.key_tmp + (size_t)i * maxn, b.err};
+      if (!staged) {
+        visit_pairs(pos, binpos, i, rc, b, FillSlots(fn));  // (a copy: it refers to cnt and percnt)
+      } else {
+        const float xi = (float)pos[3 * i], yi = (float)pos[3 * i + 1], zi = (float)pos[3 * i + 2];
+        const float margin = g.margin;
+        const int zero = pack_shift(0, 0, 0);
+        auto test = [&](int k, int& j, int& sj, int& S, bool& cand, bool& exact) {
+          j = -1;
+          sj = 0;
+          S = zero;
+          cand = exact = false;
+          if (k < total) {
+            const float4 pj = cpos[k];
+            const int w = __float_as_int(pj.w);
+            j = w & 0x0FFFFFFF;
+            sj = w >> 28;
+            S = cshift[k];
+            if (!(j == i && S == zero)) {
+              // explicit round-to-nearest ops, as visit_pairs (the shift is already in pj)
+              const float dx = __fsub_rn(pj.x, xi);
+              const float dy = __fsub_rn(pj.y, yi);
+              const float dz = __fsub_rn(pj.z, zi);
+              const float d2f = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+              exact = fabsf(d2f - rc2f) <= margin || d2f <= margin;
+              cand = exact || d2f < rc2f;
+            }
+          }
+        };
+        auto decide = [&](int j, int sj, int S, bool cand, bool exact) {
+          const int S1 = ((S >> 16) & 255) - 128, S2 = ((S >> 8) & 255) - 128, S3 = (S & 255) - 128;
+          bool keep = false;
+          double r[3] = {0, 0, 0}, d2 = -1.0, sh[3] = {0, 0, 0};
+          if (cand) {
+            if (exact) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c)
+                sh[c] = __dadd_rn(__dadd_rn(__dmul_rn((double)S1, g.h[c]), __dmul_rn((double)S2, g.h[3 + c])),
+                                  __dmul_rn((double)S3, g.h[6 + c]));
+              const bool canon = (j > i) || (j == i && lex_positive(S1, S2, S3));
+              exact_sep(pos, i, j, sh, canon, r, d2);
+              keep = d2 < rc2;
+              if (keep && d2 == 0.0) atomicOr(b.err, SG_ERR_COINCIDENT);
+            } else {
+              keep = true;
+            }
+          }
+          fn(keep, j, sj, S1, S2, S3, 0.f, 0.f, 0.f, sh, r, d2);
+        };
+        for (int base = 0; base < total; base += 64) {
+          int ja, sja, Sa, jb, sjb, Sb;
+          bool ca_, ea, cb, eb;
+          test(base + lane, ja, sja, Sa, ca_, ea);
+          test(base + 32 + lane, jb, sjb, Sb, cb, eb);
+          decide(ja, sja, Sa, ca_, ea);
+          if (base + 32 < total) decide(jb, sjb, Sb, cb, eb);
+        }
+      }
+      for (int s = 0; s < nsp; ++s) {
+        const int v = warp_sum(percnt[s]);
+        if (lane == 0) b.seg_count[i * nsp + s] = v;
+      }
+      if (lane == 0) {
+        b.slot_count[i] = cnt;
+        atomicMax(b.max_count, cnt);
+      }
+    }
+  }
+}
+
 cudaError_t sg_nbr_slots(const double* pos, const int* species, int n_atoms, int nsp, double rc,
                          int maxn, const NbrBuffers& b, cudaStream_t st) {
   cudaMemsetAsync(b.max_count, 0, sizeof(int), st);
-  if (n_atoms > 0) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // by bin pays when the bins alone fill the GPU: a single structure with a few bins per SM
+  const bool by_atom = b.sweep == 2 || (b.sweep == 0 && (b.n_struct > 1 || b.n_bins < 8 * sms));
+  if (n_atoms > 0 && by_atom) {
     const int threads = 128;
     const long long blocks = ((long long)n_atoms * 32 + threads - 1) / threads;
     fill_slots_kernel<<<(unsigned)blocks, threads, 0, st>>>(pos, species, n_atoms, nsp, rc, maxn, b,
                                                             b.binpos);
+    ++sg_kernel_launches;
+  } else if (n_atoms > 0 && b.n_bins > 0) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fill_slots_bins_kernel, NB_WARPS * 32, 0);
+    const long long grid = std::min<long long>(b.n_bins, (long long)sms * std::max(1, per_sm));
+    fill_slots_bins_kernel<<<(unsigned)grid, NB_WARPS * 32, 0, st>>>(pos, nsp, rc, maxn, b, b.binpos);
     ++sg_kernel_launches;
   }
   cudaError_t e = cudaGetLastError();

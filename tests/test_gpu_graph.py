@@ -156,16 +156,17 @@ def test_every_tile_plan_gives_the_same_results(batched):
     model = make_model(w.params(), w.n_sparse, w.zeta)
     s = Structures.from_batch(batch)
     ref = {k: v.clone() for k, v in model.compute(s, **OUT).items()}
-    assert model.plan(s) == {"adjoint_warps": 0, "gap_forward": 0, "gap_backward": 0}
+    assert model.plan(s) == {"adjoint_warps": 0, "gap_forward": 0, "gap_backward": 0, "neighbour_sweep": 0}
     for warps, fwd, bwd in itertools.product((2, 4, 5), range(3), range(4)):
-        model.set_plan(s, {"adjoint_warps": warps, "gap_forward": fwd, "gap_backward": bwd})
+        model.set_plan(s, {"adjoint_warps": warps, "gap_forward": fwd, "gap_backward": bwd,
+                           "neighbour_sweep": (fwd + bwd) % 3})
         out = model.compute(s, **OUT)
         # norm-wise: the local energies are sums of terms far larger than themselves, so
         # their last bits follow the partial-sum layout of the forward tile shape
         for k, bar in (("forces", 1e-5), ("e_struct", 1e-5), ("e_atom", 5e-5)):
             assert rel(out[k], ref[k]) < bar, (k, warps, fwd, bwd, rel(out[k], ref[k]))
     with pytest.raises(SoapGapError) as err:
-        model.set_plan(s, {"adjoint_warps": 6, "gap_forward": 0, "gap_backward": 0})
+        model.set_plan(s, {"adjoint_warps": 6, "gap_forward": 0, "gap_backward": 0, "neighbour_sweep": 0})
     assert err.value.code == L.E_INVALID_ARG
 
 

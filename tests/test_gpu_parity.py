@@ -80,9 +80,12 @@ def oracle_pairs(batch, r_cut, centers=None):
 SMALL_BATCH = synth.batched_boxes(10, n_lo=4, n_hi=150, seed=77)
 
 
+@pytest.mark.parametrize("sweep", [1, 2])
 @pytest.mark.parametrize("case", ["box64_n6l6", "box1000_n8l8", "twospecies4096_n8l8", "batch",
                                   "triclinic_small"])
-def test_pair_list_bit_exact(case):
+def test_pair_list_bit_exact(case, sweep):
+    """Both candidate sweeps (per bin from staged shared memory, per atom) give the oracle's
+    pair list exactly."""
     if case == "batch":
         batch, P = SMALL_BATCH, Params(r_cut=4.5, r_soft=4.0, sigma_r0=0.5, sigma_p0=0.5)
     elif case == "triclinic_small":
@@ -93,7 +96,10 @@ def test_pair_list_bit_exact(case):
         w = synth.get_workload(case)
         batch, P = w.structures(), Params.from_dict(w.params())
     m = model_for(params_dict(P), "mixed")
-    m.compute(structures(batch), desc=True)
+    s = structures(batch)
+    m.compute(s, desc=True)
+    m.set_plan(s, {"adjoint_warps": 0, "gap_forward": 0, "gap_backward": 0, "neighbour_sweep": sweep})
+    m.compute(s, desc=True)
     gi, gj, gs = m.pairs()
     oi, oj, os_ = oracle_pairs(batch, P.r_cut)
     assert len(gi) == len(oi)
@@ -426,7 +432,8 @@ def test_failed_evaluation_leaves_no_forward_for_the_adjoint():
     assert torch.equal(model.backward(s_good, w), g0)
 
 
-def test_pair_list_dense_corner_cluster():
+@pytest.mark.parametrize("sweep", [1, 2])
+def test_pair_list_dense_corner_cluster(sweep):
     """Atoms squeezed into one corner of a large cell: far more neighbours per atom than the
     cell's mean density predicts, so the library's first neighbour sweep overflows its
     per-atom slots and is redone with the measured count.  The pair list must still equal
@@ -436,7 +443,10 @@ def test_pair_list_dense_corner_cluster():
     batch.pos[:] = batch.pos * 0.55          # same cell, 6x the local density
     P = Params(r_cut=5.0, r_soft=4.5, sigma_r0=0.5, sigma_p0=0.5, n_max=6, l_max=6)
     m = model_for(params_dict(P), "mixed")
-    m.compute(structures(batch), desc=True)
+    s = structures(batch)
+    m.compute(s, desc=True)
+    m.set_plan(s, {"adjoint_warps": 0, "gap_forward": 0, "gap_backward": 0, "neighbour_sweep": sweep})
+    m.compute(s, desc=True)
     gi, gj, gs = m.pairs()
     oi, oj, os_ = oracle_pairs(batch, P.r_cut)
     assert len(gi) == len(oi)
@@ -508,7 +518,8 @@ def test_adjoint_variants_against_oracle(name, m_sparse, sampled):
         f_ref = gap.evaluate(batch, P, qs, al, zeta, W=W, virial=False)["forces"]
     forces = {}
     for variant in (5, 4, 2):
-        model.set_plan(s, {"adjoint_warps": variant, "gap_forward": 0, "gap_backward": 0})
+        model.set_plan(s, {"adjoint_warps": variant, "gap_forward": 0, "gap_backward": 0,
+                           "neighbour_sweep": 0})
         f = model.compute(s, energy=True, forces=True)["forces"].cpu().numpy()
         forces[variant] = f
         err = rel_all(f[atoms], f_ref)
