@@ -234,7 +234,7 @@ def stage_rooflines(stages, n_pairs, n_atoms, w, alu):
 
 
 # --------------------------------------------------------------------------- arms
-def profiled_traffic(w, stage, n_atoms):
+def profiled_traffic(w, stage, n_atoms, plan=None):
     """DRAM bytes per launch of the dominant kernel from the committed ncu summary
     (profiles/traffic_<workload>.json), or None when there is none for this stage and size or
     the kernel's source files have changed since the counters were taken."""
@@ -245,6 +245,8 @@ def profiled_traffic(w, stage, n_atoms):
             rec = json.load(f)
         if rec.get("stage") != stage or rec["scaled_to"]["atoms"] != n_atoms:
             return None
+        if plan is not None and rec.get("plan_adjoint") not in (None, plan.get("adjoint_warps")):
+            return None  # the counters were taken on the other adjoint kernel
         h = hashlib.sha256()
         for fn in rec["source_files"]:
             with open(os.path.join(ROOT, fn), "rb") as f:
@@ -769,7 +771,7 @@ def run_ours(args, rank, world, local_rank):
                     "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                     "contraction_only_frac": cflops / (stages[dom] / 1e3) / 1e12 / fp32_peak,
                     "peak_source": FP32_PEAK_NOTE}
-    roofline.update({"traffic": profiled_traffic(w, dom, n),
+    roofline.update({"traffic": profiled_traffic(w, dom, n, tuned),
                      "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
                      "flops_per_launch": flops})
     md = run_md(model, s, stream, max(args.steps, 20)) if not args.no_md else None
