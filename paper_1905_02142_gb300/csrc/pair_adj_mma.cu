@@ -151,6 +151,9 @@ __device__ __forceinline__ void adj_sweep_unrolled(const YlmCoef<float>& yc, flo
   constexpr int LP = LC + 1;
   constexpr int TE = (LC + 2) & ~1;
   float cm = 1.f, sm = 0.f, cmm1 = 0.f, smm1 = 0.f;
+  // column m + 1 of the recursion, computed at step m for the z-derivatives, is column m of
+  // step m + 1: kept here (registers, the loops being unrolled) instead of recomputed
+  float col[LC + 2];
 #pragma unroll
   for (int m = 0; m <= LC; ++m) {
     if (m > 0) {
@@ -165,7 +168,9 @@ __device__ __forceinline__ void adj_sweep_unrolled(const YlmCoef<float>& yc, flo
 #pragma unroll
     for (int l = m; l <= LC; ++l) {
       float pl, ql = 0.f;
-      if (l == m) {
+      if (m > 0) {
+        pl = col[l];
+      } else if (l == m) {
         pl = a1;
       } else {
         pl = (l == m + 1) ? (yc.s1[m] * uz) * a1 : fmaf(yc.a[l][m] * uz, a1, -yc.b[l][m] * a2);
@@ -180,6 +185,7 @@ __device__ __forceinline__ void adj_sweep_unrolled(const YlmCoef<float>& yc, flo
           b2 = b1;
           b1 = ql;
         }
+        col[l] = ql;
       }
       const float dz = yc.d[l][m] * ql;
       const float il = il_l[32 * l], dil = il_l[32 * (LP + l)];
