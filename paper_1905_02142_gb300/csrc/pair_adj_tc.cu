@@ -174,13 +174,14 @@ __device__ __forceinline__ void tc_sweep(const YlmCoef<float>& yc, float ux, flo
       } else {
         const float uc = __uint_as_float(ur[k]), us = __uint_as_float(ur[k + 1]);
         const float pc = __uint_as_float(upr[k]), ps = __uint_as_float(upr[k + 1]);
-        const float wc = uc * il, ws = us * il;
-        Rc = fmaf(fmaf(pc, il, uc * dil), pl, Rc);
-        Rs = fmaf(fmaf(ps, il, us * dil), pl, Rs);
-        Xc = fmaf(wc, pl, Xc);
-        Xs = fmaf(ws, pl, Xs);
-        Zc = fmaf(wc, dz, Zc);
-        Zs = fmaf(ws, dz, Zs);
+        // the radial and harmonic factors shared by the cos- and sin-type entries
+        const float e = il * pl, f = dil * pl, g = il * dz;
+        Rc = fmaf(pc, e, fmaf(uc, f, Rc));
+        Rs = fmaf(ps, e, fmaf(us, f, Rs));
+        Xc = fmaf(uc, e, Xc);
+        Xs = fmaf(us, e, Xs);
+        Zc = fmaf(uc, g, Zc);
+        Zs = fmaf(us, g, Zs);
       }
     }
     if (m == 0) {
