@@ -36,6 +36,10 @@ using namespace tc5;
 // Columns an epilogue takes per TMEM read: Epi::CHUNK (24 or 32) if declared, else 32.
 template <class E, class = void> struct EpiChunk { static constexpr int value = 32; };
 template <class E> struct EpiChunk<E, std::void_t<decltype(E::CHUNK)>> { static constexpr int value = E::CHUNK; };
+// Epilogues with Epi::STAGED write a 32 x 32 FP16 output box per chunk through shared memory
+// and a TMA store (two 2 KB staging buffers per epilogue warp).
+template <class E, class = void> struct EpiStaged { static constexpr bool value = false; };
+template <class E> struct EpiStaged<E, std::void_t<decltype(E::STAGED)>> { static constexpr bool value = E::STAGED; };
 
 // ------------------------------------------------------------------ epilogues
 struct EpiStore {  // C = A B^T (diagnostic)
@@ -60,6 +64,7 @@ __device__ __forceinline__ float pow_zm1(float s) {
 }
 
 struct EpiGapFwd {
+  static constexpr bool STAGED = true;  // kp through shared memory and TMA stores
   int rows, ld_kp, n_tiles, izeta;
   float zeta;
   const float *u, *nrm;              // [N]
@@ -92,9 +97,8 @@ struct EpiGapFwd {
       out[j / 2] = *reinterpret_cast<const uint32_t*>(&h2);
     }
   }
-  __device__ void apply(int row, int col0, const uint32_t* v) {
-    if (row >= rows) return;
-    uint32_t out[16];   // 32 FP16 kernel derivatives, packed in pairs (registers)
+  // S-dependent sums of one row's 32 columns; out: their 32 FP16 kernel derivatives in pairs
+  __device__ __forceinline__ void row_chunk(int col0, const uint32_t* v, uint32_t* out) {
     switch (izeta) {
       case 1: run<1>(col0, v, out); break;
       case 2: run<2>(col0, v, out); break;
@@ -102,6 +106,39 @@ struct EpiGapFwd {
       case 4: run<4>(col0, v, out); break;
       default: run<0>(col0, v, out); break;
     }
+  }
+  // The warp's 32 rows (row0 ..) x 32 columns (col0 ..): sums in registers; with kp, the
+  // kernel derivatives go to this warp's staging buffer `buf` (64 B per row) and one lane
+  // stores the 32 x 32 box with TMA (rows past the end are clipped by the tensor map).
+  __device__ void apply_staged(int row, int row0, int col0, const uint32_t* v, unsigned char* stage, int& buf,
+                               const CUtensorMap* map) {
+    const int lane = threadIdx.x & 31;
+    uint32_t out[16];
+    if (row < rows) {
+      row_chunk(col0, v, out);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) out[k] = 0u;
+    }
+    if (!kp) return;
+    if (lane == 0) bulk_wait_read1();  // the store of two chunks ago has read this buffer
+    __syncwarp();
+    unsigned char* sb = stage + buf * 2048;
+    uint4* dst = reinterpret_cast<uint4*>(sb + lane * 64);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dst[k] = make_uint4(out[4 * k], out[4 * k + 1], out[4 * k + 2], out[4 * k + 3]);
+    fence_proxy_async();
+    __syncwarp();
+    if (lane == 0) {
+      if (row0 < rows) tma_store_2d(map, col0, row0, sb);  // (a box wholly past the end: nothing)
+      bulk_commit();
+    }
+    buf ^= 1;
+  }
+  __device__ void apply(int row, int col0, const uint32_t* v) {
+    if (row >= rows) return;
+    uint32_t out[16];   // 32 FP16 kernel derivatives, packed in pairs (registers)
+    row_chunk(col0, v, out);
     if (kp) {
       uint4* dst = reinterpret_cast<uint4*>(kp + (size_t)row * ld_kp + col0);
 #pragma unroll
@@ -262,7 +299,7 @@ struct EpiDesignGrad {
 template <int BN, int STAGES, int EPI_WARPS, class Epi, bool MFAST = false>
 __global__ void __launch_bounds__(32 * (2 + EPI_WARPS), 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-               int num_kb, int m_tiles, int n_tiles, Epi epi, int* err) {
+               const __grid_constant__ CUtensorMap tmC, int num_kb, int m_tiles, int n_tiles, Epi epi, int* err) {
   constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
   constexpr int HALVES = EPI_WARPS / 4;           // column groups per tile
   constexpr int COLS = BN / HALVES;               // columns per epilogue warp
@@ -369,6 +406,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int ew = warp - 2;                 // 0 .. EPI_WARPS-1
     const int lg = warp & 3;                 // TMEM lane group this warp may access
     const int half = ew / 4;                 // column group
+    unsigned char* stage = sB + STAGES * B_BYTES + ew * 4096;  // staged epilogues only
+    int buf = 0;
     int lt = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++lt) {
       const int b = lt & 1, use = lt >> 1;
@@ -396,12 +435,17 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           tmem_ld8_nw(ta + 16, v + 16);
           tmem_wait();
         }
-        epi.apply(row, n0 + col, v);
+        if constexpr (EpiStaged<Epi>::value) epi.apply_staged(row, m0 + lg * 32, n0 + col, v, stage, buf, &tmC);
+        else epi.apply(row, n0 + col, v);
       }
       epi.end(row, (MFAST ? t / m_tiles : t % n_tiles) * HALVES + half);
       fence_before();
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty_bar[b])) : "memory");
+    }
+    if constexpr (EpiStaged<Epi>::value) {
+      if (lane == 0) bulk_wait_all();  // every TMA store of this warp has completed
+      __syncwarp();
     }
   }
   fence_before();
@@ -411,9 +455,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                  : "memory");
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, int EPI_WARPS = 0, bool STAGED = false>
 constexpr size_t smem_bytes() {
-  return (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 1024;
+  return (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 1024 + (STAGED ? (size_t)EPI_WARPS * 4096 : 0);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -443,17 +487,31 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int box_rows
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 2D FP16 output [rows][cols] (row stride cols) written in boxes of 32 x 32 by TMA stores
+bool make_store_map(CUtensorMap* m, void* base, int rows, int cols) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 // C = A B^T over K = k; lda, ldb: row strides of A and B in elements (k when 0)
 template <int BN, int STAGES, int EPI_WARPS, bool MFAST = false, class Epi>
 cudaError_t launch_gemm(const void* A, int a_rows, const void* B, int b_rows, int k, Epi epi, int* err,
-                        cudaStream_t st, int lda = 0, int ldb = 0) {
+                        cudaStream_t st, int lda = 0, int ldb = 0, const CUtensorMap* mc = nullptr) {
   if (k % BK != 0 || a_rows <= 0 || b_rows <= 0) return cudaErrorInvalidValue;
   if ((lda > 0 && lda < k) || (ldb > 0 && ldb < k)) return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, a_rows, k, BM, lda) || !make_map(&mb, B, b_rows, k, BN, ldb))
     return cudaErrorInvalidValue;
   auto kern = tc_gemm_kernel<BN, STAGES, EPI_WARPS, Epi, MFAST>;
-  constexpr size_t smem = smem_bytes<BN, STAGES>();
+  constexpr size_t smem = smem_bytes<BN, STAGES, EPI_WARPS, EpiStaged<Epi>::value>();
+  static_assert(smem <= 227 * 1024, "shared memory per block");
   cudaError_t e = sg_set_smem<tc_gemm_kernel<BN, STAGES, EPI_WARPS, Epi, MFAST>>(smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
@@ -462,7 +520,7 @@ cudaError_t launch_gemm(const void* A, int a_rows, const void* B, int b_rows, in
   const int m_tiles = (a_rows + BM - 1) / BM, n_tiles = (b_rows + BN - 1) / BN;
   if ((long long)m_tiles * n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
   const int grid = std::min(sms, m_tiles * n_tiles);
-  kern<<<grid, 32 * (2 + EPI_WARPS), smem, st>>>(ma, mb, k / BK, m_tiles, n_tiles, epi, err);
+  kern<<<grid, 32 * (2 + EPI_WARPS), smem, st>>>(ma, mb, mc ? *mc : ma, k / BK, m_tiles, n_tiles, epi, err);
   ++sg_kernel_launches;
   return cudaGetLastError();
 }
@@ -551,10 +609,14 @@ cudaError_t sg_gap_tc_forward(const GapTcModel& md, int terms, const __half* A, 
   // one FP16 product hi.hi: A rows [hi] against the first dp columns of the sparse rows
   // [hi | lo | hi]; three: A rows [hi | hi | lo] against the whole rows
   const int k = terms * md.dp, lda = terms * md.dp, ldb = 3 * md.dp;
+  // the kernel derivatives [n][mp] leave through shared memory in 32 x 32 TMA stores
+  CUtensorMap mc;
+  if (kp && !make_store_map(&mc, kp, n, md.mp)) return cudaErrorInvalidValue;
+  const CUtensorMap* pmc = kp ? &mc : nullptr;
   switch (md.fwd_cfg) {
-    case 0: return launch_gemm<256, 4, 8>(A, n, md.B, md.mp, k, e, err, st, lda, ldb);
-    case 1: return launch_gemm<128, 6, 4>(A, n, md.B, md.mp, k, e, err, st, lda, ldb);
-    case 2: return launch_gemm<128, 6, 8>(A, n, md.B, md.mp, k, e, err, st, lda, ldb);
+    case 0: return launch_gemm<256, 4, 8>(A, n, md.B, md.mp, k, e, err, st, lda, ldb, pmc);
+    case 1: return launch_gemm<128, 6, 4>(A, n, md.B, md.mp, k, e, err, st, lda, ldb, pmc);
+    case 2: return launch_gemm<128, 6, 8>(A, n, md.B, md.mp, k, e, err, st, lda, ldb, pmc);
     default: return cudaErrorInvalidValue;
   }
 }
