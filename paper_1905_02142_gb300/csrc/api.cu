@@ -778,6 +778,7 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
   ENS(h, h->c, es * N1 * nch * L);
   ENS(h, h->q, es * N1 * D);
   ENS(h, h->pnorm, es * N1);
+  bool fused_operand = false;  // A16 / nrm / uq written by the power-spectrum kernel
   if (!backward) {
     mark(h, EV_FILL0, st);
     if (rebuild || device_decides) {
@@ -824,7 +825,19 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     fa.c = (T*)h->c.p;
     CK(h, sg_pair_forward<T>(fa, h->cls, h->mixed, st));
     mark(h, EV_PS0, st);
-    CK(h, sg_power_spectrum<T>((const T*)h->c.p, N, nch, h->prm.l_max, (T*)h->q.p, (T*)h->pnorm.p, st));
+    GapOperand op{};
+    if constexpr (sizeof(T) == 4) {
+      if (want_energy) {
+        // the tensor-core GAP operand of each atom is written by the power-spectrum kernel
+        const GapTcModel& tm = h->tcm;
+        ENS(h, h->A16, sizeof(__half) * N1 * tm.terms * tm.dp);
+        ENS(h, h->nrm, sizeof(float) * N1);
+        ENS(h, h->uq, sizeof(float) * N1);
+        op = GapOperand{(__half*)h->A16.p, (float*)h->nrm.p, (float*)h->uq.p, tm.qbar, tm.dp, tm.terms};
+        fused_operand = true;
+      }
+    }
+    CK(h, sg_power_spectrum<T>((const T*)h->c.p, N, nch, h->prm.l_max, (T*)h->q.p, (T*)h->pnorm.p, st, op));
     if ((flags & SOAPGAP_DESC) && q_out)
       CK(h, cudaMemcpyAsync(q_out, h->q.p, es * (size_t)N * D, cudaMemcpyDeviceToDevice, st));
     if ((flags & SOAPGAP_DESC) && pnorm_out)
@@ -858,8 +871,9 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
       ENS(h, h->uq, sizeof(float) * N1);
       ENS(h, h->r_part, sizeof(float) * N1 * tiles_alloc);
       if (want_grad) ENS(h, h->kp16, sizeof(__half) * N1 * tm.mp);
-      CK(h, sg_gap_tc_prepare((const float*)h->q.p, N, D, tm.dp, tm.qbar, (__half*)h->A16.p,
-                              (float*)h->nrm.p, (float*)h->uq.p, tm.terms, st));
+      if (!fused_operand)
+        CK(h, sg_gap_tc_prepare((const float*)h->q.p, N, D, tm.dp, tm.qbar, (__half*)h->A16.p,
+                                (float*)h->nrm.p, (float*)h->uq.p, tm.terms, st));
       CK(h, sg_gap_tc_forward(tm, tm.terms, (const __half*)h->A16.p, (const float*)h->nrm.p, (const float*)h->uq.p, N,
                               (float*)h->eps_part.p, (float*)h->r_part.p,
                               want_grad ? (__half*)h->kp16.p : nullptr, (int*)h->err.p, st));

@@ -136,9 +136,18 @@ template <typename T> cudaError_t sg_pair_forward(const FwdArgs<T>& a, int cls, 
                                                   cudaStream_t st);
 
 // ---------------------------------------------------------------- powspec.cu
+// The mixed path's GAP operand of each atom, written by the power-spectrum kernel when a16
+// is set (the same values as sg_gap_tc_prepare; FP32 descriptors only).
+struct GapOperand {
+  __half* a16;        // [N][terms * dp]
+  float* nrm;         // [N] |q - qbar|
+  float* uq;          // [N] qbar.(q - qbar)
+  const float* qbar;  // [dp]
+  int dp, terms;
+};
 template <typename T>
 cudaError_t sg_power_spectrum(const T* c, int n_atoms, int nch, int lmax, T* q, T* pnorm,
-                              cudaStream_t st);
+                              cudaStream_t st, const GapOperand& op = GapOperand{});
 
 // ---------------------------------------------------------------- gap_simt.cu
 // eps_part[i][t] = sum over sparse tile t of alpha_s S_is^zeta,

@@ -5,9 +5,40 @@
 
 #include "internal.h"
 
+// Optional GAP operand of the mixed path (op.a16 set): from q in shared memory, u = (q - qbar)
+// / |q - qbar| in FP16 ([hi] or [hi | hi | lo] by op.terms), |q - qbar| and qbar.(q - qbar),
+// in the operation order of prep_atoms_kernel (gap_tc.cu).
+template <typename T>
+__device__ __forceinline__ void gap_operand(const GapOperand& op, int atom, const T* qs, int D, int lane) {
+  float s2 = 0.f, dq = 0.f;
+  for (int k = lane; k < D; k += 32) {
+    const float t = (float)qs[k] - op.qbar[k];
+    s2 = fmaf(t, t, s2);
+    dq = fmaf(t, op.qbar[k], dq);
+  }
+  s2 = warp_sum(s2);
+  dq = warp_sum(dq);
+  const float nn = sqrtf(s2);
+  const float iv = nn > 0.f ? 1.f / nn : 0.f;
+  __half* row = op.a16 + (size_t)atom * op.terms * op.dp;
+  for (int k = lane; k < op.dp; k += 32) {
+    const float uk = k < D ? ((float)qs[k] - op.qbar[k]) * iv : 0.f;
+    const __half hi = __float2half_rn(uk);
+    row[k] = hi;
+    if (op.terms == 3) {
+      row[op.dp + k] = hi;
+      row[2 * op.dp + k] = __float2half_rn(uk - __half2float(hi));
+    }
+  }
+  if (lane == 0) {
+    op.nrm[atom] = nn;
+    op.uq[atom] = dq;
+  }
+}
+
 template <typename T>
 __global__ void powspec_kernel(const T* __restrict__ c, int n_atoms, int nch, int lmax,
-                               int per_warp, T* q, T* pnorm) {
+                               int per_warp, T* q, T* pnorm, GapOperand op) {
   // one warp per atom: c staged in shared memory, each lane owns whole channel pairs
   // (c1 <= c2) and all their l, the unnormalised p stays in shared memory until |p| is known
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -51,13 +82,21 @@ __global__ void powspec_kernel(const T* __restrict__ c, int n_atoms, int nch, in
     const T inv = T(1) / norm;
     __syncwarp();
     T* qi = q + (size_t)atom * D;
-    for (int k = lane; k < D; k += 32) qi[k] = ps[k] * inv;
+    for (int k = lane; k < D; k += 32) {
+      const T v = ps[k] * inv;
+      qi[k] = v;
+      if (op.a16) ps[k] = v;  // q, kept for the GAP operand
+    }
+    if (op.a16) {
+      __syncwarp();
+      gap_operand<T>(op, atom, ps, D, lane);
+    }
   }
 }
 
 template <typename T>
 cudaError_t sg_power_spectrum(const T* c, int n_atoms, int nch, int lmax, T* q, T* pnorm,
-                              cudaStream_t st) {
+                              cudaStream_t st, const GapOperand& op) {
   if (n_atoms == 0) return cudaSuccess;
   const int L = (lmax + 1) * (lmax + 1);
   const int D = nch * (nch + 1) / 2 * (lmax + 1);
@@ -77,10 +116,12 @@ cudaError_t sg_power_spectrum(const T* c, int n_atoms, int nch, int lmax, T* q, 
   long long grid = (long long)sms * per_sm;
   const long long need = (n_atoms + wpb - 1) / wpb;
   if (grid > need) grid = need;
-  kern<<<(unsigned)grid, wpb * 32, smem, st>>>(c, n_atoms, nch, lmax, per_warp, q, pnorm);
+  kern<<<(unsigned)grid, wpb * 32, smem, st>>>(c, n_atoms, nch, lmax, per_warp, q, pnorm, op);
   ++sg_kernel_launches;
   return cudaGetLastError();
 }
 
-template cudaError_t sg_power_spectrum<float>(const float*, int, int, int, float*, float*, cudaStream_t);
-template cudaError_t sg_power_spectrum<double>(const double*, int, int, int, double*, double*, cudaStream_t);
+template cudaError_t sg_power_spectrum<float>(const float*, int, int, int, float*, float*, cudaStream_t,
+                                              const GapOperand&);
+template cudaError_t sg_power_spectrum<double>(const double*, int, int, int, double*, double*, cudaStream_t,
+                                               const GapOperand&);

@@ -527,3 +527,47 @@ def test_adjoint_variants_against_oracle(name, m_sparse, sampled):
         assert err < MIXED["f"]
     assert rel_all(forces[5], forces[4]) < 1e-5
     assert rel_all(forces[2], forces[4]) < 1e-5
+
+
+def test_adjoint_variants_on_dense_cluster_and_empty_structures():
+    """Edges of the tcgen05 adjoint and the per-bin neighbour sweep, forced through the tile
+    plan: atoms squeezed into a corner (~470 pairs per atom: several 128-pair MMA tiles per
+    atom, and bins over the shared-memory capacity), and a batch with empty structures and an
+    isolated atom; forces against the oracle and against the mma.sync kernel."""
+    P = Params(r_cut=5.0, r_soft=4.5, sigma_r0=0.5, sigma_p0=0.5, n_max=6, l_max=6)
+    W = oracle_W(P.n_max, P.r_cut, P.sigma_r0)
+    qs = soap.descriptors(synth.concat([synth.random_box(24, density=0.15, dmin=1.2, seed=43)]), P,
+                          W=W)["q"].numpy()
+    al = synth.gap_weights(len(qs), 44)
+    base = synth.random_box(300, density=0.15, dmin=1.2, seed=41)
+    dense = synth.concat([base])
+    dense.pos[:] = dense.pos * 0.55
+    lone = synth.Structure(pos=np.array([[5.0, 5.0, 5.0]]), cell=np.eye(3) * 20.0,
+                           species=np.zeros(1, np.int32))
+    empty = synth.Structure(pos=np.zeros((0, 3)), cell=np.eye(3) * 9.0, species=np.zeros(0, np.int32))
+    ragged = synth.concat([empty, lone, synth.random_box(16, side=5.0, dmin=1.2, seed=3), empty])
+    for batch, atoms in ((dense, np.array([0, 150])), (ragged, None)):
+        model = model_for(params_dict(P), "mixed", qs, al, 2.0)
+        s = structures(batch)
+        model.compute(s, energy=True)
+        if atoms is None:
+            ref = gap.evaluate(batch, P, qs, al, 2.0, W=W, virial=False)
+            f_ref, idx, e_ref = ref["forces"], np.arange(batch.n_atoms), ref["e_struct"]
+        else:
+            f_ref, idx = gap.forces_at(batch, P, qs, al, 2.0, atoms, W=W)
+            e_ref = None
+        got = {}
+        for variant, sweep in ((5, 1), (4, 2)):
+            model.set_plan(s, {"adjoint_warps": variant, "gap_forward": 0, "gap_backward": 0,
+                               "neighbour_sweep": sweep})
+            out = model.compute(s, energy=True, forces=True)
+            f = out["forces"].cpu().numpy()
+            got[variant] = f
+            err = rel_all(f[idx], f_ref)
+            print(f"PARITY edges {batch.n_atoms} atoms, adjoint {variant}, sweep {sweep}: F {err:.2e}")
+            assert err < MIXED["f"]
+            if e_ref is not None:
+                e = out["e_struct"].cpu().numpy()
+                assert np.allclose(e, e_ref, rtol=MIXED["e"], atol=1e-12)
+                assert e[0] == 0.0 and e[3] == 0.0 and np.all(f[0] == 0.0)
+        assert rel_all(got[5], got[4]) < 1e-5
