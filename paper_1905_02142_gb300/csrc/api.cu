@@ -823,6 +823,7 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     if constexpr (sizeof(T) == 4) { fa.yc = h->yc32; fa.bc = h->bc32; }
     else { fa.yc = h->yc64; fa.bc = h->bc64; }
     fa.c = (T*)h->c.p;
+    fa.err = (int*)h->err.p;
     CK(h, sg_pair_forward<T>(fa, h->cls, h->mixed, st));
     mark(h, EV_PS0, st);
     GapOperand op{};

@@ -131,6 +131,7 @@ template <typename T> struct FwdArgs {
   YlmCoef<T> yc;
   BasisConst<T> bc;       // W (recursion path) and central terms (both)
   T* c;                   // [N][nsp*nmax][L]
+  int* err;               // device error word (SG_ERR_TIMEOUT if a table copy never lands)
 };
 template <typename T> cudaError_t sg_pair_forward(const FwdArgs<T>& a, int cls, bool table,
                                                   cudaStream_t st);

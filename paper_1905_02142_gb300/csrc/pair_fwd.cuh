@@ -5,7 +5,10 @@
 // per lane: the lane evaluates its neighbour's radial coefficients b_n (table path:
 // cubic-Hermite interpolation of FP64-built nodes; recursion path: Eq. 04 per pair in
 // FP64) and the angular factors a_lm = 4 pi ilexp_l(z) Y_lm(r_hat) (real Y_lm from a
-// pole-free recurrence), and stages them in shared memory.  The warp then contracts the
+// pole-free recurrence), and stages them in shared memory.  On the table path each lane
+// first has its pair's table interval (nodes k and k + 1, 4 FP floats) bulk-copied into
+// the warp's a_lm buffer, so the 32 scattered intervals of a batch arrive as 32 bulk
+// copies from L2 instead of 32-way divergent loads through L1.  The warp then contracts the
 // batch, c[n][lm] += sum_k b_n(k) a_lm(k), with every lane owning the columns
 // lm = lane + 32 j for all n, so the sum over neighbours is a register accumulation
 // with no atomics.  The recursion path accumulates in the primitive basis and applies
@@ -14,20 +17,46 @@
 #include "internal.h"
 #include "soapmath.cuh"
 #include "table.cuh"
+#include "tcgen05.cuh"
 
 template <typename T> __device__ __forceinline__ T sq(T x) { return x * x; }
+
+// Shared memory of one warp, in elements of T: the a_lm rows (32 x AS), which on the table
+// path first hold the 32 table intervals (32 x CS, CS = 4 FP + 4 so that the lanes' 16-byte
+// reads of their own intervals fall in distinct banks), then the b_n rows (32 x NP).
+template <typename T, int NC, int LC, bool TABLE> struct FwdSmem {
+  static constexpr int LCC = (LC + 1) * (LC + 1);
+  static constexpr int AS = (LCC % 2 == 0) ? LCC + 1 : LCC;
+  static constexpr int NP = (NC + 3) / 4 * 4;
+  static constexpr int CH = 4 * TableDims<NC, LC>::FP;  // floats of one interval
+  static constexpr int CS = CH + 4;
+  static constexpr int REG_A = (TABLE && CS > AS) ? 32 * CS : 32 * AS;
+  static constexpr int WARP = REG_A + 32 * NP;
+  // all warps' buffers, then one mbarrier per warp (table path)
+  static constexpr size_t bytes() { return (size_t)SG_WARPS * WARP * sizeof(T) + (TABLE ? SG_WARPS * 8 : 0); }
+};
 
 template <typename T, int NC, int LC, bool TABLE>
 __global__ void __launch_bounds__(SG_WARPS * 32)
 pair_fwd_kernel(const FwdArgs<T> a) {
-  constexpr int LCC = (LC + 1) * (LC + 1);
+  using SM = FwdSmem<T, NC, LC, TABLE>;
+  constexpr int LCC = SM::LCC;
   constexpr int LPL = (LCC + 31) / 32;
-  constexpr int AS = (LCC % 2 == 0) ? LCC + 1 : LCC;
-  constexpr int NP = (NC + 3) / 4 * 4;
+  constexpr int AS = SM::AS;
+  constexpr int NP = SM::NP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  T* a_s = reinterpret_cast<T*>(smem_raw) + warp * (32 * AS + 32 * NP);
-  T* b_s = a_s + 32 * AS;
+  T* a_s = reinterpret_cast<T*>(smem_raw) + warp * SM::WARP;
+  T* b_s = a_s + SM::REG_A;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + (size_t)SG_WARPS * SM::WARP * sizeof(T)) + warp;
+  uint32_t phase = 0;
+  if constexpr (TABLE) {
+    if (lane == 0) {
+      tc5::mbar_init(bar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+  }
   const int L = (a.lmax + 1) * (a.lmax + 1);
   const int nch = a.nsp * a.nmax;
   const T FOUR_PI = (T)12.566370614359172;
@@ -45,16 +74,38 @@ pair_fwd_kernel(const FwdArgs<T> a) {
 
       for (int base = beg; base < end; base += 32) {
         const int pidx = base + lane;
-        if (pidx < end) {
-          const Vec4<T> v = a.pair_r[a.pair_idx ? a.pair_idx[pidx] : pidx];
-          // |r| < 0 marks a pair beyond r_cut in a list built with a skin: no contribution
-          const bool live = v.w >= T(0);
-          const T r = live ? v.w : T(1), inv = T(1) / r;
-          const T ux = live ? v.x * inv : T(0), uy = live ? v.y * inv : T(0), uz = live ? v.z * inv : T(1);
-          T bn[NC], il[LC + 1];
+        const bool has = pidx < end;
+        Vec4<T> v{T(0), T(0), T(0), T(-1)};
+        if (has) v = a.pair_r[a.pair_idx ? a.pair_idx[pidx] : pidx];
+        // |r| < 0 marks a pair beyond r_cut in a list built with a skin: no contribution
+        const bool live = v.w >= T(0);
+        const T r = live ? v.w : T(1), inv = T(1) / r;
+        float tt = 0.f;
+        if constexpr (TABLE) {
+          // this batch's table intervals into the a_lm buffer (the previous batch's reads of
+          // it ended at the __syncwarp closing that batch)
+          const int k = table_locate(a.ti, (float)r, tt);
+          const int cnt = min(32, end - base);
+          tc5::fence_proxy_async();
+          if (lane == 0) tc5::mbar_expect_tx(bar, (uint32_t)(cnt * SM::CH * sizeof(float)));
+          __syncwarp();
+          if (has)
+            tc5::bulk_load(a_s + lane * SM::CS, a.table + (size_t)k * (SM::CH / 2), SM::CH * sizeof(float), bar);
+          const bool ok = __all_sync(0xffffffffu, tc5::mbar_wait(bar, phase));
+          phase ^= 1;
+          if (!ok) {
+            // copies that never completed: report, give them one more bounded wait, stop
+            if (lane == 0) atomicOr(a.err, SG_ERR_TIMEOUT);
+            tc5::mbar_wait(bar, phase ^ 1);
+            return;
+          }
+        }
+        T bn[NC], il[LC + 1];
+        if (has) {
           if constexpr (TABLE) {
             float f[NC + LC + 1];
-            table_interp<NC, LC, false>(a.table, a.ti, (float)r, f, nullptr);
+            table_interp_at<NC, LC, false>(reinterpret_cast<const float4*>(a_s + lane * SM::CS), tt, a.ti.inv_h, f,
+                                           nullptr);
 #pragma unroll
             for (int n = 0; n < NC; ++n) bn[n] = f[n];
 #pragma unroll
@@ -71,6 +122,10 @@ pair_fwd_kernel(const FwdArgs<T> a) {
             for (int l = 0; l <= LC; ++l)
               il[l] = (l <= a.lmax) ? (T)(ild[l] * (a.p.eq08 ? (2.0 * l + 1.0) : 1.0)) * FOUR_PI : T(0);
           }
+        }
+        if constexpr (TABLE) __syncwarp();  // every interval read before the a_lm rows overwrite them
+        if (has) {
+          const T ux = live ? v.x * inv : T(0), uy = live ? v.y * inv : T(0), uz = live ? v.z * inv : T(1);
 #pragma unroll
           for (int n = 0; n < NP; ++n) b_s[lane * NP + n] = (n < NC && live) ? bn[n] : T(0);
           T* arow = a_s + lane * AS;
@@ -137,10 +192,7 @@ pair_fwd_kernel(const FwdArgs<T> a) {
 
 template <typename T, int NC, int LC, bool TABLE>
 static cudaError_t launch_fwd(const FwdArgs<T>& a, cudaStream_t st) {
-  constexpr int LCC = (LC + 1) * (LC + 1);
-  constexpr int AS = (LCC % 2 == 0) ? LCC + 1 : LCC;
-  constexpr int NP = (NC + 3) / 4 * 4;
-  const size_t smem = (size_t)SG_WARPS * (32 * AS + 32 * NP) * sizeof(T);
+  const size_t smem = FwdSmem<T, NC, LC, TABLE>::bytes();
   auto kern = pair_fwd_kernel<T, NC, LC, TABLE>;
   cudaError_t e = sg_set_smem<pair_fwd_kernel<T, NC, LC, TABLE>>(smem);
   if (e != cudaSuccess) return e;

@@ -14,29 +14,42 @@ template <int NC, int LC> struct TableDims {
   static constexpr int FP = NCP + LPP;              // floats per half-node
 };
 
-// f[0..NC) = b_n(r), f[NC..NC+LC] = 4 pi ilexp_l(r); df = d/dr of the same (if DERIV).
-template <int NC, int LC, bool DERIV>
-__device__ __forceinline__ void table_interp(const float* __restrict__ tab, const TableInfo& ti,
-                                             float r, float* f, float* df) {
-  using TD = TableDims<NC, LC>;
-  constexpr int Q = TD::FP / 4;  // float4 per half-node
+// Interval of r: node index k (the interval [r_k, r_k+1], clamped to the table) and the
+// fraction t of the way through it.
+__device__ __forceinline__ int table_locate(const TableInfo& ti, float r, float& t) {
   const float x = r * ti.inv_h;
   int k = (int)x;
   k = k < 0 ? 0 : (k >= ti.K ? ti.K - 1 : k);
-  const float t = x - (float)k;
-  const float4* n0 = reinterpret_cast<const float4*>(tab) + (size_t)k * 2 * Q;
+  t = x - (float)k;
+  return k;
+}
+
+// Cubic-Hermite interpolation from the 4 FP floats of one interval (nodes k and k + 1),
+// in global memory (GLOBAL: read-only loads) or in a shared-memory copy:
+// f[0..NC) = b_n(r), f[NC..NC+LC] = 4 pi ilexp_l(r); df = d/dr of the same (if DERIV).
+template <int NC, int LC, bool DERIV, bool GLOBAL = false>
+__device__ __forceinline__ void table_interp_at(const float4* __restrict__ n0, float t, float invh, float* f,
+                                                float* df) {
+  using TD = TableDims<NC, LC>;
+  constexpr int Q = TD::FP / 4;  // float4 per half-node
   const float t2 = t * t;
   const float h00 = (2.f * t - 3.f) * t2 + 1.f, h10 = ((t - 2.f) * t + 1.f) * t;
   const float h01 = (3.f - 2.f * t) * t2, h11 = (t - 1.f) * t2;
   const float d00 = 6.f * t * (t - 1.f), d10 = (3.f * t - 4.f) * t + 1.f, d11 = (3.f * t - 2.f) * t;
-  const float invh = ti.inv_h;
   float4 v0[Q], g0[Q], v1[Q], g1[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    v0[q] = __ldg(n0 + q);
-    g0[q] = __ldg(n0 + Q + q);
-    v1[q] = __ldg(n0 + 2 * Q + q);
-    g1[q] = __ldg(n0 + 3 * Q + q);
+    if constexpr (GLOBAL) {
+      v0[q] = __ldg(n0 + q);
+      g0[q] = __ldg(n0 + Q + q);
+      v1[q] = __ldg(n0 + 2 * Q + q);
+      g1[q] = __ldg(n0 + 3 * Q + q);
+    } else {
+      v0[q] = n0[q];
+      g0[q] = n0[Q + q];
+      v1[q] = n0[2 * Q + q];
+      g1[q] = n0[3 * Q + q];
+    }
   }
 #pragma unroll
   for (int j = 0; j < TD::FP; ++j) {
@@ -52,4 +65,15 @@ __device__ __forceinline__ void table_interp(const float* __restrict__ tab, cons
     f[o] = h00 * a0 + h10 * b0 + h01 * a1 + h11 * b1;
     if (DERIV) df[o] = (d00 * (a0 - a1) + d10 * b0 + d11 * b1) * invh;
   }
+}
+
+// The same, reading the interval of r from the table in global memory.
+template <int NC, int LC, bool DERIV>
+__device__ __forceinline__ void table_interp(const float* __restrict__ tab, const TableInfo& ti,
+                                             float r, float* f, float* df) {
+  constexpr int Q = TableDims<NC, LC>::FP / 4;
+  float t;
+  const int k = table_locate(ti, r, t);
+  const float4* n0 = reinterpret_cast<const float4*>(tab) + (size_t)k * 2 * Q;
+  table_interp_at<NC, LC, DERIV, true>(n0, t, ti.inv_h, f, df);
 }
