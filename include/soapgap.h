@@ -209,17 +209,20 @@ int soapgap_sync_status(soapgap_handle* h, void* stream);
  *   plan[3]  the neighbour sweep: 1 = one block per bin, the bin's candidates staged once in
  *            shared memory; 2 = one warp per atom; 0 = per bin for a single structure with at
  *            least 8 bins per SM, else per atom (timed only without a Verlet skin)
+ *   plan[4]  the forward pair kernel's neighbour contraction c[n][lm] += b_n a_lm: 1 = FP32
+ *            FMA on the lanes; 2 = tensor cores (mma.sync m16n8k16, FP16 hi/lo operands,
+ *            three products, FP32 accumulation); 0 = FP32 FMA
  * and keeps the fastest of each for the batch's problem class (basis class, species count,
  * 32-pair batches per atom, power of two of the atom count).  Later calls on the handle
- * in that class use the plan; classes without one use {0 (by pairs per atom), 0, 0, 0}.  The
+ * in that class use the plan; classes without one use {0 (by pairs per atom), 0, 0, 0, 0}.  The
  * results do not depend on the plan beyond the order of floating-point sums.  `plan` (may
  * be NULL) receives the choice (on the FP64 path only the neighbour sweep is tuned).
  * Synchronises; afterwards soapgap_backward needs a new evaluation. */
-#define SOAPGAP_PLAN_LEN 4
+#define SOAPGAP_PLAN_LEN 5
 int soapgap_autotune(soapgap_handle* h, const soapgap_batch* batch, int32_t* plan, void* stream);
 
 /* Tile plan of the batch's problem class: soapgap_get_plan writes it to plan[SOAPGAP_PLAN_LEN]
- * (the defaults {0, 0, 0, 0} if none was tuned or set); soapgap_set_plan installs one (e.g. read
+ * (the defaults {0, 0, 0, 0, 0} if none was tuned or set); soapgap_set_plan installs one (e.g. read
  * back from a cache of earlier tuning runs).  Both need a synchronous evaluation of this
  * batch on the handle first (its pair count fixes the class): SOAPGAP_E_STATE otherwise;
  * SOAPGAP_E_INVALID_ARG for an entry out of range (plan[0] may also be 0: chosen by the

@@ -29,7 +29,7 @@ DESIGN_DK = 256
 N_DESIGN_STAGES = 4
 DESIGN_STAGES = ("descriptors", "kernel_rows", "jacobian", "force_rows")
 N_STAGES = 7
-PLAN_LEN = 4
+PLAN_LEN = 5
 PEAK_FP32_FMA = 0
 PEAK_FP64_FMA = 1
 STAGES = ("neighbours", "pair_forward", "power_spectrum", "gap_forward", "gap_backward",

@@ -260,7 +260,7 @@ class SoapGap:
         st = (stream or torch.cuda.current_stream()).cuda_stream
         self._check(self.lib.soapgap_sync_status(self.h, st))
 
-    PLAN_KEYS = ("adjoint_warps", "gap_forward", "gap_backward", "neighbour_sweep")
+    PLAN_KEYS = ("adjoint_warps", "gap_forward", "gap_backward", "neighbour_sweep", "pair_forward")
 
     def _plan_cache_key(self, s: Structures) -> str:
         """Problem class of a batch as the library tunes it (after an evaluation of it), with

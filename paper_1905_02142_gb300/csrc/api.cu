@@ -85,6 +85,7 @@ struct soapgap_handle {
   YlmCoef<double> yc64;
   TableInfo ti{}, ti_adj{};
   Buf table, table_adj;      // radial tables: descriptors (and fitting rows), adjoint
+  float fwd_sa = 0.f, fwd_sb = 0.f;  // FP16 operand scales of the tensor-core forward
   // model
   int M = 0;
   double zeta = 0;
@@ -126,7 +127,7 @@ struct soapgap_handle {
   bool async_call = false;        // current call must not allocate or synchronise
   // tile plan per problem class (soapgap_autotune / soapgap_set_plan): adjoint warps per
   // block (0: by pairs per atom) and the configurations of the two GAP products
-  struct TilePlan { int adj_warps = 0, gap_fwd = 0, gap_bwd = 0, nbr_sweep = 0; };
+  struct TilePlan { int adj_warps = 0, gap_fwd = 0, gap_bwd = 0, nbr_sweep = 0, pair_fwd = 0; };
   std::map<long long, TilePlan> plans;
   StructGeom* h_geom = nullptr;   // pinned staging
   size_t h_geom_cap = 0;
@@ -271,6 +272,9 @@ extern "C" int soapgap_create(const soapgap_params* params, soapgap_handle** out
       if (e == cudaSuccess) e = ensure(h->table_adj, (size_t)(h->ti_adj.K + 1) * 2 * h->ti_adj.fp * sizeof(float));
       if (e == cudaSuccess) e = sg_build_table(h->dp, h->bc64, h->cls, h->ti_adj, (float*)h->table_adj.p, 0);
       if (e == cudaSuccess) e = cudaDeviceSynchronize();
+      if (e == cudaSuccess)
+        e = sg_fwd_mma_scales((const float*)h->table.p, h->ti, (h->NC + 3) / 4 * 4, p.n_max, p.l_max, &h->fwd_sa,
+                              &h->fwd_sb);
     }
   }
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_err, sizeof(int));
@@ -590,6 +594,34 @@ static AdjArgs<T> adj_args(soapgap_handle* h, int N, const int* species) {
   return aa;
 }
 
+// arguments of the forward pair kernel (after the neighbour list of this batch)
+template <typename T>
+static FwdArgs<T> fwd_args(soapgap_handle* h, int N, const int* species) {
+  FwdArgs<T> fa{};
+  fa.n_atoms = N; fa.nsp = h->prm.n_species; fa.nmax = h->prm.n_max; fa.lmax = h->prm.l_max;
+  fa.species = species; fa.pair_r = (const Vec4<T>*)h->pair_r.p;
+  fa.seg_offs = h->skin > 0.0 ? (const int*)h->live_offs.p : (const int*)h->seg_offs.p;
+  fa.pair_idx = h->skin > 0.0 ? (const int*)h->live_idx.p : nullptr;
+  fa.table = (const float*)h->table.p; fa.ti = h->ti; fa.p = h->dp;
+  if constexpr (sizeof(T) == 4) { fa.yc = h->yc32; fa.bc = h->bc32; }
+  else { fa.yc = h->yc64; fa.bc = h->bc64; }
+  fa.c = (T*)h->c.p;
+  fa.err = (int*)h->err.p;
+  fa.mma_sa = h->fwd_sa;
+  fa.mma_sb = h->fwd_sb;
+  return fa;
+}
+
+// the forward pair kernel of tile-plan variant v (mixed path: 1 = FP32 FMA contraction,
+// 2 = tensor cores, 0 = the default, FP32 FMA); the FP64 path has one kernel
+template <typename T>
+static cudaError_t launch_forward(const soapgap_handle* h, const FwdArgs<T>& fa, int v, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (v == 2 && sg_pair_forward_mma_supported(h->cls)) return sg_pair_forward_mma(fa, h->cls, st);
+  }
+  return sg_pair_forward<T>(fa, h->cls, h->mixed, st);
+}
+
 template <typename T>
 static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* q_out,
                void* pnorm_out, void* e_atom_out, double* e_struct, double* forces,
@@ -814,17 +846,8 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
     }
     mark(h, EV_FWD0, st);
     h->stage_ran[0] = h->stage_ran[1] = h->stage_ran[2] = true;
-    FwdArgs<T> fa{};
-    fa.n_atoms = N; fa.nsp = nsp; fa.nmax = h->prm.n_max; fa.lmax = h->prm.l_max;
-    fa.species = b->species; fa.pair_r = (const Vec4<T>*)h->pair_r.p;
-    fa.seg_offs = h->skin > 0.0 ? (const int*)h->live_offs.p : nb.seg_offs;
-    fa.pair_idx = h->skin > 0.0 ? (const int*)h->live_idx.p : nullptr;
-    fa.table = (const float*)h->table.p; fa.ti = h->ti; fa.p = h->dp;
-    if constexpr (sizeof(T) == 4) { fa.yc = h->yc32; fa.bc = h->bc32; }
-    else { fa.yc = h->yc64; fa.bc = h->bc64; }
-    fa.c = (T*)h->c.p;
-    fa.err = (int*)h->err.p;
-    CK(h, sg_pair_forward<T>(fa, h->cls, h->mixed, st));
+    const FwdArgs<T> fa = fwd_args<T>(h, N, b->species);
+    CK(h, launch_forward<T>(h, fa, plan_for(h, N).pair_fwd, st));
     mark(h, EV_PS0, st);
     GapOperand op{};
     if constexpr (sizeof(T) == 4) {
@@ -1243,6 +1266,23 @@ extern "C" int soapgap_autotune(soapgap_handle* h, const soapgap_batch* batch, i
     CK(h, cudaEventCreate(&e0));
     CK(h, cudaEventCreate(&e1));
     float best_ms = -1.f;
+    // the forward pair kernel: FP32 FMA or tensor-core contraction; afterwards the variant
+    // of the evaluation above runs again, so that c matches the stages computed from it
+    {
+      const FwdArgs<float> fa = fwd_args<float>(h, N, batch->species);
+      const int used = plan_for(h, N).pair_fwd;
+      for (int v = 1; v <= 2; ++v) {
+        if (v == 2 && !sg_pair_forward_mma_supported(h->cls)) continue;
+        float ms = 0.f;
+        TL(time_launches(h, st, e0, e1, 2, [&] { return launch_forward<float>(h, fa, v, st); }, &ms));
+        if (ms >= 0.f && (best_ms < 0.f || ms < best_ms)) {
+          best.pair_fwd = v;
+          best_ms = ms;
+        }
+      }
+      CK(h, launch_forward<float>(h, fa, used, st));
+    }
+    best_ms = -1.f;
     for (int w = 2; w <= SG_ADJ_TCGEN05; ++w) {
       AdjArgs<float> aa = adj_args<float>(h, N, batch->species);
       if (w == SG_ADJ_TCGEN05 && !sg_pair_adjoint_tc_supported(aa, h->cls)) continue;
@@ -1304,6 +1344,7 @@ extern "C" int soapgap_autotune(soapgap_handle* h, const soapgap_batch* batch, i
     plan[1] = best.gap_fwd;
     plan[2] = best.gap_bwd;
     plan[3] = best.nbr_sweep;
+    plan[4] = best.pair_fwd;
   }
   h->msg.clear();
   return SOAPGAP_OK;
@@ -1330,6 +1371,7 @@ extern "C" int soapgap_get_plan(soapgap_handle* h, const soapgap_batch* batch, i
   plan[1] = p.gap_fwd;
   plan[2] = p.gap_bwd;
   plan[3] = p.nbr_sweep;
+  plan[4] = p.pair_fwd;
   h->msg.clear();
   return SOAPGAP_OK;
 }
@@ -1337,8 +1379,9 @@ extern "C" int soapgap_get_plan(soapgap_handle* h, const soapgap_batch* batch, i
 extern "C" int soapgap_set_plan(soapgap_handle* h, const soapgap_batch* batch, const int32_t* plan) {
   if (!h || !plan) return SOAPGAP_E_INVALID_ARG;
   if (!(plan[0] == 0 || (plan[0] >= 2 && plan[0] <= SG_ADJ_TCGEN05)) || plan[1] < 0 || plan[1] >= SG_GAP_FWD_CFGS ||
-      plan[2] < 0 || plan[2] >= SG_GAP_BWD_CFGS || plan[3] < 0 || plan[3] > 2)
-    return fail(h, SOAPGAP_E_INVALID_ARG, "set_plan: adjoint variant 0 or 2..5, GAP configurations and neighbour sweep in range");
+      plan[2] < 0 || plan[2] >= SG_GAP_BWD_CFGS || plan[3] < 0 || plan[3] > 2 || plan[4] < 0 || plan[4] > 2)
+    return fail(h, SOAPGAP_E_INVALID_ARG,
+                "set_plan: adjoint variant 0 or 2..5, GAP configurations, neighbour sweep and forward variant in range");
   long long key = 0;
   int rc = plan_batch_key(h, batch, &key);
   if (rc != SOAPGAP_OK) return rc;
@@ -1347,6 +1390,7 @@ extern "C" int soapgap_set_plan(soapgap_handle* h, const soapgap_batch* batch, c
   p.gap_fwd = plan[1];
   p.gap_bwd = plan[2];
   p.nbr_sweep = plan[3];
+  p.pair_fwd = plan[4];
   h->plans[key] = p;
   h->have_forward = false;  // a new forward pass must produce the layout of the new plan
   h->msg.clear();

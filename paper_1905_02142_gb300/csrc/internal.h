@@ -46,6 +46,9 @@ struct TableInfo {
 // 4 pi ilexp_l(z(r)) [x (2l+1) with eq08] (l <= lmax, padded to LC+1), and h * d/dr of each.
 cudaError_t sg_build_table(const DevParams& p, const BasisConst<double>& W, int cls,
                            const TableInfo& ti, float* table, cudaStream_t st);
+// FP16 operand scales of the tensor-core forward kernel (powers of two), from the table.
+cudaError_t sg_fwd_mma_scales(const float* table, const TableInfo& ti, int ncp, int nmax, int lmax, float* sa,
+                              float* sb);
 // Central-atom constants: cen_n (orthonormal basis, for the table path) and cen_alpha.
 cudaError_t sg_central_terms(const DevParams& p, const BasisConst<double>& W, double* out_n,
                              double* out_alpha, cudaStream_t st);
@@ -132,9 +135,14 @@ template <typename T> struct FwdArgs {
   BasisConst<T> bc;       // W (recursion path) and central terms (both)
   T* c;                   // [N][nsp*nmax][L]
   int* err;               // device error word (SG_ERR_TIMEOUT if a table copy never lands)
+  float mma_sa, mma_sb;   // tensor-core forward: powers of two scaling a_lm and b_n into FP16 range
 };
 template <typename T> cudaError_t sg_pair_forward(const FwdArgs<T>& a, int cls, bool table,
                                                   cudaStream_t st);
+// Mixed path: the same coefficients with the neighbour contraction on tensor cores
+// (pair_fwd_mma.cu); needs mma_sa, mma_sb (sg_fwd_mma_scales).
+bool sg_pair_forward_mma_supported(int cls);
+cudaError_t sg_pair_forward_mma(const FwdArgs<float>& a, int cls, cudaStream_t st);
 
 // ---------------------------------------------------------------- powspec.cu
 // The mixed path's GAP operand of each atom, written by the power-spectrum kernel when a16

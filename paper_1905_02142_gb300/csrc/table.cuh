@@ -25,9 +25,10 @@ __device__ __forceinline__ int table_locate(const TableInfo& ti, float r, float&
 }
 
 // Cubic-Hermite interpolation from the 4 FP floats of one interval (nodes k and k + 1),
-// in global memory (GLOBAL: read-only loads) or in a shared-memory copy:
+// in global memory (GLOBAL: read-only loads) or in a shared-memory copy (STREAM: four slots
+// at a time, fewer live registers; otherwise the whole interval is loaded first):
 // f[0..NC) = b_n(r), f[NC..NC+LC] = 4 pi ilexp_l(r); df = d/dr of the same (if DERIV).
-template <int NC, int LC, bool DERIV, bool GLOBAL = false>
+template <int NC, int LC, bool DERIV, bool GLOBAL = false, bool STREAM = false>
 __device__ __forceinline__ void table_interp_at(const float4* __restrict__ n0, float t, float invh, float* f,
                                                 float* df) {
   using TD = TableDims<NC, LC>;
@@ -36,34 +37,48 @@ __device__ __forceinline__ void table_interp_at(const float4* __restrict__ n0, f
   const float h00 = (2.f * t - 3.f) * t2 + 1.f, h10 = ((t - 2.f) * t + 1.f) * t;
   const float h01 = (3.f - 2.f * t) * t2, h11 = (t - 1.f) * t2;
   const float d00 = 6.f * t * (t - 1.f), d10 = (3.f * t - 4.f) * t + 1.f, d11 = (3.f * t - 2.f) * t;
-  float4 v0[Q], g0[Q], v1[Q], g1[Q];
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    if constexpr (GLOBAL) {
-      v0[q] = __ldg(n0 + q);
-      g0[q] = __ldg(n0 + Q + q);
-      v1[q] = __ldg(n0 + 2 * Q + q);
-      g1[q] = __ldg(n0 + 3 * Q + q);
-    } else {
-      v0[q] = n0[q];
-      g0[q] = n0[Q + q];
-      v1[q] = n0[2 * Q + q];
-      g1[q] = n0[3 * Q + q];
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < TD::FP; ++j) {
+  auto out = [&](int j, float a0, float b0, float a1, float b1) {
     int o;  // logical output index, or -1 for a padding slot
     if (j < TD::NCP) o = j < NC ? j : -1;
     else o = (j - TD::NCP) <= LC ? NC + (j - TD::NCP) : -1;
-    if (o < 0) continue;
-    const int q = j >> 2, c = j & 3;
-    const float a0 = c == 0 ? v0[q].x : c == 1 ? v0[q].y : c == 2 ? v0[q].z : v0[q].w;
-    const float b0 = c == 0 ? g0[q].x : c == 1 ? g0[q].y : c == 2 ? g0[q].z : g0[q].w;
-    const float a1 = c == 0 ? v1[q].x : c == 1 ? v1[q].y : c == 2 ? v1[q].z : v1[q].w;
-    const float b1 = c == 0 ? g1[q].x : c == 1 ? g1[q].y : c == 2 ? g1[q].z : g1[q].w;
+    if (o < 0) return;
     f[o] = h00 * a0 + h10 * b0 + h01 * a1 + h11 * b1;
     if (DERIV) df[o] = (d00 * (a0 - a1) + d10 * b0 + d11 * b1) * invh;
+  };
+  if constexpr (!STREAM) {
+    // the whole interval first (all loads in flight together)
+    float4 v0[Q], g0[Q], v1[Q], g1[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      if constexpr (GLOBAL) {  // read-only path
+        v0[q] = __ldg(n0 + q);
+        g0[q] = __ldg(n0 + Q + q);
+        v1[q] = __ldg(n0 + 2 * Q + q);
+        g1[q] = __ldg(n0 + 3 * Q + q);
+      } else {
+        v0[q] = n0[q];
+        g0[q] = n0[Q + q];
+        v1[q] = n0[2 * Q + q];
+        g1[q] = n0[3 * Q + q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      out(4 * q + 0, v0[q].x, g0[q].x, v1[q].x, g1[q].x);
+      out(4 * q + 1, v0[q].y, g0[q].y, v1[q].y, g1[q].y);
+      out(4 * q + 2, v0[q].z, g0[q].z, v1[q].z, g1[q].z);
+      out(4 * q + 3, v0[q].w, g0[q].w, v1[q].w, g1[q].w);
+    }
+  } else {
+    static_assert(!GLOBAL, "streamed interpolation reads shared memory");
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const float4 v0 = n0[q], g0 = n0[Q + q], v1 = n0[2 * Q + q], g1 = n0[3 * Q + q];
+      out(4 * q + 0, v0.x, g0.x, v1.x, g1.x);
+      out(4 * q + 1, v0.y, g0.y, v1.y, g1.y);
+      out(4 * q + 2, v0.z, g0.z, v1.z, g1.z);
+      out(4 * q + 3, v0.w, g0.w, v1.w, g1.w);
+    }
   }
 }
 

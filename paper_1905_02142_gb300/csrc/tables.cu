@@ -8,6 +8,10 @@
 // The FP32 pair kernels interpolate these nodes (cubic Hermite) instead of running the
 // recursion per pair: in FP32 the per-pair primitive-basis coefficients lose their
 // accuracy in W (cond(S) grows like a Hilbert matrix), which the FP64 nodes avoid.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "internal.h"
 #include "soapmath.cuh"
 #include "table.cuh"
@@ -75,4 +79,34 @@ cudaError_t sg_central_terms(const DevParams& p, const BasisConst<double>& W, do
   central_kernel<<<1, 1, 0, st>>>(p, W, out_n, out_alpha);
   ++sg_kernel_launches;
   return cudaGetLastError();
+}
+
+// Powers of two that bring the tensor-core forward's FP16 operands near 2^13 (FP16 holds up
+// to 65504 and is normal from 2^-14): sb for b_n, sa for a_lm = 4 pi ilexp_l Y_lm, from
+// the table's node values (Hermite overshoot between nodes stays well inside the margin)
+// and |Y_lm| <= sqrt((2l + 1) / 4 pi) for orthonormal real harmonics.  Reads the table
+// back to the host (set-up only).
+cudaError_t sg_fwd_mma_scales(const float* table, const TableInfo& ti, int ncp, int nmax, int lmax, float* sa,
+                              float* sb) {
+  std::vector<float> h((size_t)(ti.K + 1) * 2 * ti.fp);
+  cudaError_t e = cudaMemcpy(h.data(), table, sizeof(float) * h.size(), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return e;
+  double bmax = 0.0, amax = 0.0;
+  const double inv4pi = 1.0 / 12.566370614359172;
+  for (int k = 0; k <= ti.K; ++k) {
+    const float* v = h.data() + (size_t)k * 2 * ti.fp;  // values half-node
+    for (int n = 0; n < nmax; ++n) bmax = std::max(bmax, (double)std::fabs(v[n]));
+    for (int l = 0; l <= lmax; ++l)
+      amax = std::max(amax, std::fabs((double)v[ncp + l]) * std::sqrt((2.0 * l + 1.0) * inv4pi));
+  }
+  auto scale = [](double m) {
+    if (!(m > 0.0) || !std::isfinite(m)) return 1.f;
+    int ex = 0;
+    std::frexp(m, &ex);  // m < 2^ex
+    ex = std::max(-100, std::min(100, ex));
+    return std::ldexp(1.f, 13 - ex);
+  };
+  *sb = scale(bmax);
+  *sa = scale(amax);
+  return cudaSuccess;
 }

@@ -138,6 +138,7 @@ def test_autotune_keeps_results(batched):
     plan = model.autotune(s)
     assert plan["adjoint_warps"] in (2, 3, 4, 5)
     assert 0 <= plan["gap_forward"] < 3 and 0 <= plan["gap_backward"] < 4
+    assert plan["pair_forward"] in (1, 2)
     assert model.plan(s) == {k: plan[k] for k in model.PLAN_KEYS}
     after = model.compute(s, **OUT)
     # results depend on the plan only through the order of floating-point sums
@@ -146,8 +147,9 @@ def test_autotune_keeps_results(batched):
 
 
 def test_every_tile_plan_gives_the_same_results(batched):
-    """All GEMM tile configurations of the GAP products and all adjoint block shapes give
-    the same energies and forces, up to the order of sums."""
+    """All GEMM tile configurations of the GAP products, adjoint block shapes and neighbour
+    sweeps give the same energies and forces, up to the order of sums, for each forward
+    kernel; the two forward kernels agree to their precision."""
     import itertools
 
     from paper_1905_02142_gb300.api import SoapGapError, Structures
@@ -155,18 +157,31 @@ def test_every_tile_plan_gives_the_same_results(batched):
     w, batch = batched
     model = make_model(w.params(), w.n_sparse, w.zeta)
     s = Structures.from_batch(batch)
-    ref = {k: v.clone() for k, v in model.compute(s, **OUT).items()}
-    assert model.plan(s) == {"adjoint_warps": 0, "gap_forward": 0, "gap_backward": 0, "neighbour_sweep": 0}
+    model.compute(s, **OUT)
+    assert model.plan(s) == {"adjoint_warps": 0, "gap_forward": 0, "gap_backward": 0, "neighbour_sweep": 0,
+                             "pair_forward": 0}
+    base = {"adjoint_warps": 0, "gap_forward": 0, "gap_backward": 0, "neighbour_sweep": 0}
+    ref = {}
+    for pf in (1, 2):  # the two forward kernels differ in arithmetic, not only in the order of sums
+        model.set_plan(s, dict(base, pair_forward=pf))
+        ref[pf] = {k: v.clone() for k, v in model.compute(s, **OUT).items()}
+    for k, bar in (("forces", 1e-4), ("e_struct", 1e-5), ("e_atom", 1e-4)):
+        assert rel(ref[2][k], ref[1][k]) < bar, (k, rel(ref[2][k], ref[1][k]))
     for warps, fwd, bwd in itertools.product((2, 4, 5), range(3), range(4)):
+        pf = 1 + (fwd + 2 * bwd + warps) % 2
         model.set_plan(s, {"adjoint_warps": warps, "gap_forward": fwd, "gap_backward": bwd,
-                           "neighbour_sweep": (fwd + bwd) % 3})
+                           "neighbour_sweep": (fwd + bwd) % 3, "pair_forward": pf})
         out = model.compute(s, **OUT)
         # norm-wise: the local energies are sums of terms far larger than themselves, so
         # their last bits follow the partial-sum layout of the forward tile shape
         for k, bar in (("forces", 1e-5), ("e_struct", 1e-5), ("e_atom", 5e-5)):
-            assert rel(out[k], ref[k]) < bar, (k, warps, fwd, bwd, rel(out[k], ref[k]))
+            assert rel(out[k], ref[pf][k]) < bar, (k, warps, fwd, bwd, pf, rel(out[k], ref[pf][k]))
     with pytest.raises(SoapGapError) as err:
-        model.set_plan(s, {"adjoint_warps": 6, "gap_forward": 0, "gap_backward": 0, "neighbour_sweep": 0})
+        model.set_plan(s, {"adjoint_warps": 6, "gap_forward": 0, "gap_backward": 0, "neighbour_sweep": 0,
+                           "pair_forward": 0})
+    with pytest.raises(SoapGapError) as err:
+        model.set_plan(s, {"adjoint_warps": 0, "gap_forward": 0, "gap_backward": 0, "neighbour_sweep": 0,
+                           "pair_forward": 3})
     assert err.value.code == L.E_INVALID_ARG
 
 

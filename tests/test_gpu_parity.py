@@ -98,7 +98,8 @@ def test_pair_list_bit_exact(case, sweep):
     m = model_for(params_dict(P), "mixed")
     s = structures(batch)
     m.compute(s, desc=True)
-    m.set_plan(s, {"adjoint_warps": 0, "gap_forward": 0, "gap_backward": 0, "neighbour_sweep": sweep})
+    m.set_plan(s, {"adjoint_warps": 0, "gap_forward": 0, "gap_backward": 0, "neighbour_sweep": sweep,
+                   "pair_forward": 0})
     m.compute(s, desc=True)
     gi, gj, gs = m.pairs()
     oi, oj, os_ = oracle_pairs(batch, P.r_cut)
@@ -445,7 +446,8 @@ def test_pair_list_dense_corner_cluster(sweep):
     m = model_for(params_dict(P), "mixed")
     s = structures(batch)
     m.compute(s, desc=True)
-    m.set_plan(s, {"adjoint_warps": 0, "gap_forward": 0, "gap_backward": 0, "neighbour_sweep": sweep})
+    m.set_plan(s, {"adjoint_warps": 0, "gap_forward": 0, "gap_backward": 0, "neighbour_sweep": sweep,
+                   "pair_forward": 0})
     m.compute(s, desc=True)
     gi, gj, gs = m.pairs()
     oi, oj, os_ = oracle_pairs(batch, P.r_cut)
@@ -519,7 +521,7 @@ def test_adjoint_variants_against_oracle(name, m_sparse, sampled):
     forces = {}
     for variant in (5, 4, 2):
         model.set_plan(s, {"adjoint_warps": variant, "gap_forward": 0, "gap_backward": 0,
-                           "neighbour_sweep": 0})
+                           "neighbour_sweep": 0, "pair_forward": 0})
         f = model.compute(s, energy=True, forces=True)["forces"].cpu().numpy()
         forces[variant] = f
         err = rel_all(f[atoms], f_ref)
@@ -559,7 +561,7 @@ def test_adjoint_variants_on_dense_cluster_and_empty_structures():
         got = {}
         for variant, sweep in ((5, 1), (4, 2)):
             model.set_plan(s, {"adjoint_warps": variant, "gap_forward": 0, "gap_backward": 0,
-                               "neighbour_sweep": sweep})
+                               "neighbour_sweep": sweep, "pair_forward": sweep})
             out = model.compute(s, energy=True, forces=True)
             f = out["forces"].cpu().numpy()
             got[variant] = f
@@ -571,3 +573,61 @@ def test_adjoint_variants_on_dense_cluster_and_empty_structures():
                 assert np.allclose(e, e_ref, rtol=MIXED["e"], atol=1e-12)
                 assert e[0] == 0.0 and e[3] == 0.0 and np.all(f[0] == 0.0)
         assert rel_all(got[5], got[4]) < 1e-5
+
+
+# ------------------------------------------------------------------ forward kernel variants
+FORWARD_CASES = ["box64_n6l6", "box1000_n8l8", "twospecies4096_n8l8", "timing_n3l3", "timing_n12l12",
+                 "timing_n11l12", "timing_n12l3", "timing_n10l10", "hp0", "hp1", "hp2", "hp3", "hp4",
+                 "dense_cluster", "ragged"]
+
+
+def forward_case(case, golden):
+    """(params, batch, sampled centres or None for all atoms) of a forward-kernel case."""
+    g66 = Params(r_cut=5.0, r_soft=4.5, sigma_r0=0.5, sigma_p0=0.5, n_max=6, l_max=6)
+    if case.startswith("box") or case.startswith("twospecies"):
+        w = synth.get_workload(case)
+        b = w.structures()
+        return Params.from_dict(w.params()), b, np.arange(0, b.n_atoms, max(1, b.n_atoms // 40))
+    if case.startswith("timing"):
+        n, l = (int(x) for x in case[len("timing_n"):].split("l"))
+        P = Params(r_cut=5.0, r_soft=4.5, sigma_r0=0.5, sigma_p0=0.5, n_max=n, l_max=l)
+        return P, TIMING_BOX, np.random.default_rng(n * 100 + l).choice(TIMING_BOX.n_atoms, 8, replace=False)
+    if case.startswith("hp"):
+        k = int(case[2:])
+        return hp_variants(golden)[k], synth.concat([synth.random_box(40, side=7.5, dmin=1.0, seed=40 + k)]), None
+    if case == "dense_cluster":
+        dense = synth.concat([synth.random_box(300, density=0.15, dmin=1.2, seed=41)])
+        dense.pos[:] = dense.pos * 0.55
+        return g66, dense, np.array([0, 77, 150, 299])
+    lone = synth.Structure(pos=np.array([[5.0, 5.0, 5.0]]), cell=np.eye(3) * 20.0,
+                           species=np.zeros(1, np.int32))
+    empty = synth.Structure(pos=np.zeros((0, 3)), cell=np.eye(3) * 9.0, species=np.zeros(0, np.int32))
+    return g66, synth.concat([empty, lone, synth.random_box(16, side=5.0, dmin=1.2, seed=3), empty]), None
+
+
+@pytest.mark.parametrize("case", FORWARD_CASES)
+def test_forward_variants_against_oracle(case, golden):
+    """Both forward pair kernels, forced through the tile plan (1 = FP32 FMA contraction,
+    2 = tensor-core contraction with FP16 hi/lo operands), against the oracle's descriptors
+    (sampled centres on the larger boxes) and against each other: basis sizes 3..12, the
+    paper's hyperparameter sets, two species, a dense cluster (several 32-pair batches per
+    atom) and a batch with empty structures and an isolated atom."""
+    P, batch, centers = forward_case(case, golden)
+    m = model_for(params_dict(P), "mixed")
+    s = structures(batch)
+    m.compute(s, desc=True)
+    outs = {}
+    for v in (1, 2):
+        m.set_plan(s, {"adjoint_warps": 0, "gap_forward": 0, "gap_backward": 0, "neighbour_sweep": 0,
+                       "pair_forward": v})
+        out = m.compute(s, desc=True)
+        outs[v] = out["q"].double().cpu().numpy() * out["pnorm"].double().cpu().numpy()[:, None]
+        if centers is None:
+            ref = soap.descriptors(batch, P, W=oracle_W(P.n_max, P.r_cut, P.sigma_r0))
+            c = ref["centers"]
+            err = rel_rows(outs[v][c], (ref["q"] * ref["pnorm"][:, None]).numpy())
+        else:
+            err = sampled_p_error(batch, P, out, centers)
+        print(f"PARITY forward variant {v} {case}: p {err:.2e}")
+        assert err < MIXED["p"]
+    assert rel_rows(outs[2], outs[1]) < 1e-5
