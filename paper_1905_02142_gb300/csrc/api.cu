@@ -861,7 +861,7 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
         fused_operand = true;
       }
     }
-    CK(h, sg_power_spectrum<T>((const T*)h->c.p, N, nch, h->prm.l_max, (T*)h->q.p, (T*)h->pnorm.p, st, op));
+    CK(h, sg_power_spectrum<T>((const T*)h->c.p, N, nch, h->prm.l_max, h->LC, (T*)h->q.p, (T*)h->pnorm.p, st, op));
     if ((flags & SOAPGAP_DESC) && q_out)
       CK(h, cudaMemcpyAsync(q_out, h->q.p, es * (size_t)N * D, cudaMemcpyDeviceToDevice, st));
     if ((flags & SOAPGAP_DESC) && pnorm_out)

@@ -155,8 +155,8 @@ struct GapOperand {
   int dp, terms;
 };
 template <typename T>
-cudaError_t sg_power_spectrum(const T* c, int n_atoms, int nch, int lmax, T* q, T* pnorm,
-                              cudaStream_t st, const GapOperand& op = GapOperand{});
+cudaError_t sg_power_spectrum(const T* c, int n_atoms, int nch, int lmax, int lc, T* q, T* pnorm,
+                              cudaStream_t st, const GapOperand& op = GapOperand{});  // lc: class bound on l_max
 
 // ---------------------------------------------------------------- gap_simt.cu
 // eps_part[i][t] = sum over sparse tile t of alpha_s S_is^zeta,

@@ -36,7 +36,8 @@ __device__ __forceinline__ void gap_operand(const GapOperand& op, int atom, cons
   }
 }
 
-template <typename T>
+// LC: the basis class's bound on l_max (the (l, m) loops unrolled to it, l_max <= LC at run time)
+template <typename T, int LC>
 __global__ void powspec_kernel(const T* __restrict__ c, int n_atoms, int nch, int lmax,
                                int per_warp, T* q, T* pnorm, GapOperand op) {
   // one warp per atom: c staged in shared memory, each lane owns whole channel pairs
@@ -68,12 +69,20 @@ __global__ void powspec_kernel(const T* __restrict__ c, int n_atoms, int nch, in
       const T* b = cs + c2 * L;
       const T f = c1 != c2 ? SQRT2 : T(1);
       T* out = ps + pc * lp1;
-      for (int l = 0; l <= lmax; ++l) {
-        T v = 0;
-        for (int m = l * l; m < (l + 1) * (l + 1); ++m) v = fma(a[m], b[m], v);
-        v *= f;
-        out[l] = v;
-        ss += v * v;
+#pragma unroll
+      for (int l = 0; l <= LC; ++l) {
+        if (l <= lmax) {
+          // two partial sums: the m terms of one l are independent products
+          T v0 = 0, v1 = 0;
+#pragma unroll
+          for (int m = 0; m <= 2 * l; ++m) {
+            if (m & 1) v1 = fma(a[l * l + m], b[l * l + m], v1);
+            else v0 = fma(a[l * l + m], b[l * l + m], v0);
+          }
+          const T v = (v0 + v1) * f;
+          out[l] = v;
+          ss += v * v;
+        }
       }
     }
     ss = warp_sum(ss);
@@ -94,9 +103,9 @@ __global__ void powspec_kernel(const T* __restrict__ c, int n_atoms, int nch, in
   }
 }
 
-template <typename T>
-cudaError_t sg_power_spectrum(const T* c, int n_atoms, int nch, int lmax, T* q, T* pnorm,
-                              cudaStream_t st, const GapOperand& op) {
+template <typename T, int LC>
+static cudaError_t launch_powspec(const T* c, int n_atoms, int nch, int lmax, T* q, T* pnorm, cudaStream_t st,
+                                  const GapOperand& op) {
   if (n_atoms == 0) return cudaSuccess;
   const int L = (lmax + 1) * (lmax + 1);
   const int D = nch * (nch + 1) / 2 * (lmax + 1);
@@ -105,8 +114,8 @@ cudaError_t sg_power_spectrum(const T* c, int n_atoms, int nch, int lmax, T* q, 
   int wpb = (int)std::min<size_t>(4, (200 * 1024) / warp_bytes);
   if (wpb < 1) return cudaErrorInvalidConfiguration;
   const size_t smem = warp_bytes * wpb;
-  auto kern = powspec_kernel<T>;
-  cudaError_t e = sg_set_smem<powspec_kernel<T>>(smem);
+  auto kern = powspec_kernel<T, LC>;
+  cudaError_t e = sg_set_smem<powspec_kernel<T, LC>>(smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
@@ -121,7 +130,20 @@ cudaError_t sg_power_spectrum(const T* c, int n_atoms, int nch, int lmax, T* q, 
   return cudaGetLastError();
 }
 
-template cudaError_t sg_power_spectrum<float>(const float*, int, int, int, float*, float*, cudaStream_t,
+template <typename T>
+cudaError_t sg_power_spectrum(const T* c, int n_atoms, int nch, int lmax, int lc, T* q, T* pnorm, cudaStream_t st,
+                              const GapOperand& op) {
+  if (lmax > lc) return cudaErrorInvalidValue;
+  switch (lc) {
+    case 6: return launch_powspec<T, 6>(c, n_atoms, nch, lmax, q, pnorm, st, op);
+    case 8: return launch_powspec<T, 8>(c, n_atoms, nch, lmax, q, pnorm, st, op);
+    case 10: return launch_powspec<T, 10>(c, n_atoms, nch, lmax, q, pnorm, st, op);
+    case 12: return launch_powspec<T, 12>(c, n_atoms, nch, lmax, q, pnorm, st, op);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t sg_power_spectrum<float>(const float*, int, int, int, int, float*, float*, cudaStream_t,
                                               const GapOperand&);
-template cudaError_t sg_power_spectrum<double>(const double*, int, int, int, double*, double*, cudaStream_t,
+template cudaError_t sg_power_spectrum<double>(const double*, int, int, int, int, double*, double*, cudaStream_t,
                                                const GapOperand&);
