@@ -101,6 +101,7 @@ struct soapgap_handle {
   Buf geom, atom_offs, atom_struct, atom_bin, atom_bin4, atom_slot, bin_count, bin_start, bin_atoms, binpos,
       atom_hi, atom_lo;
   Buf seg_count, seg_offs, scan_tmp, key_tmp, key, pair_j, pair_r, rev, dedr, slot_count, max_count;
+  Buf adj_img, adj_exp;      // tcgen05 adjoint: per-atom G operand images and their exponents
   // Verlet skin: the list holds pairs within r_cut + skin and is reused while no atom has
   // moved by skin/2 since the positions pos_ref of its build
   double skin = 0.0;
@@ -591,6 +592,8 @@ static AdjArgs<T> adj_args(soapgap_handle* h, int N, const int* species) {
   aa.c = (const T*)h->c.p; aa.q = (const T*)h->q.p; aa.pnorm = (const T*)h->pnorm.p;
   aa.g = (const T*)h->g.p; aa.dedr = (Vec4<T>*)h->dedr.p; aa.vir_atom = (T*)h->vir_atom.p;
   aa.err = (int*)h->err.p;
+  aa.gimg = (unsigned char*)h->adj_img.p;
+  aa.gexp = (int*)h->adj_exp.p;
   return aa;
 }
 
@@ -884,6 +887,10 @@ static int run(soapgap_handle* h, const soapgap_batch* b, uint32_t flags, void* 
       ENS(h, h->g, es * N1 * D);
       ENS(h, h->vir_atom, es * N1 * 9);
       ENS(h, h->dedr, sizeof(Vec4<T>) * Pc);
+      if (h->mixed) {
+        ENS(h, h->adj_img, sg_adj_tc_image_bytes(h->cls, nsp) * N1);
+        ENS(h, h->adj_exp, sizeof(int) * N1);
+      }
       ENS(h, h->struct_w, sizeof(double) * (size_t)S);
     }
     mark(h, EV_GF0, st);
@@ -1147,7 +1154,7 @@ extern "C" void soapgap_destroy(soapgap_handle* h) {
                  &h->r_part, &h->kp16, &h->table, &h->table_adj, &h->qs, &h->alpha, &h->geom, &h->atom_offs, &h->atom_struct,
                  &h->atom_bin, &h->atom_bin4, &h->atom_slot, &h->bin_count, &h->bin_start, &h->bin_atoms,
                  &h->binpos, &h->atom_hi, &h->atom_lo, &h->seg_count, &h->seg_offs, &h->scan_tmp, &h->key_tmp,
-                 &h->key, &h->pair_j, &h->pair_r, &h->rev, &h->dedr, &h->c, &h->q, &h->pnorm,
+                 &h->key, &h->pair_j, &h->pair_r, &h->rev, &h->dedr, &h->adj_img, &h->adj_exp, &h->c, &h->q, &h->pnorm,
                  &h->e_atom, &h->eps_part, &h->kp, &h->g, &h->vir_atom, &h->struct_w, &h->err,
                  &h->finish_part, &h->slot_count, &h->max_count, &h->pos_ref, &h->skin_flag, &h->live_count, &h->live_offs, &h->live_idx, &h->pos_w, &h->img,
                  &h->cen_tmp, &h->host_in_pos, &h->host_in_species, &h->host_q, &h->host_pnorm,

@@ -231,6 +231,8 @@ template <typename T> struct AdjArgs {
   Vec4<T>* dedr;            // [P] dE/dr_ij
   T* vir_atom;              // [N][9]
   int* err;                 // device error word (SG_ERR_*)
+  unsigned char* gimg;      // tcgen05 variant: per atom, the FP16 operand image of dE/dc
+  int* gexp;                //   (sg_adj_tc_image_bytes bytes) and its power-of-two exponent
 };
 template <typename T> cudaError_t sg_pair_adjoint(const AdjArgs<T>& a, int cls, bool table,
                                                   cudaStream_t st);
@@ -241,6 +243,8 @@ cudaError_t sg_pair_adjoint_mma(const AdjArgs<float>& a, int cls, cudaStream_t s
 #define SG_ADJ_TCGEN05 5
 bool sg_pair_adjoint_tc_supported(const AdjArgs<float>& a, int cls);
 cudaError_t sg_pair_adjoint_tc(const AdjArgs<float>& a, int cls, cudaStream_t st);
+// bytes of one atom's operand image of the tcgen05 variant (a.gimg holds n_atoms of them)
+size_t sg_adj_tc_image_bytes(int cls, int nsp);
 // 32-pair batches of a typical atom (sum over its neighbour-species segments)
 int sg_adj_batches_per_atom(long long n_pairs, int n_atoms, int nsp);
 

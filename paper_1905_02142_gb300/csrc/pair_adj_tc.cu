@@ -4,9 +4,13 @@
 // recomputing the pair's radial terms (Eq. 04 through the radial table) and its real
 // harmonics (Sec. III.C) instead of storing dc/dr.
 //
-//   one block of 4 warps per atom (persistent over atoms)
-//     prologue: h = dE/dp, G_l = M_l c_l, stored as FP16 split rows G16[tau] (B operand,
-//     K-major, 128-byte swizzled rows; tau = harmonic index in the recursion's visit order)
+//   the G-operand kernel (adj_gop_kernel), one block per atom: h = dE/dp, G_l = M_l c_l,
+//     stored as FP16 split rows G16[tau] (B operand, K-major, 128-byte swizzled rows; tau =
+//     harmonic index in the recursion's visit order) in a per-atom image in global memory:
+//     rows tau and tau + 64 of each 128 share one 128-byte row (the first and the second 64
+//     bytes), as the A tile packs b and b'; with the image, the power of two scaling G
+//   the adjoint kernel, one block of 4 warps per atom (persistent over atoms): the atom's
+//     image is bulk-copied into shared memory while the block works on the previous atom
 //   one thread per pair, 128 pairs of one (atom, neighbour species) segment per tile:
 //     b_n(r) and b_n'(r) from the radial table, as FP16 split rows of the A operand
 //     u[pair][tau] = sum_n b_n G[tau][n] and u'[pair][tau] = sum_n b_n' G[tau][n]:
@@ -49,14 +53,33 @@ template <int NC, int LC> struct TcDims {
   static constexpr int T16 = (TN + 15) & ~15;         // harmonic rows (B operand rows)
   static constexpr int NPH = (T16 + TC_PHASE - 1) / TC_PHASE;
   static constexpr int A_BYTES = PACKED ? 128 * 128 : 2 * 128 * 128;
+  // image of one species: with split rows of at most 64 bytes (PACKED), phase ph (harmonic rows
+  // 64 ph + [0, 64)) in image rows (ph / 2) 64 + [0, 64), bytes (ph % 2) 64 + [0, 64); else
+  // one harmonic row per image row
+  static constexpr int ROWS = PACKED ? 64 * ((NPH + 1) / 2) : T16;
+  static constexpr int IMG = ROWS * 128;
+  __device__ __forceinline__ static int img_row(int tau) { return PACKED ? ((tau >> 6) >> 1) * 64 + (tau & 63) : tau; }
+  __device__ __forceinline__ static int img_chunk(int tau) { return PACKED ? ((tau >> 6) & 1) * 4 : 0; }
+  // byte offset of phase ph's first row in the image
+  __device__ __forceinline__ static uint32_t img_phase(int ph) {
+    return PACKED ? (uint32_t)((ph >> 1) * 64 * 128 + (ph & 1) * 64) : (uint32_t)(ph * 64 * 128);
+  }
 };
 
 struct TcLayout {
-  int off_g16;    // [nsp][T16] rows of 128 B
-  int off_union;  // prologue scratch, or the A tile(s) then the per-warp ild arrays
-  int off_ild;    // from the smem base
+  int off_g16;    // two buffers of the atom's image ([nsp][ROWS] rows of 128 B each)
+  int off_union;  // the A tile(s)
+  int off_ild;    // the per-warp ild arrays
   int off_red;
   int total;      // bytes to request (includes 1024 for the base alignment)
+};
+
+struct GopLayout {
+  int off_stage;  // the atom's image, staged for the bulk store
+  int off_pc;     // packed channel-pair decode
+  int off_scr;    // scratch: dE/dp, q, dE/dq, c, M, G (FP32)
+  int off_red;
+  int total;
 };
 
 template <int NC, int LC>
@@ -67,21 +90,31 @@ int tc_prologue_floats(int nsp, int dim) {
 }
 
 template <int NC, int LC>
-TcLayout make_tc_layout(int nsp, int dim) {
+TcLayout make_tc_layout(int nsp) {
   using Dm = TcDims<NC, LC>;
   TcLayout m{};
-  const int nch = nsp * NC;
-  const int pcdec = 4 * (nch * (nch + 1) / 2);
-  m.off_g16 = (pcdec + 1023) / 1024 * 1024;
-  m.off_union = (m.off_g16 + nsp * Dm::T16 * 128 + 1023) / 1024 * 1024;
+  m.off_g16 = 0;
+  m.off_union = (2 * nsp * Dm::IMG + 1023) / 1024 * 1024;
   const int ild = 4 * 2 * Dm::LP * 32 * 4;  // four warps
-  const int uni = std::max(4 * tc_prologue_floats<NC, LC>(nsp, dim), Dm::A_BYTES + ild);
   m.off_ild = m.off_union + Dm::A_BYTES;
-  m.off_red = (m.off_union + uni + 15) / 16 * 16;
-  m.total = m.off_red + (4 * 11) * 4 + 1024;
+  m.off_red = (m.off_ild + ild + 15) / 16 * 16;
+  m.total = m.off_red + (4 * 9) * 4 + 1024;
   // at most 4 blocks per SM (228 KB of shared memory, 1 KB reserved per block), so that the
   // blocks' tensor-memory allocations (4 x 128 columns) never exceed the SM's 512
   m.total = std::max(m.total, 47 * 1024);
+  return m;
+}
+
+template <int NC, int LC>
+GopLayout make_gop_layout(int nsp, int dim) {
+  using Dm = TcDims<NC, LC>;
+  GopLayout m{};
+  const int nch = nsp * NC;
+  m.off_stage = 0;
+  m.off_pc = nsp * Dm::IMG;
+  m.off_scr = (m.off_pc + 4 * (nch * (nch + 1) / 2) + 15) / 16 * 16;
+  m.off_red = m.off_scr + 4 * tc_prologue_floats<NC, LC>(nsp, dim);
+  m.total = m.off_red + 4 * 8 + 1024;
   return m;
 }
 
@@ -197,41 +230,34 @@ __device__ __forceinline__ void tc_sweep(const YlmCoef<float>& yc, float ux, flo
   }
 }
 
+// The per-atom G operand of the adjoint (one block per atom, persistent): h = dE/dp, the
+// packed-pair derivative matrices M, G = M c in FP32, scaled by 2^(14 - e) with 2^e > max |G|
+// and split into FP16 rows, stored as the atom's image (bulk store from shared memory) and e.
 template <int NC, int LC>
-__global__ void __launch_bounds__(TC_THREADS, 4) pair_adj_tc_kernel(const AdjArgs<float> a, const TcLayout lay) {
+__global__ void __launch_bounds__(TC_THREADS) adj_gop_kernel(const AdjArgs<float> a, const GopLayout lay) {
   using Dm = TcDims<NC, LC>;
-  constexpr int KP = Dm::KP, KS = Dm::KS, NP = Dm::NP, LP = Dm::LP, T16 = Dm::T16, NPH = Dm::NPH;
+  constexpr int KP = Dm::KP, NP = Dm::NP, LP = Dm::LP, T16 = Dm::T16;
   constexpr int TE = Dm::TE, TN = Dm::TN;
   constexpr int W = 4, NT = TC_THREADS;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t mma_bar;
-  __shared__ uint32_t tmem_slot;
-  __shared__ volatile int abort_flag;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x;
   constexpr int lmax = LC, nmax = NC;
   constexpr int L = LP * LP, lp1 = LP;
   const int nch = a.nsp * nmax;
   const int D = a.dim;
   const int npair = nch * (nch + 1) / 2;
-
-  int* pcdec = reinterpret_cast<int*>(smem);
-  unsigned char* g16 = smem + lay.off_g16;
-  unsigned char* uni = smem + lay.off_union;
-  float* red = reinterpret_cast<float*>(smem + lay.off_red);  // [W][9] virial | [2 W] reductions
-  float* red2 = red + W * 9;
-  // prologue scratch (aliases the A tiles and the ild arrays)
-  float* hs = reinterpret_cast<float*>(uni);     // [D] dE/dp
-  float* qs = hs + align4(D);                    // [D]
-  float* gs = qs + align4(D);                    // [D]
-  float* cs = gs + align4(D);                    // [nch][L]
-  float* ms = cs + align4(nch * L);              // [nsp][lp1][nch][NP]
-  float* g32 = ms + a.nsp * lp1 * nch * NP;      // [nsp][T16][NP]
-  unsigned char* atile = uni;                    // A: b rows (and b' rows when packed)
-  unsigned char* atile_p = Dm::PACKED ? uni : uni + 128 * 128;
-  constexpr int chunk_p = Dm::PACKED ? 4 : 0;    // first 16-byte chunk of the b' rows
-  float* ild = reinterpret_cast<float*>(smem + lay.off_ild) + warp * 2 * LP * 32;  // [2][LP][32]
+  unsigned char* stage = smem + lay.off_stage;
+  int* pcdec = reinterpret_cast<int*>(smem + lay.off_pc);
+  float* hs = reinterpret_cast<float*>(smem + lay.off_scr);  // [D] dE/dp
+  float* qs = hs + align4(D);                                 // [D]
+  float* gs = qs + align4(D);                                 // [D]
+  float* cs = gs + align4(D);                                 // [nch][L]
+  float* ms = cs + align4(nch * L);                           // [nsp][lp1][nch][NP]
+  float* g32 = ms + a.nsp * lp1 * nch * NP;                   // [nsp][T16][NP]
+  float* red2 = reinterpret_cast<float*>(smem + lay.off_red);
+  const uint32_t img_bytes = (uint32_t)(a.nsp * Dm::IMG);
 
   for (int pc = tid; pc < npair; pc += NT) {
     int c1 = 0, rem = pc;
@@ -241,20 +267,9 @@ __global__ void __launch_bounds__(TC_THREADS, 4) pair_adj_tc_kernel(const AdjArg
     }
     pcdec[pc] = c1 | ((c1 + rem) << 16);
   }
-  if (tid == 0) {
-    tc5::mbar_init(&mma_bar, 1);
-    abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) tc5::tmem_alloc(&tmem_slot, TC_TMEM_COLS);
-  tc5::fence_before();
   __syncthreads();
-  tc5::fence_after();
-  const uint32_t tmem = tmem_slot;
-  uint32_t mma_done = 0;  // MMA phases committed so far (the same count in every thread)
-
   for (int atom = blockIdx.x; atom < a.n_atoms; atom += gridDim.x) {
-    __syncthreads();  // previous atom done with G16, the A tiles and the scratch
+    __syncthreads();  // the previous atom done with the scratch
     // ---- c, q, g -> shared memory: asynchronous copies, all in flight together
     {
       const float* qi = a.q + (size_t)atom * D;
@@ -337,6 +352,8 @@ __global__ void __launch_bounds__(TC_THREADS, 4) pair_adj_tc_kernel(const AdjArg
     frexpf(gmax, &eg);
     eg = max(-100, min(eg, 100));
     const float sg = ldexpf(1.f, 14 - eg);
+    if (tid == 0) tc5::bulk_wait_read0();  // the previous atom's image has left the stage
+    __syncthreads();
     for (int row = tid; row < a.nsp * T16; row += NT) {
       const int s = row / T16, tau = row - s * T16;
       const bool real = tau < TE ? tau <= lmax : tau < TN;
@@ -350,27 +367,93 @@ __global__ void __launch_bounds__(TC_THREADS, 4) pair_adj_tc_kernel(const AdjArg
         if (4 * q4 + 2 < NC) v[4 * q4 + 2] = x.z * sg;
         if (4 * q4 + 3 < NC) v[4 * q4 + 3] = x.w * sg;
       }
-      write_split_row_sw<NC, KP, false>(g16 + (size_t)s * T16 * 128, tau, 0, v);
+      write_split_row_sw<NC, KP, false>(stage + (size_t)s * Dm::IMG, Dm::img_row(tau), Dm::img_chunk(tau), v);
     }
-    __syncthreads();  // G16 complete; the prologue scratch may now become the A tiles
+    tc5::fence_proxy_async();  // the rows, written by threads, reach the bulk copy
+    __syncthreads();
+    if (tid == 0) {
+      tc5::bulk_store(a.gimg + (size_t)atom * img_bytes, stage, img_bytes);
+      tc5::bulk_commit();
+      a.gexp[atom] = eg;
+    }
+  }
+  if (tid == 0) tc5::bulk_wait_all();
+}
 
-    // next atom's inputs towards L2 while this one's pairs run
-    {
-      const int nxt = atom + gridDim.x;
-      if (nxt < a.n_atoms) {
-        const int lc = (nch * L * 4 + 127) >> 7, lq = (D * 4 + 127) >> 7;
-        const int pb = a.list_offs[nxt * a.nsp], pe = a.list_offs[(nxt + 1) * a.nsp];
-        const char* pr = reinterpret_cast<const char*>(a.pair_r + pb);
-        const int lp = pe > pb ? (int)(((pe - pb) * sizeof(Vec4<float>) + 127) >> 7) : 0;
-        for (int k = tid; k < lc + 2 * lq + lp; k += NT) {
-          const char* p;
-          if (k < lc) p = reinterpret_cast<const char*>(a.c + (size_t)nxt * nch * L) + ((size_t)k << 7);
-          else if (k < lc + lq) p = reinterpret_cast<const char*>(a.q + (size_t)nxt * D) + ((size_t)(k - lc) << 7);
-          else if (k < lc + 2 * lq) p = reinterpret_cast<const char*>(a.g + (size_t)nxt * D) + ((size_t)(k - lc - lq) << 7);
-          else p = pr + ((size_t)(k - lc - 2 * lq) << 7);
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-        }
+template <int NC, int LC>
+__global__ void __launch_bounds__(TC_THREADS, 4) pair_adj_tc_kernel(const AdjArgs<float> a, const TcLayout lay) {
+  using Dm = TcDims<NC, LC>;
+  constexpr int KP = Dm::KP, KS = Dm::KS, LP = Dm::LP, T16 = Dm::T16, NPH = Dm::NPH;
+  constexpr int W = 4, NT = TC_THREADS;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ __align__(8) uint64_t gbar[2];  // per image buffer: its bulk copy has landed
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  unsigned char* gimg = smem + lay.off_g16;  // [2][nsp][ROWS][128 B]
+  unsigned char* uni = smem + lay.off_union;
+  float* red = reinterpret_cast<float*>(smem + lay.off_red);  // [W][9] virial
+  unsigned char* atile = uni;                    // A: b rows (and b' rows when packed)
+  unsigned char* atile_p = Dm::PACKED ? uni : uni + 128 * 128;
+  constexpr int chunk_p = Dm::PACKED ? 4 : 0;    // first 16-byte chunk of the b' rows
+  float* ild = reinterpret_cast<float*>(smem + lay.off_ild) + warp * 2 * LP * 32;  // [2][LP][32]
+
+  const uint32_t img_bytes = (uint32_t)(a.nsp * Dm::IMG);
+  if (tid == 0) {
+    tc5::mbar_init(&mma_bar, 1);
+    tc5::mbar_init(&gbar[0], 1);
+    tc5::mbar_init(&gbar[1], 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tc5::tmem_alloc(&tmem_slot, TC_TMEM_COLS);
+  tc5::fence_before();
+  __syncthreads();
+  tc5::fence_after();
+  const uint32_t tmem = tmem_slot;
+  uint32_t mma_done = 0;  // MMA phases committed so far (the same count in every thread)
+  int buf = 0;            // image buffer of the current atom
+  uint32_t gpar = 0;      // bit b: parity of the next completion of gbar[b]
+  uint32_t pend = 0;      // (thread 0) bit b: a copy into buffer b not yet waited for
+  if (tid == 0 && (int)blockIdx.x < a.n_atoms) {
+    tc5::mbar_expect_tx(&gbar[0], img_bytes);
+    tc5::bulk_load(gimg, a.gimg + (size_t)blockIdx.x * img_bytes, img_bytes, &gbar[0]);
+    pend = 1u;
+  }
+
+  for (int atom = blockIdx.x; atom < a.n_atoms; atom += gridDim.x) {
+    __syncthreads();  // previous atom done with its image buffer and the A tiles
+    // ---- the next atom's image into the other buffer (the previous atom, which used it,
+    //      has awaited all its MMAs); then this atom's, copied during the previous atom
+    const int nxt = atom + gridDim.x;
+    if (tid == 0 && nxt < a.n_atoms && !abort_flag) {
+      const int nb = buf ^ 1;
+      tc5::mbar_expect_tx(&gbar[nb], img_bytes);
+      tc5::bulk_load(gimg + (size_t)nb * img_bytes, a.gimg + (size_t)nxt * img_bytes, img_bytes, &gbar[nb]);
+      pend |= 1u << nb;
+    }
+    if (!abort_flag) {
+      if (!tc5::mbar_wait(&gbar[buf], (gpar >> buf) & 1u)) {
+        abort_flag = 1;
+        if (a.err) atomicOr(a.err, SG_ERR_TIMEOUT);
+      } else {
+        gpar ^= 1u << buf;
+        pend &= ~(1u << buf);
       }
+    }
+    const int eg = a.gexp[atom];
+    __syncthreads();  // every thread past the wait: the image is in shared memory
+
+    // next atom's pair vectors towards L2 while this one's pairs run
+    if (nxt < a.n_atoms) {
+      const int pb = a.list_offs[nxt * a.nsp], pe = a.list_offs[(nxt + 1) * a.nsp];
+      const char* pr = reinterpret_cast<const char*>(a.pair_r + pb);
+      const int lp = pe > pb ? (int)(((pe - pb) * sizeof(Vec4<float>) + 127) >> 7) : 0;
+      for (int k = tid; k < lp; k += NT) asm volatile("prefetch.global.L2 [%0];" ::"l"(pr + ((size_t)k << 7)));
     }
 
     float vir[9];
@@ -379,7 +462,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) pair_adj_tc_kernel(const AdjArg
     for (int s = 0; s < a.nsp; ++s) {
       const int beg = a.seg_offs[atom * a.nsp + s];
       const int end = a.seg_offs[atom * a.nsp + s + 1];
-      const uint32_t gsp = tc5::smem_u32(g16 + (size_t)s * T16 * 128);
+      const uint32_t gsp = tc5::smem_u32(gimg + (size_t)buf * img_bytes + (size_t)s * Dm::IMG);
       for (int tbase = beg; tbase < end; tbase += NT) {
         // ---- radial terms of this thread's pair -> A rows (b, b') and ild
         const int pidx = tbase + tid;
@@ -433,7 +516,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) pair_adj_tc_kernel(const AdjArg
           const int n = min(TC_PHASE, T16 - ph * TC_PHASE);
           const uint32_t idesc = tc5::idesc_f16(128, n);
           const uint32_t a0 = tc5::smem_u32(atile), ap = tc5::smem_u32(atile_p) + chunk_p * 16;
-          const uint32_t b0 = gsp + (uint32_t)(ph * TC_PHASE * 128);
+          const uint32_t b0 = gsp + Dm::img_phase(ph);
 #pragma unroll
           for (int ks = 0; ks < KS; ++ks) {
             tc5::mma_f16(tmem, tc5::sw128_desc(a0 + ks * 32), tc5::sw128_desc(b0 + ks * 32), idesc, ks > 0);
@@ -517,7 +600,13 @@ __global__ void __launch_bounds__(TC_THREADS, 4) pair_adj_tc_kernel(const AdjArg
       for (int w2 = 0; w2 < W; ++w2) vt += red[w2 * 9 + tid];
       a.vir_atom[(size_t)atom * 9 + tid] = vt;
     }
+    buf ^= 1;
   }
+  // after a timeout the block stopped waiting: give a copy still in flight one more bounded
+  // wait before the shared memory is released
+  if (tid == 0 && abort_flag)
+    for (int b = 0; b < 2; ++b)
+      if (pend & (1u << b)) tc5::mbar_wait(&gbar[b], (gpar >> b) & 1u);
   tc5::fence_before();
   __syncthreads();
   if (warp == 0) tc5::tmem_dealloc(tmem, TC_TMEM_COLS);
@@ -525,25 +614,42 @@ __global__ void __launch_bounds__(TC_THREADS, 4) pair_adj_tc_kernel(const AdjArg
 
 template <int NC, int LC>
 cudaError_t launch_tc(const AdjArgs<float>& a, cudaStream_t st) {
-  const TcLayout lay = make_tc_layout<NC, LC>(a.nsp, a.dim);
+  if (!a.gimg || !a.gexp) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0, smem_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
+    return cudaGetLastError();
+  // ---- the per-atom G operand images
+  const GopLayout gl = make_gop_layout<NC, LC>(a.nsp, a.dim);
+  if (gl.total > 220 * 1024) return cudaErrorInvalidConfiguration;
+  {
+    auto kern = adj_gop_kernel<NC, LC>;
+    cudaError_t e = sg_set_smem<adj_gop_kernel<NC, LC>>(gl.total);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TC_THREADS, gl.total);
+    long long grid = (long long)sms * std::max(1, per_sm);
+    if (grid > a.n_atoms) grid = a.n_atoms;
+    kern<<<(unsigned)grid, TC_THREADS, gl.total, st>>>(a, gl);
+    ++sg_kernel_launches;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  // ---- the adjoint
+  const TcLayout lay = make_tc_layout<NC, LC>(a.nsp);
   if (lay.total > 220 * 1024) return cudaErrorInvalidConfiguration;
   auto kern = pair_adj_tc_kernel<NC, LC>;
   cudaError_t e = sg_set_smem<pair_adj_tc_kernel<NC, LC>>(lay.total);
   if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   // resident blocks per SM from the kernel's shared memory and registers (the occupancy
   // query reports one block per SM for kernels that allocate tensor memory), and at most
   // 512 / 128 by the tensor memory
   cudaFuncAttributes fa{};
-  int smem_sm = 0;
-  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess ||
-      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
-    return cudaGetLastError();
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return cudaGetLastError();
   const int by_smem = smem_sm / (lay.total + (int)fa.sharedSizeBytes + 1024);
   const int by_regs = fa.numRegs > 0 ? 65536 / (((fa.numRegs + 7) & ~7) * TC_THREADS) : 1;
-  per_sm = std::max(1, std::min(std::min(by_smem, by_regs), (int)(512 / TC_TMEM_COLS)));
+  const int per_sm = std::max(1, std::min(std::min(by_smem, by_regs), (int)(512 / TC_TMEM_COLS)));
   long long grid = (long long)sms * per_sm;
   if (grid > a.n_atoms) grid = a.n_atoms;
   kern<<<(unsigned)grid, TC_THREADS, lay.total, st>>>(a, lay);
@@ -566,5 +672,14 @@ cudaError_t sg_pair_adjoint_tc(const AdjArgs<float>& a, int cls, cudaStream_t st
     case 1: return launch_tc<8, 8>(a, st);
     case 2: return launch_tc<10, 10>(a, st);
     default: return launch_tc<12, 12>(a, st);
+  }
+}
+
+size_t sg_adj_tc_image_bytes(int cls, int nsp) {
+  switch (cls) {
+    case 0: return (size_t)nsp * TcDims<6, 6>::IMG;
+    case 1: return (size_t)nsp * TcDims<8, 8>::IMG;
+    case 2: return (size_t)nsp * TcDims<10, 10>::IMG;
+    default: return (size_t)nsp * TcDims<12, 12>::IMG;
   }
 }
