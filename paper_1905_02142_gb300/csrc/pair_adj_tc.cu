@@ -75,18 +75,18 @@ struct TcLayout {
 };
 
 struct GopLayout {
-  int off_stage;  // the atom's image, staged for the bulk store
   int off_pc;     // packed channel-pair decode
   int off_scr;    // scratch: dE/dp, q, dE/dq, c, M, G (FP32)
   int off_red;
   int total;
 };
 
+// scratch of the G-operand kernel, in floats: [q | dE/dq], later reused for G; c; M
 template <int NC, int LC>
 int tc_prologue_floats(int nsp, int dim) {
   using Dm = TcDims<NC, LC>;
   const int nch = nsp * NC, L = Dm::LP * Dm::LP;
-  return 3 * align4(dim) + align4(nch * L) + nsp * Dm::LP * nch * Dm::NP + nsp * Dm::T16 * Dm::NP;
+  return std::max(2 * align4(dim), nsp * Dm::T16 * Dm::NP) + align4(nch * L) + nsp * Dm::LP * nch * Dm::NP;
 }
 
 template <int NC, int LC>
@@ -110,11 +110,10 @@ GopLayout make_gop_layout(int nsp, int dim) {
   using Dm = TcDims<NC, LC>;
   GopLayout m{};
   const int nch = nsp * NC;
-  m.off_stage = 0;
-  m.off_pc = nsp * Dm::IMG;
+  m.off_pc = 0;
   m.off_scr = (m.off_pc + 4 * (nch * (nch + 1) / 2) + 15) / 16 * 16;
   m.off_red = m.off_scr + 4 * tc_prologue_floats<NC, LC>(nsp, dim);
-  m.total = m.off_red + 4 * 8 + 1024;
+  m.total = m.off_red + 4 * 8;
   return m;
 }
 
@@ -232,30 +231,27 @@ __device__ __forceinline__ void tc_sweep(const YlmCoef<float>& yc, float ux, flo
 
 // The per-atom G operand of the adjoint (one block per atom, persistent): h = dE/dp, the
 // packed-pair derivative matrices M, G = M c in FP32, scaled by 2^(14 - e) with 2^e > max |G|
-// and split into FP16 rows, stored as the atom's image (bulk store from shared memory) and e.
+// and split into FP16 rows, written to the atom's image (each thread 64 bytes of a row: two
+// whole 32-byte sectors), and e.
 template <int NC, int LC>
 __global__ void __launch_bounds__(TC_THREADS) adj_gop_kernel(const AdjArgs<float> a, const GopLayout lay) {
   using Dm = TcDims<NC, LC>;
   constexpr int KP = Dm::KP, NP = Dm::NP, LP = Dm::LP, T16 = Dm::T16;
   constexpr int TE = Dm::TE, TN = Dm::TN;
   constexpr int W = 4, NT = TC_THREADS;
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x;
   constexpr int lmax = LC, nmax = NC;
   constexpr int L = LP * LP, lp1 = LP;
   const int nch = a.nsp * nmax;
   const int D = a.dim;
   const int npair = nch * (nch + 1) / 2;
-  unsigned char* stage = smem + lay.off_stage;
   int* pcdec = reinterpret_cast<int*>(smem + lay.off_pc);
-  float* hs = reinterpret_cast<float*>(smem + lay.off_scr);  // [D] dE/dp
-  float* qs = hs + align4(D);                                 // [D]
-  float* gs = qs + align4(D);                                 // [D]
-  float* cs = gs + align4(D);                                 // [nch][L]
+  float* qs = reinterpret_cast<float*>(smem + lay.off_scr);  // [D]
+  float* gs = qs + align4(D);                                 // [D] dE/dq
+  float* g32 = qs;  // [nsp][T16][NP] G (several species), written once q and dE/dq are used up
+  float* cs = qs + max(2 * align4(D), a.nsp * T16 * NP);      // [nch][L]
   float* ms = cs + align4(nch * L);                           // [nsp][lp1][nch][NP]
-  float* g32 = ms + a.nsp * lp1 * nch * NP;                   // [nsp][T16][NP]
   float* red2 = reinterpret_cast<float*>(smem + lay.off_red);
   const uint32_t img_bytes = (uint32_t)(a.nsp * Dm::IMG);
 
@@ -286,13 +282,11 @@ __global__ void __launch_bounds__(TC_THREADS) adj_gop_kernel(const AdjArgs<float
     const float pn = a.pnorm[atom];
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    // ---- h = dE/dp = w (g - q (q.g)) / |p|
+    // ---- h = dE/dp = w (g - q (q.g)) / |p|, formed where M needs it
     float dot = 0.f;
     for (int k = tid; k < D; k += NT) dot += qs[k] * gs[k];
     dot = block_sum<W>(dot, red2);
     const float sc = w / pn;
-    for (int k = tid; k < D; k += NT) hs[k] = sc * (gs[k] - qs[k] * dot);
-    __syncthreads();
 
     // ---- M[s][l][c2][n] = d p_(c1 c2 l) / d(c1, c2 product) with c1 = (s, n): 2 h on the
     //      diagonal, sqrt(2) h off it; one thread per packed channel pair writes both halves
@@ -302,82 +296,110 @@ __global__ void __launch_bounds__(TC_THREADS) adj_gop_kernel(const AdjArgs<float
       const int s1 = c1 / nmax, n1 = c1 - s1 * nmax;
       const int s2 = c2 / nmax, n2 = c2 - s2 * nmax;
       const float f = c1 == c2 ? 2.f : 1.41421356237f;
-      const float* hrow = hs + pc * lp1;
+      const float* qrow = qs + pc * lp1;
+      const float* grow = gs + pc * lp1;
       float* m1 = ms + ((size_t)s1 * lp1 * nch + c2) * NP + n1;  // + l nch NP
       float* m2 = ms + ((size_t)s2 * lp1 * nch + c1) * NP + n2;
       for (int l = 0; l <= lmax; ++l) {
-        const float hv = f * hrow[l];
+        const float hv = f * (sc * (grow[l] - qrow[l] * dot));
         m1[(size_t)l * nch * NP] = hv;
         if (c1 != c2) m2[(size_t)l * nch * NP] = hv;
       }
     }
     __syncthreads();
 
-    // ---- G[s][lm][n] = sum_c2 M[s][l][c2][n] c[c2][lm]
-    float gmax = 0.f;
-    for (int lm = tid; lm < L; lm += NT) {
-      const int l = (int)sqrtf((float)lm + 0.5f);
-      const int tau = tau_of(l, lm - l * l - l, lmax);
-      for (int s = 0; s < a.nsp; ++s) {
-        float acc[NP];
+    // ---- G[s][lm][n] = sum_c2 M[s][l][c2][n] c[c2][lm], one thread per lm row
+    auto grow_of = [&](int lm, int l, int sp, float (&acc)[NP]) {
 #pragma unroll
-        for (int n = 0; n < NP; ++n) acc[n] = 0.f;
-        const float4* m4 = reinterpret_cast<const float4*>(ms + (size_t)(s * lp1 + l) * nch * NP);
-        const float* cp = cs + lm;
+      for (int n = 0; n < NP; ++n) acc[n] = 0.f;
+      const float4* m4 = reinterpret_cast<const float4*>(ms + (size_t)(sp * lp1 + l) * nch * NP);
+      const float* cp = cs + lm;
 #pragma unroll 2
-        for (int c2 = 0; c2 < nch; ++c2) {
-          const float cv = cp[c2 * L];
+      for (int c2 = 0; c2 < nch; ++c2) {
+        const float cv = cp[c2 * L];
 #pragma unroll
-          for (int q4 = 0; q4 < NP / 4; ++q4) {
-            const float4 mv = m4[c2 * (NP / 4) + q4];
-            if (4 * q4 + 0 < NC) acc[4 * q4 + 0] = fmaf(mv.x, cv, acc[4 * q4 + 0]);
-            if (4 * q4 + 1 < NC) acc[4 * q4 + 1] = fmaf(mv.y, cv, acc[4 * q4 + 1]);
-            if (4 * q4 + 2 < NC) acc[4 * q4 + 2] = fmaf(mv.z, cv, acc[4 * q4 + 2]);
-            if (4 * q4 + 3 < NC) acc[4 * q4 + 3] = fmaf(mv.w, cv, acc[4 * q4 + 3]);
-          }
+        for (int q4 = 0; q4 < NP / 4; ++q4) {
+          const float4 mv = m4[c2 * (NP / 4) + q4];
+          if (4 * q4 + 0 < NC) acc[4 * q4 + 0] = fmaf(mv.x, cv, acc[4 * q4 + 0]);
+          if (4 * q4 + 1 < NC) acc[4 * q4 + 1] = fmaf(mv.y, cv, acc[4 * q4 + 1]);
+          if (4 * q4 + 2 < NC) acc[4 * q4 + 2] = fmaf(mv.z, cv, acc[4 * q4 + 2]);
+          if (4 * q4 + 3 < NC) acc[4 * q4 + 3] = fmaf(mv.w, cv, acc[4 * q4 + 3]);
         }
-#pragma unroll
-        for (int n = 0; n < NP; ++n) {
-          if (!(n < NC)) acc[n] = 0.f;
-          gmax = fmaxf(gmax, fabsf(acc[n]));
-        }
-        float4* row = reinterpret_cast<float4*>(g32 + ((size_t)s * T16 + tau) * NP);
-#pragma unroll
-        for (int q4 = 0; q4 < NP / 4; ++q4)
-          row[q4] = make_float4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3]);
       }
-    }
-    gmax = block_max<W>(gmax, red2 + W);
+    };
+    unsigned char* img = a.gimg + (size_t)atom * img_bytes;
+    float gmax = 0.f;
     int eg = 0;
-    frexpf(gmax, &eg);
-    eg = max(-100, min(eg, 100));
-    const float sg = ldexpf(1.f, 14 - eg);
-    if (tid == 0) tc5::bulk_wait_read0();  // the previous atom's image has left the stage
-    __syncthreads();
-    for (int row = tid; row < a.nsp * T16; row += NT) {
-      const int s = row / T16, tau = row - s * T16;
-      const bool real = tau < TE ? tau <= lmax : tau < TN;
-      float v[NC];
-      const float4* r4 = reinterpret_cast<const float4*>(g32 + (size_t)row * NP);
+    if (a.nsp == 1) {
+      // rows kept in registers across the block maximum, then scaled, split and written; the
+      // padding rows of the image are never read by the adjoint's sweep and stay unwritten
+      constexpr int RPT = (L + NT - 1) / NT;
+      float accr[RPT][NP];
 #pragma unroll
-      for (int q4 = 0; q4 < NP / 4; ++q4) {
-        const float4 x = real ? r4[q4] : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (4 * q4 + 0 < NC) v[4 * q4 + 0] = x.x * sg;
-        if (4 * q4 + 1 < NC) v[4 * q4 + 1] = x.y * sg;
-        if (4 * q4 + 2 < NC) v[4 * q4 + 2] = x.z * sg;
-        if (4 * q4 + 3 < NC) v[4 * q4 + 3] = x.w * sg;
+      for (int r = 0; r < RPT; ++r) {
+        const int lm = tid + r * NT;
+        if (lm < L) {
+          grow_of(lm, (int)sqrtf((float)lm + 0.5f), 0, accr[r]);
+#pragma unroll
+          for (int n = 0; n < NC; ++n) gmax = fmaxf(gmax, fabsf(accr[r][n]));
+        }
       }
-      write_split_row_sw<NC, KP, false>(stage + (size_t)s * Dm::IMG, Dm::img_row(tau), Dm::img_chunk(tau), v);
+      gmax = block_max<W>(gmax, red2 + W);
+      frexpf(gmax, &eg);
+      eg = max(-100, min(eg, 100));
+      const float sg = ldexpf(1.f, 14 - eg);
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const int lm = tid + r * NT;
+        if (lm < L) {
+          const int l = (int)sqrtf((float)lm + 0.5f);
+          const int tau = tau_of(l, lm - l * l - l, lmax);
+          float v[NC];
+#pragma unroll
+          for (int n = 0; n < NC; ++n) v[n] = accr[r][n] * sg;
+          write_split_row_sw<NC, KP, false>(img, Dm::img_row(tau), Dm::img_chunk(tau), v);
+        }
+      }
+    } else {
+      for (int lm = tid; lm < L; lm += NT) {
+        const int l = (int)sqrtf((float)lm + 0.5f);
+        const int tau = tau_of(l, lm - l * l - l, lmax);
+        for (int sp = 0; sp < a.nsp; ++sp) {
+          float acc[NP];
+          grow_of(lm, l, sp, acc);
+#pragma unroll
+          for (int n = 0; n < NP; ++n) {
+            if (!(n < NC)) acc[n] = 0.f;
+            gmax = fmaxf(gmax, fabsf(acc[n]));
+          }
+          float4* row = reinterpret_cast<float4*>(g32 + ((size_t)sp * T16 + tau) * NP);
+#pragma unroll
+          for (int q4 = 0; q4 < NP / 4; ++q4)
+            row[q4] = make_float4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3]);
+        }
+      }
+      gmax = block_max<W>(gmax, red2 + W);
+      frexpf(gmax, &eg);
+      eg = max(-100, min(eg, 100));
+      const float sg = ldexpf(1.f, 14 - eg);
+      for (int row = tid; row < a.nsp * T16; row += NT) {
+        const int sp = row / T16, tau = row - sp * T16;
+        const bool real = tau < TE ? tau <= lmax : tau < TN;
+        float v[NC];
+        const float4* r4 = reinterpret_cast<const float4*>(g32 + (size_t)row * NP);
+#pragma unroll
+        for (int q4 = 0; q4 < NP / 4; ++q4) {
+          const float4 x = real ? r4[q4] : make_float4(0.f, 0.f, 0.f, 0.f);
+          if (4 * q4 + 0 < NC) v[4 * q4 + 0] = x.x * sg;
+          if (4 * q4 + 1 < NC) v[4 * q4 + 1] = x.y * sg;
+          if (4 * q4 + 2 < NC) v[4 * q4 + 2] = x.z * sg;
+          if (4 * q4 + 3 < NC) v[4 * q4 + 3] = x.w * sg;
+        }
+        write_split_row_sw<NC, KP, false>(img + (size_t)sp * Dm::IMG, Dm::img_row(tau), Dm::img_chunk(tau), v);
+      }
     }
-    tc5::fence_proxy_async();  // the rows, written by threads, reach the bulk copy
-    __syncthreads();
-    if (tid == 0) {
-      tc5::bulk_store(a.gimg + (size_t)atom * img_bytes, stage, img_bytes);
-      tc5::bulk_commit();
-      a.gexp[atom] = eg;
-    }
+    if (tid == 0) a.gexp[atom] = eg;
   }
-  if (tid == 0) tc5::bulk_wait_all();
 }
 
 template <int NC, int LC>
