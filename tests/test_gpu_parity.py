@@ -631,3 +631,33 @@ def test_forward_variants_against_oracle(case, golden):
         print(f"PARITY forward variant {v} {case}: p {err:.2e}")
         assert err < MIXED["p"]
     assert rel_rows(outs[2], outs[1]) < 1e-5
+
+
+@pytest.mark.parametrize("n_max,l_max", [(12, 12), (8, 8)])
+def test_tcgen05_adjoint_every_image_layout(n_max, l_max):
+    """The tcgen05 adjoint reads its per-atom G operand from an image: two harmonic rows per
+    128-byte row when the split rows take 64 bytes (n_max <= 10), one per row at n_max = 12;
+    and a G buffer in shared memory when there are several species.  n = l = 12 (one species)
+    and n = l = 8 with two species, forced through the tile plan, against the oracle's forces
+    and the mma.sync kernel's."""
+    nsp = 2 if n_max == 8 else 1
+    P = Params(r_cut=5.0, r_soft=4.5, sigma_r0=0.5, sigma_p0=0.5, n_max=n_max, l_max=l_max, n_species=nsp)
+    W = oracle_W(P.n_max, P.r_cut, P.sigma_r0)
+    probs = [0.6, 0.4] if nsp == 2 else None
+    batch = synth.concat([synth.random_box(48, density=0.12, dmin=1.1, seed=51, species_probs=probs)])
+    sb = synth.concat([synth.random_box(20, density=0.12, dmin=1.1, seed=52, species_probs=probs)])
+    qs = soap.descriptors(sb, P, W=W)["q"].numpy()
+    al = synth.gap_weights(len(qs), 53)
+    ref = gap.evaluate(batch, P, qs, al, 3.0, W=W, virial=False)["forces"]
+    model = model_for(params_dict(P), "mixed", qs, al, 3.0)
+    s = structures(batch)
+    model.compute(s, energy=True)
+    forces = {}
+    for variant in (5, 4):
+        model.set_plan(s, {"adjoint_warps": variant, "gap_forward": 0, "gap_backward": 0,
+                           "neighbour_sweep": 0, "pair_forward": 0})
+        forces[variant] = model.compute(s, energy=True, forces=True)["forces"].cpu().numpy()
+        err = rel_all(forces[variant], ref)
+        print(f"PARITY n={n_max} l={l_max} species {nsp}: adjoint variant {variant}: F {err:.2e}")
+        assert err < MIXED["f"]
+    assert rel_all(forces[5], forces[4]) < 1e-5
