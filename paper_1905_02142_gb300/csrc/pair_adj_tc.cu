@@ -5,13 +5,15 @@
 // harmonics (Sec. III.C) instead of storing dc/dr.
 //
 //   the G-operand kernel (adj_gop_kernel), one block per atom: h = dE/dp, G_l = M_l c_l,
-//     stored as FP16 split rows G16[tau] (B operand, K-major, 128-byte swizzled rows; tau =
-//     harmonic index in the recursion's visit order) in a per-atom image in global memory:
-//     rows tau and tau + 64 of each 128 share one 128-byte row (the first and the second 64
-//     bytes), as the A tile packs b and b'; with the image, the power of two scaling G
+//     scaled by a power of two and stored as FP16 split rows G16[tau] (B operand, K-major,
+//     128-byte swizzled rows; tau = harmonic index in the recursion's visit order) in a
+//     per-atom image in global memory, with the exponent of the scale: rows tau and tau + 64
+//     of each 128 share one 128-byte row (its first and second 64 bytes) when a split row
+//     takes 64 bytes (n_max <= 10), as the A tile packs b and b'
 //   the adjoint kernel, one block of 4 warps per atom (persistent over atoms): the atom's
-//     image is bulk-copied into shared memory while the block works on the previous atom
-//   one thread per pair, 128 pairs of one (atom, neighbour species) segment per tile:
+//     image is bulk-copied into one of two shared-memory buffers while the block works on
+//     the previous atom; then one thread per pair, 128 pairs of one (atom, neighbour
+//     species) segment per tile:
 //     b_n(r) and b_n'(r) from the radial table, as FP16 split rows of the A operand
 //     u[pair][tau] = sum_n b_n G[tau][n] and u'[pair][tau] = sum_n b_n' G[tau][n]:
 //       tcgen05.mma M = 128 pairs, N = 64 harmonics per phase, K = 3 n_max (padded to 16),
@@ -83,7 +85,7 @@ struct GopLayout {
 
 // scratch of the G-operand kernel, in floats: [q | dE/dq], later reused for G; c; M
 template <int NC, int LC>
-int tc_prologue_floats(int nsp, int dim) {
+int gop_scratch_floats(int nsp, int dim) {
   using Dm = TcDims<NC, LC>;
   const int nch = nsp * NC, L = Dm::LP * Dm::LP;
   return std::max(2 * align4(dim), nsp * Dm::T16 * Dm::NP) + align4(nch * L) + nsp * Dm::LP * nch * Dm::NP;
@@ -112,7 +114,7 @@ GopLayout make_gop_layout(int nsp, int dim) {
   const int nch = nsp * NC;
   m.off_pc = 0;
   m.off_scr = (m.off_pc + 4 * (nch * (nch + 1) / 2) + 15) / 16 * 16;
-  m.off_red = m.off_scr + 4 * tc_prologue_floats<NC, LC>(nsp, dim);
+  m.off_red = m.off_scr + 4 * gop_scratch_floats<NC, LC>(nsp, dim);
   m.total = m.off_red + 4 * 8;
   return m;
 }
