@@ -205,7 +205,7 @@ int soapgap_sync_status(soapgap_handle* h, void* stream);
  *   plan[1]  tile configuration of the GAP forward product (columns per tile, pipeline
  *            stages, epilogue warps): 0 = (256, 4, 8), 1 = (128, 6, 4), 2 = (128, 6, 8)
  *   plan[2]  the same for the GAP backward product: 0 = (224, 5, 4), 1 = (128, 6, 4),
- *            2 = (192, 5, 4), 3 = (256, 4, 4)
+ *            2 = (192, 5, 4), 3 = (256, 4, 4), 4 = (160, 6, 4)
  *   plan[3]  the neighbour sweep: 1 = one block per bin, the bin's candidates staged once in
  *            shared memory; 2 = one warp per atom; 0 = per bin for a single structure with at
  *            least 8 bins per SM, else per atom (timed only without a Verlet skin)

@@ -566,7 +566,7 @@ __global__ void prep_atoms_kernel(const float* __restrict__ q, int n, int d, int
 // Tile configurations of the two GAP products, chosen by the autotuner.  Each is a
 // (columns per tile BN, pipeline stages, epilogue warps) instance of tc_gemm_kernel:
 //   forward  0: (256, 4, 8)   1: (128, 6, 4)   2: (128, 6, 8)
-//   backward 0: (224, 5, 4)   1: (128, 6, 4)   2: (192, 5, 4)   3: (256, 4, 4)
+//   backward 0: (224, 5, 4)   1: (128, 6, 4)   2: (192, 5, 4)   3: (256, 4, 4)   4: (160, 6, 4)
 // The forward's columns are the sparse set padded to 256 (every BN above divides it); the
 // backward's, the descriptor padded to 64 (ragged last tiles read TMA's zero fill).
 static int fwd_bn(int cfg) { return cfg == 0 ? 256 : 128; }
@@ -637,6 +637,7 @@ cudaError_t sg_gap_tc_backward(const GapTcModel& md, const __half* kp, const flo
     case 1: return launch_gemm<128, 6, 4>(kp, n, md.BT, md.dp, md.mp, e, err, st);
     case 2: return launch_gemm<192, 5, 4>(kp, n, md.BT, md.dp, md.mp, e, err, st);
     case 3: return launch_gemm<256, 4, 4>(kp, n, md.BT, md.dp, md.mp, e, err, st);
+    case 4: return launch_gemm<160, 6, 4>(kp, n, md.BT, md.dp, md.mp, e, err, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -189,7 +189,7 @@ struct GapTcModel {
   int fwd_cfg, bwd_cfg;   // tile configurations of the forward and backward products
 };
 #define SG_GAP_FWD_CFGS 3
-#define SG_GAP_BWD_CFGS 4
+#define SG_GAP_BWD_CFGS 5
 // partial-sum slots per atom row of the forward product with configuration fwd_cfg, and
 // the most any configuration needs
 int sg_gap_tc_tiles(int mp, int fwd_cfg);

@@ -137,7 +137,7 @@ def test_autotune_keeps_results(batched):
     before = {k: v.clone() for k, v in model.compute(s, **OUT).items()}
     plan = model.autotune(s)
     assert plan["adjoint_warps"] in (2, 3, 4, 5)
-    assert 0 <= plan["gap_forward"] < 3 and 0 <= plan["gap_backward"] < 4
+    assert 0 <= plan["gap_forward"] < 3 and 0 <= plan["gap_backward"] < 5
     assert plan["pair_forward"] in (1, 2)
     assert model.plan(s) == {k: plan[k] for k in model.PLAN_KEYS}
     after = model.compute(s, **OUT)
@@ -167,7 +167,7 @@ def test_every_tile_plan_gives_the_same_results(batched):
         ref[pf] = {k: v.clone() for k, v in model.compute(s, **OUT).items()}
     for k, bar in (("forces", 1e-4), ("e_struct", 1e-5), ("e_atom", 1e-4)):
         assert rel(ref[2][k], ref[1][k]) < bar, (k, rel(ref[2][k], ref[1][k]))
-    for warps, fwd, bwd in itertools.product((2, 4, 5), range(3), range(4)):
+    for warps, fwd, bwd in itertools.product((2, 4, 5), range(3), range(5)):
         pf = 1 + (fwd + 2 * bwd + warps) % 2
         model.set_plan(s, {"adjoint_warps": warps, "gap_forward": fwd, "gap_backward": bwd,
                            "neighbour_sweep": (fwd + bwd) % 3, "pair_forward": pf})
