@@ -135,16 +135,6 @@ struct EpiGapFwd {
     }
     buf ^= 1;
   }
-  __device__ void apply(int row, int col0, const uint32_t* v) {
-    if (row >= rows) return;
-    uint32_t out[16];   // 32 FP16 kernel derivatives, packed in pairs (registers)
-    row_chunk(col0, v, out);
-    if (kp) {
-      uint4* dst = reinterpret_cast<uint4*>(kp + (size_t)row * ld_kp + col0);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) dst[k] = make_uint4(out[4 * k], out[4 * k + 1], out[4 * k + 2], out[4 * k + 3]);
-    }
-  }
   __device__ void end(int row, int slot) {
     if (row >= rows) return;
     eps_part[(size_t)row * n_tiles + slot] = eps;
