@@ -10,10 +10,11 @@
 //     per-atom image in global memory, with the exponent of the scale: rows tau and tau + 64
 //     of each 128 share one 128-byte row (its first and second 64 bytes) when a split row
 //     takes 64 bytes (n_max <= 10), as the A tile packs b and b'
-//   the adjoint kernel, one block of 4 warps per atom (persistent over atoms): the atom's
+//   the adjoint kernel, one block of 3 warps per atom (persistent over atoms): the atom's
 //     image is bulk-copied into one of two shared-memory buffers while the block works on
-//     the previous atom; then one thread per pair, 128 pairs of one (atom, neighbour
-//     species) segment per tile:
+//     the previous atom; then one thread per pair, 96 pairs of one (atom, neighbour
+//     species) segment per tile (the MMA's rows 96..127 are not read), the pair's radial
+//     factors in registers for the sweep (168 registers, 4 blocks per SM):
 //     b_n(r) and b_n'(r) from the radial table, as FP16 split rows of the A operand
 //     u[pair][tau] = sum_n b_n G[tau][n] and u'[pair][tau] = sum_n b_n' G[tau][n]:
 //       tcgen05.mma M = 128 pairs, N = 64 harmonics per phase, K = 3 n_max (padded to 16),
@@ -40,7 +41,8 @@
 
 namespace {
 
-constexpr int TC_THREADS = 128;        // 4 warps: the MMA's 128 rows, one pair per thread
+constexpr int TC_THREADS = 96;         // 3 warps, one pair per thread: 96 of the MMA's 128 rows
+constexpr int GOP_THREADS = 128;       // G-operand kernel
 constexpr int TC_PHASE = 64;           // harmonics per MMA phase
 constexpr uint32_t TC_TMEM_COLS = 128; // u (64 columns) | u' (64 columns)
 
@@ -71,7 +73,6 @@ template <int NC, int LC> struct TcDims {
 struct TcLayout {
   int off_g16;    // two buffers of the atom's image ([nsp][ROWS] rows of 128 B each)
   int off_union;  // the A tile(s)
-  int off_ild;    // the per-warp ild arrays
   int off_red;
   int total;      // bytes to request (includes 1024 for the base alignment)
 };
@@ -97,10 +98,8 @@ TcLayout make_tc_layout(int nsp) {
   TcLayout m{};
   m.off_g16 = 0;
   m.off_union = (2 * nsp * Dm::IMG + 1023) / 1024 * 1024;
-  const int ild = 4 * 2 * Dm::LP * 32 * 4;  // four warps
-  m.off_ild = m.off_union + Dm::A_BYTES;
-  m.off_red = (m.off_ild + ild + 15) / 16 * 16;
-  m.total = m.off_red + (4 * 9) * 4 + 1024;
+  m.off_red = (m.off_union + Dm::A_BYTES + 15) / 16 * 16;
+  m.total = m.off_red + (TC_THREADS / 32 * 9) * 4 + 1024;
   // at most 4 blocks per SM (228 KB of shared memory, 1 KB reserved per block), so that the
   // blocks' tensor-memory allocations (4 x 128 columns) never exceed the SM's 512
   m.total = std::max(m.total, 47 * 1024);
@@ -147,16 +146,16 @@ __device__ __forceinline__ void write_split_row_sw(unsigned char* tile, int row,
   }
 }
 
-__device__ __forceinline__ void phase_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void phase_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(TC_THREADS) : "memory"); }
 
 // The (l, m) sweep of one pair, fully unrolled for l_max = LC (as adj_sweep_unrolled in
 // pair_adj_mma.cu), reading u / u' of harmonic tau from ur / upr[tau & 15] after
 // refill(tau >> 4) at every multiple of 16.
 template <int LC, typename Refill>
-__device__ __forceinline__ void tc_sweep(const YlmCoef<float>& yc, float ux, float uy, float uz, const float* il_l,
+__device__ __forceinline__ void tc_sweep(const YlmCoef<float>& yc, float ux, float uy, float uz,
+                                         const float (&il_l)[LC + 1], const float (&dil_l)[LC + 1],
                                          const uint32_t (&ur)[16], const uint32_t (&upr)[16], Refill&& refill,
                                          float& srad, float& hx, float& hy, float& hz) {
-  constexpr int LP = LC + 1;
   constexpr int TE = (LC + 2) & ~1;
   float cm = 1.f, sm = 0.f, cmm1 = 0.f, smm1 = 0.f;
   // column m + 1 of the recursion, computed at step m for the z-derivatives, is column m of
@@ -196,7 +195,7 @@ __device__ __forceinline__ void tc_sweep(const YlmCoef<float>& yc, float ux, flo
         col[l] = ql;
       }
       const float dz = yc.d[l][m] * ql;
-      const float il = il_l[32 * l], dil = il_l[32 * (LP + l)];
+      const float il = il_l[l], dil = dil_l[l];
       // tau of (l, m): l for m = 0, else the cos-type entry of the (cos, sin) pair
       const int tau = m == 0 ? l : TE + 2 * ((m - 1) * (LC + 1) - m * (m - 1) / 2) + 2 * (l - m);
       if ((tau & 15) == 0) refill(tau >> 4);
@@ -236,11 +235,11 @@ __device__ __forceinline__ void tc_sweep(const YlmCoef<float>& yc, float ux, flo
 // and split into FP16 rows, written to the atom's image (each thread 64 bytes of a row: two
 // whole 32-byte sectors), and e.
 template <int NC, int LC>
-__global__ void __launch_bounds__(TC_THREADS) adj_gop_kernel(const AdjArgs<float> a, const GopLayout lay) {
+__global__ void __launch_bounds__(GOP_THREADS) adj_gop_kernel(const AdjArgs<float> a, const GopLayout lay) {
   using Dm = TcDims<NC, LC>;
   constexpr int KP = Dm::KP, NP = Dm::NP, LP = Dm::LP, T16 = Dm::T16;
   constexpr int TE = Dm::TE, TN = Dm::TN;
-  constexpr int W = 4, NT = TC_THREADS;
+  constexpr int W = GOP_THREADS / 32, NT = GOP_THREADS;
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x;
   constexpr int lmax = LC, nmax = NC;
@@ -408,7 +407,7 @@ template <int NC, int LC>
 __global__ void __launch_bounds__(TC_THREADS, 4) pair_adj_tc_kernel(const AdjArgs<float> a, const TcLayout lay) {
   using Dm = TcDims<NC, LC>;
   constexpr int KP = Dm::KP, KS = Dm::KS, LP = Dm::LP, T16 = Dm::T16, NPH = Dm::NPH;
-  constexpr int W = 4, NT = TC_THREADS;
+  constexpr int W = TC_THREADS / 32, NT = TC_THREADS;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -424,7 +423,6 @@ __global__ void __launch_bounds__(TC_THREADS, 4) pair_adj_tc_kernel(const AdjArg
   unsigned char* atile = uni;                    // A: b rows (and b' rows when packed)
   unsigned char* atile_p = Dm::PACKED ? uni : uni + 128 * 128;
   constexpr int chunk_p = Dm::PACKED ? 4 : 0;    // first 16-byte chunk of the b' rows
-  float* ild = reinterpret_cast<float*>(smem + lay.off_ild) + warp * 2 * LP * 32;  // [2][LP][32]
 
   const uint32_t img_bytes = (uint32_t)(a.nsp * Dm::IMG);
   if (tid == 0) {
@@ -488,7 +486,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) pair_adj_tc_kernel(const AdjArg
       const int end = a.seg_offs[atom * a.nsp + s + 1];
       const uint32_t gsp = tc5::smem_u32(gimg + (size_t)buf * img_bytes + (size_t)s * Dm::IMG);
       for (int tbase = beg; tbase < end; tbase += NT) {
-        // ---- radial terms of this thread's pair -> A rows (b, b') and ild
+        // ---- radial terms of this thread's pair -> A rows (b, b'), il and dil (registers)
         const int pidx = tbase + tid;
         const bool valid = pidx < end;
         float ux = 0.f, uy = 0.f, uz = 1.f, r = 1.f, inv_r = 1.f;
@@ -505,6 +503,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) pair_adj_tc_kernel(const AdjArg
           uz = v.z * inv_r;
         }
         int eb = 0;
+        float il[LP], dil[LP];  // 4 pi ilexp_l and its r-derivative, kept for the sweep
         {
           float f[NC + LC + 1], df[NC + LC + 1];
           table_interp<NC, LC, true>(a.table, a.ti, r, f, df);
@@ -528,8 +527,8 @@ __global__ void __launch_bounds__(TC_THREADS, 4) pair_adj_tc_kernel(const AdjArg
           write_split_row_sw<NC, KP, true>(atile_p, tid, chunk_p, dbn);
 #pragma unroll
           for (int l = 0; l < LP; ++l) {
-            ild[l * 32 + lane] = f[NC + l];
-            ild[(LP + l) * 32 + lane] = df[NC + l];
+            il[l] = f[NC + l];
+            dil[l] = df[NC + l];
           }
         }
         tc5::fence_proxy_async();  // the A rows, written by threads, reach the tensor cores
@@ -580,7 +579,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) pair_adj_tc_kernel(const AdjArg
             tc5::tmem_ld16_nw(ta + TC_PHASE, upr);
             tc5::tmem_wait();
           };
-          tc_sweep<LC>(a.yc, ux, uy, uz, ild + lane, ur, upr, refill, srad, hx, hy, hz);
+          tc_sweep<LC>(a.yc, ux, uy, uz, il, dil, ur, upr, refill, srad, hx, hy, hz);
         } else {
           // no pair in this warp: only the phase barriers, and the MMA counter
           for (int ph = 0; ph < NPH; ++ph) {
@@ -652,10 +651,10 @@ cudaError_t launch_tc(const AdjArgs<float>& a, cudaStream_t st) {
     cudaError_t e = sg_set_smem<adj_gop_kernel<NC, LC>>(gl.total);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TC_THREADS, gl.total);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, GOP_THREADS, gl.total);
     long long grid = (long long)sms * std::max(1, per_sm);
     if (grid > a.n_atoms) grid = a.n_atoms;
-    kern<<<(unsigned)grid, TC_THREADS, gl.total, st>>>(a, gl);
+    kern<<<(unsigned)grid, GOP_THREADS, gl.total, st>>>(a, gl);
     ++sg_kernel_launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
