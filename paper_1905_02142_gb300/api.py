@@ -277,13 +277,15 @@ class SoapGap:
 
     def autotune(self, s: Structures, stream=None, cache: str | None = None) -> dict:
         """Pick the tile plan of this batch's problem class (soapgap_autotune): the adjoint
-        variant, the tile configurations of the two GAP products and the neighbour sweep.
+        variant, the tile configurations of the two GAP products, the neighbour sweep and the
+        forward pair kernel.
 
         cache: path of a JSON file of earlier choices, keyed by device, precision, basis,
-        species, model size, FP16 products and problem class.  A plan found there is
-        installed without timing (soapgap_set_plan); a new one is timed and added.
+        species, model size, FP16 products and problem class.  A complete plan found there is
+        installed without timing (soapgap_set_plan); an entry written by a version with fewer
+        plan entries, or one the library rejects, is timed again and replaced.
         Returns {"adjoint_warps", "gap_forward", "gap_backward", "neighbour_sweep",
-        "cached"}."""
+        "pair_forward", "cached"}."""
         st = (stream or torch.cuda.current_stream(s.pos.device)).cuda_stream
         b = s.c_batch()
         key = None
@@ -295,11 +297,12 @@ class SoapGap:
                     known = json.load(f)
             except (OSError, ValueError):
                 known = {}
-            if key in known:
-                vals = [int(known[key][k]) for k in self.PLAN_KEYS]
+            entry = known.get(key)
+            if isinstance(entry, dict) and all(k in entry for k in self.PLAN_KEYS):
+                vals = [int(entry[k]) for k in self.PLAN_KEYS]
                 arr = (ctypes.c_int32 * L.PLAN_LEN)(*vals)
-                self._check(self.lib.soapgap_set_plan(self.h, ctypes.byref(b), arr))
-                return dict(zip(self.PLAN_KEYS, vals), cached=True)
+                if self.lib.soapgap_set_plan(self.h, ctypes.byref(b), arr) == L.OK:
+                    return dict(zip(self.PLAN_KEYS, vals), cached=True)
         arr = (ctypes.c_int32 * L.PLAN_LEN)()
         self._check(self.lib.soapgap_autotune(self.h, ctypes.byref(b), arr, st))
         plan = dict(zip(self.PLAN_KEYS, [int(x) for x in arr]))

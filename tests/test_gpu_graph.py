@@ -198,3 +198,27 @@ def test_plan_cache_round_trip(batched, tmp_path):
     assert second["cached"]
     assert {k: second[k] for k in other.PLAN_KEYS} == {k: first[k] for k in model.PLAN_KEYS}
     assert other.plan(s) == {k: first[k] for k in model.PLAN_KEYS}
+
+
+def test_plan_cache_entry_without_the_forward_kernel_is_retuned(batched, tmp_path):
+    """A cache entry written before the plan held the forward-kernel choice is timed again
+    and replaced, not read with a missing key."""
+    import json
+
+    from paper_1905_02142_gb300.api import Structures
+    w, batch = batched
+    cache = str(tmp_path / "plans.json")
+    model = make_model(w.params(), w.n_sparse, w.zeta)
+    s = Structures.from_batch(batch)
+    model.autotune(s, cache=cache)
+    with open(cache) as f:
+        known = json.load(f)
+    for entry in known.values():
+        entry.pop("pair_forward")
+    with open(cache, "w") as f:
+        json.dump(known, f)
+    other = make_model(w.params(), w.n_sparse, w.zeta)
+    again = other.autotune(s, cache=cache)
+    assert not again["cached"]
+    with open(cache) as f:
+        assert all("pair_forward" in e for e in json.load(f).values())
