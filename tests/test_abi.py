@@ -25,6 +25,42 @@ def lib():
     return _lib.load()
 
 
+def declared_constants():
+    """Integer #defines of the header (SOAPGAP_X -> value), comments removed."""
+    src = open(os.path.join(ROOT, "include", "soapgap.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for name, val in re.findall(r"#define\s+SOAPGAP_([A-Z0-9_]+)\s+\(?(-?\d+)u?\)?", src):
+        out[name] = int(val)
+    return out
+
+
+def test_binding_constants_match_the_header():
+    """Every constant the Python binding mirrors (status codes, precisions, call flags, stage
+    and plan lengths, peak kinds) has the header's value, and the name tuples have the
+    header's lengths."""
+    from paper_1905_02142_gb300 import _lib
+    from paper_1905_02142_gb300.api import SoapGap
+    hdr = declared_constants()
+    mirrored = ["OK", "E_INVALID_ARG", "E_UNSUPPORTED", "E_CAPACITY", "E_CUDA", "E_STATE",
+                "FP64", "MIXED", "DESC", "ENERGY", "FORCES", "VIRIAL", "TIMING", "ASYNC",
+                "DESIGN_K", "DESIGN_KSTRUCT", "DESIGN_DK", "N_DESIGN_STAGES", "N_STAGES",
+                "PLAN_LEN", "PEAK_FP32_FMA", "PEAK_FP64_FMA"]
+    for name in mirrored:
+        assert name in hdr, name
+        assert getattr(_lib, name) == hdr[name], (name, getattr(_lib, name), hdr[name])
+    assert len(_lib.STAGES) == hdr["N_STAGES"]
+    assert len(_lib.DESIGN_STAGES) == hdr["N_DESIGN_STAGES"]
+    assert len(SoapGap.PLAN_KEYS) == hdr["PLAN_LEN"]
+    flags = [hdr[f] for f in ("DESC", "ENERGY", "FORCES", "VIRIAL", "TIMING", "ASYNC",
+                              "DESIGN_K", "DESIGN_KSTRUCT", "DESIGN_DK")]
+    assert all(f & (f - 1) == 0 for f in flags) and len(set(flags)) == len(flags)
+    # the kernels size their per-species arrays by the library's own limit, which the
+    # parameter check takes from the header
+    common = open(os.path.join(ROOT, "paper_1905_02142_gb300", "csrc", "common.cuh")).read()
+    assert int(re.search(r"#define\s+SG_MAX_SPECIES\s+(\d+)", common).group(1)) == hdr["MAX_SPECIES"]
+
+
 def test_every_declared_symbol_is_exported(lib):
     from paper_1905_02142_gb300 import _lib
     names = declared_functions()
