@@ -22,6 +22,17 @@ class SoapGapError(RuntimeError):
         self.code = code
 
 
+def _read_plan_cache(path: str) -> dict:
+    """The plan cache's entries by problem class; empty when the file is missing, unreadable
+    or not a JSON object."""
+    try:
+        with open(path) as f:
+            known = json.load(f)
+    except (OSError, ValueError):
+        return {}
+    return known if isinstance(known, dict) else {}
+
+
 def _ptr(t) -> int | None:
     if t is None:
         return None
@@ -292,14 +303,14 @@ class SoapGap:
         if cache:
             self.compute(s, energy=True, forces=True, stream=stream)
             key = self._plan_cache_key(s)
-            try:
-                with open(cache) as f:
-                    known = json.load(f)
-            except (OSError, ValueError):
-                known = {}
-            entry = known.get(key)
+            entry = _read_plan_cache(cache).get(key)
+            vals = None
             if isinstance(entry, dict) and all(k in entry for k in self.PLAN_KEYS):
-                vals = [int(entry[k]) for k in self.PLAN_KEYS]
+                try:
+                    vals = [int(entry[k]) for k in self.PLAN_KEYS]
+                except (TypeError, ValueError):
+                    vals = None
+            if vals is not None:
                 arr = (ctypes.c_int32 * L.PLAN_LEN)(*vals)
                 if self.lib.soapgap_set_plan(self.h, ctypes.byref(b), arr) == L.OK:
                     return dict(zip(self.PLAN_KEYS, vals), cached=True)
@@ -307,11 +318,7 @@ class SoapGap:
         self._check(self.lib.soapgap_autotune(self.h, ctypes.byref(b), arr, st))
         plan = dict(zip(self.PLAN_KEYS, [int(x) for x in arr]))
         if cache:
-            try:
-                with open(cache) as f:
-                    known = json.load(f)
-            except (OSError, ValueError):
-                known = {}
+            known = _read_plan_cache(cache)
             known[key] = plan
             d = os.path.dirname(os.path.abspath(cache))
             os.makedirs(d, exist_ok=True)
